@@ -1,0 +1,18 @@
+"""CPU FP64 oracle for the semilinear lens-inversion inner loop.
+
+TEST INFRASTRUCTURE ONLY.  This package is the plain, slow, obviously
+correct restatement of what the GPU path computes, written from the paper
+(Rogers & Fiege 2011, Sections 2.1-2.6): explicit sparse L, explicit B,
+diagonal W, explicit H, dense Cholesky per lambda, and the L-curve corner by
+spline curvature.  It shares no code with the CUDA library and neither side
+imports the other; only the seeded input generators in ``synth`` serve both.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import it.  The product path never calls it.
+
+Modules: ``lens`` (ray trace), ``operators`` (L, B, W, H), ``solve``
+(Cholesky solve, chi^2, regularisation measure, forward batch), ``lcurve``
+(corner), ``data`` (synthetic observations), ``mlp`` (surrogate network
+forward/backward/Adam), ``cg`` (matrix-free FP64 conjugate gradient, used
+where a dense B does not fit).
+"""

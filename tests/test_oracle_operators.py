@@ -1,0 +1,161 @@
+"""Pins for the oracle's explicit operators L, B, W, H (Sections 2.1, 2.2).
+
+L is pinned by exact reproduction of bilinear functions, the identity lens,
+partition of unity and brute force on a tiny grid; B by SciPy's 2-D
+convolution / correlation and the delta PSF; H by hand-computed stencils.
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy.signal import convolve2d, correlate2d
+
+from oracle.lens import ray_trace
+from oracle.operators import (REG_GRADIENT, REG_IDENTITY, REG_LAPLACIAN, blur_matrix, image_centres,
+                              lens_matrix, reg_matrix, source_cell, weight_vector)
+from synth import Geometry, gaussian_psf
+
+LENS = [1.0, 0.7, 0.5, 0.02, -0.03, 0.05, 1.0]
+
+
+def _geom(**kw):
+    base = dict(nx=24, ny=20, pix=0.1, sx=12, sy=10, sxmin=-0.8, sxmax=0.8, symin=-0.7, symax=0.7,
+                kpsf=5, subpix=1, reg=REG_LAPLACIAN)
+    base.update(kw)
+    return Geometry(**base)
+
+
+def _source_centres(g):
+    hx = (g.sxmax - g.sxmin) / g.sx
+    hy = (g.symax - g.symin) / g.sy
+    cx = g.sxmin + (np.arange(g.sx) + 0.5) * hx
+    cy = g.symin + (np.arange(g.sy) + 0.5) * hy
+    X, Y = np.meshgrid(cx, cy)
+    return X.ravel(), Y.ravel()
+
+
+@pytest.mark.parametrize("subpix", [1, 2, 3])
+def test_bilinear_reproduces_bilinear_functions(subpix):
+    g = _geom(subpix=subpix)
+    L, mapped = lens_matrix(g, LENS)
+    X, Y = _source_centres(g)
+    f = lambda x, y: 0.3 + 1.7 * x - 0.4 * y + 2.1 * x * y
+    model = L @ f(X, Y)
+    # expected: mean over the mapped sub-rays of f(beta) (unmapped rays give 0)
+    tx, ty = image_centres(g)
+    o = ((np.arange(subpix) + 0.5) / subpix - 0.5) * g.pix
+    ox, oy = np.meshgrid(o, o)
+    rx = (tx[:, None] + ox.ravel()[None, :])
+    ry = (ty[:, None] + oy.ravel()[None, :])
+    bx, by = ray_trace(rx.ravel(), ry.ravel(), LENS)
+    m, *_ = source_cell(g, bx, by)
+    exp = np.where(m, f(bx, by), 0.0).reshape(g.npix, -1).mean(axis=1)
+    np.testing.assert_allclose(model, exp, atol=1e-12)
+    assert mapped.sum() > 0.3 * g.npix
+
+
+def test_partition_of_unity_and_positivity():
+    g = _geom()
+    L, mapped = lens_matrix(g, LENS)
+    rs = np.asarray(L.sum(axis=1)).ravel()
+    np.testing.assert_allclose(rs[mapped], 1.0, atol=1e-13)
+    assert np.all(rs[~mapped] == 0.0)
+    assert L.data.min() >= 0.0
+
+
+def test_identity_lens():
+    # b = 0, no shear, source centres on the image centres: L = I
+    g = Geometry(nx=8, ny=6, pix=0.1, sx=8, sy=6, sxmin=-0.4, sxmax=0.4, symin=-0.3, symax=0.3,
+                 kpsf=3, subpix=1, reg=REG_IDENTITY)
+    L, mapped = lens_matrix(g, [0.0, 0.8, 0.0, 0, 0, 0, 0])
+    np.testing.assert_allclose(L.toarray(), np.eye(48), atol=1e-12)
+    assert mapped.all()
+
+
+def test_brute_force_tiny():
+    # a 2x2 source and a 3x1 image, traced by hand through a pure shift
+    # (b = 0, shear only would be linear; use the identity lens with an
+    # offset source grid instead)
+    g = Geometry(nx=3, ny=1, pix=0.5, sx=2, sy=2, sxmin=-0.5, sxmax=0.5, symin=-0.5, symax=0.5,
+                 kpsf=1, subpix=1, reg=REG_IDENTITY)
+    L, mapped = lens_matrix(g, [0.0, 0.8, 0.0, 0, 0, 0, 0])
+    # source centres at +-0.25; image centres at x = -0.5, 0, 0.5, y = 0
+    # x = 0 lies midway between the centres on both axes: weights 1/4 each
+    Ld = L.toarray()
+    assert list(mapped) == [False, True, False]
+    np.testing.assert_allclose(Ld[1], [0.25, 0.25, 0.25, 0.25])
+    np.testing.assert_allclose(Ld[0], 0.0)
+
+
+def test_tie_on_last_centre():
+    # unit cells, centres at -1.5, -0.5, 0.5, 1.5 (exact in binary)
+    g = Geometry(nx=1, ny=1, pix=1.0, sx=4, sy=4, sxmin=-2.0, sxmax=2.0, symin=-2.0, symax=2.0,
+                 kpsf=1, subpix=1, reg=REG_IDENTITY)
+    m, ix, iy, u, v = source_cell(g, np.array([1.5]), np.array([1.5]))
+    assert m[0] and ix[0] == 2 and iy[0] == 2 and u[0] == 1.0 and v[0] == 1.0
+    m, ix, iy, u, v = source_cell(g, np.array([-1.5]), np.array([0.25]))
+    assert m[0] and ix[0] == 0 and iy[0] == 1 and u[0] == 0.0 and v[0] == 0.75
+    m, *_ = source_cell(g, np.array([1.5000001]), np.array([0.0]))
+    assert not m[0]
+    m, *_ = source_cell(g, np.array([0.0]), np.array([-1.5000001]))
+    assert not m[0]
+
+
+@pytest.mark.parametrize("k", [1, 3, 5, 9])
+def test_blur_matches_scipy(k):
+    g = _geom(kpsf=k)
+    rng = np.random.default_rng(4)
+    psf = rng.uniform(0, 1, (k, k))
+    x = rng.standard_normal((g.ny, g.nx))
+    y = rng.standard_normal((g.ny, g.nx))
+    B = blur_matrix(g, psf)
+    np.testing.assert_allclose((B @ x.ravel()).reshape(g.ny, g.nx), convolve2d(x, psf, mode="same"),
+                               atol=1e-12)
+    np.testing.assert_allclose((B.T @ y.ravel()).reshape(g.ny, g.nx), correlate2d(y, psf, mode="same"),
+                               atol=1e-12)
+    Bs = blur_matrix(g, psf, dense=False)
+    np.testing.assert_allclose(Bs.toarray(), B, atol=0)
+
+
+def test_delta_psf_is_identity():
+    g = _geom(kpsf=5)
+    psf = np.zeros((5, 5))
+    psf[2, 2] = 1.0
+    np.testing.assert_array_equal(blur_matrix(g, psf), np.eye(g.npix))
+
+
+def test_gaussian_psf_normalised():
+    p = gaussian_psf(9, 1.5)
+    assert abs(p.sum() - 1.0) < 1e-14
+    assert p[4, 4] == p.max()
+    np.testing.assert_allclose(p, p.T)
+    np.testing.assert_allclose(p, p[::-1, ::-1])
+
+
+def test_weights():
+    mask = np.array([[1, 1, 0]], dtype=np.uint8)
+    mapped = np.array([True, False, True])
+    sigma = np.array([[2.0, 2.0, 2.0]])
+    np.testing.assert_allclose(weight_vector(mask, mapped, sigma), [0.25, 0.0, 0.0])
+
+
+def test_regularisers_by_hand():
+    g = Geometry(nx=1, ny=1, pix=1, sx=3, sy=2, sxmin=0, sxmax=3, symin=0, symax=2, kpsf=1)
+    s = np.array([1.0, 2.0, 4.0, 0.5, -1.0, 3.0])  # rows: [1 2 4], [0.5 -1 3]
+    np.testing.assert_allclose(reg_matrix(g, REG_IDENTITY) @ s, s)
+    # gradient: Dx then Dy, zero beyond the grid
+    dx = [2 - 1, 4 - 2, 0 - 4, -1 - 0.5, 3 + 1, 0 - 3]
+    dy = [0.5 - 1, -1 - 2, 3 - 4, 0 - 0.5, 0 + 1, 0 - 3]
+    np.testing.assert_allclose(reg_matrix(g, REG_GRADIENT) @ s, dx + dy)
+    # Laplacian: 4 s - neighbours
+    lap = [4 * 1 - 2 - 0.5, 4 * 2 - 1 - 4 + 1, 4 * 4 - 2 - 3,
+           4 * 0.5 - 1 + 1, 4 * -1 - 0.5 - 3 - 2, 4 * 3 + 1 - 4]
+    np.testing.assert_allclose(reg_matrix(g, REG_LAPLACIAN) @ s, lap)
+
+
+@pytest.mark.parametrize("reg", [REG_IDENTITY, REG_GRADIENT, REG_LAPLACIAN])
+def test_hth_positive_definite(reg):
+    g = _geom()
+    H = reg_matrix(g, reg).toarray()
+    ev = np.linalg.eigvalsh(H.T @ H)
+    assert ev.min() > 1e-6

@@ -1,0 +1,331 @@
+"""Benchmark: lens-model evaluations per second on the 64x64 GA workload.
+
+One step = one batched evaluation of a 256-candidate population: ray trace,
+CGLS to relative residual 1e-6 for each of 16 lambdas (log-spaced 1e-4..1e2,
+Laplacian regulariser) and the L-curve corner of every candidate
+(64x64 image at 0.05"/px, 32x32 source over +-0.8", 9x9 Gaussian PSF).
+
+Prints one JSON line.  ``value`` is device-timed throughput with inputs
+resident in HBM; ``e2e`` is the same metric through the C ABI with pinned
+host buffers (copies inside the timed region); ``roofline`` is for the CGLS
+kernel (FP32 FFMA pipe); ``cpu_baseline`` is the FP64 oracle on the host
+cores on a bounded sample; ``plain`` is the one-candidate-per-launch
+evaluator on a sample of the same population.
+
+``--impl reference`` times the CPU oracle alone on the same metric.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "lens-model evals/s at 64^2 image, CG rel-res 1e-6 (256 cand x 16 lambda)"
+UNIT = "evals/s"
+N_CAND, N_LAM, TOL = 256, 16, 1e-6
+CONFIG = {"workload": "ga64: 64x64 image 0.05\"/px, 32x32 source +-0.8\", 9x9 PSF sigma 1.5px, Laplacian H, "
+                      "256 candidates x 16 lambdas 1e-4..1e2, CGLS rel-res 1e-6, L-curve corner",
+          "global_batch": N_CAND, "n_lambda": N_LAM, "l2": "flushed between timed steps (512 MiB write)"}
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    return rank, world
+
+
+def _cpu_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        n = [i.get("num_threads", 0) for i in threadpool_info() if i.get("user_api") == "blas"]
+        if n:
+            return int(max(n))
+    except Exception:
+        pass
+    return os.cpu_count() or 1
+
+
+def oracle_evals_per_s(n_sample: int, seed: int = 0, budget_s: float = 20.0):
+    """The FP64 oracle (dense Cholesky per lambda + L-curve) on a sample of the workload."""
+    import synth
+    from oracle.data import observe
+    from oracle.solve import eval_candidate
+    rng = np.random.default_rng(seed)
+    g = synth.geom_ga64()
+    comps = synth.drawn_source(rng)
+    prob = observe(g, synth.TRUE_LENS, comps, synth.gaussian_psf(9, 1.5), synth.standard_normal(rng, (64, 64)))
+    pop = synth.lens_population(rng, n_sample)
+    lams = synth.lambda_grid(N_LAM)
+    t0 = time.perf_counter()
+    done = 0
+    for lens in pop:
+        eval_candidate(prob, lens, lams)
+        done += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return done / dt, done, dt
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.f.flush()
+        rows = [l.split(",") for l in open(self.f.name).read().strip().splitlines() if l.strip()]
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        loaded = [s for s in sm if smax and s > 0.5 * max(smax)] or sm
+        return {"sm_mhz": statistics.median(loaded) if loaded else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        return json.load(open(p)), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def flops_per_item(geom, iters):
+    """Algorithmic FLOPs of one CGLS item: iters x F_it + one chi2 forward pass.
+
+    F_it = 4 K^2 N_pix (B and B^T) + 16 N_pix (L, L^T) + 20 N_s (Laplacian
+    H^T H) + 12 N_s (vector updates and dots)."""
+    npix, ns, k = geom.nx * geom.ny, geom.ns, geom.kpsf
+    f_it = 4 * k * k * npix + 16 * npix + 20 * ns + 12 * ns
+    return iters * f_it + (2 * k * k * npix + 6 * npix)
+
+
+def run_reference(args):
+    rank, world = _dist()
+    if rank != 0:
+        return 0
+    per_step = max(2, int(os.environ.get("MIRAGE_REF_SAMPLE", "4")))
+    vals = []
+    for s in range(args.warmup + args.steps):
+        v, done, dt = oracle_evals_per_s(per_step, seed=s, budget_s=60.0)
+        if s >= args.warmup:
+            vals.append((v, done, dt))
+    tot_done = sum(d for _, d, _ in vals)
+    tot_t = sum(t for _, _, t in vals)
+    value = tot_done / tot_t
+    cores = _cpu_threads()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": CONFIG,
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{per_step} candidates x {N_LAM} lambdas per step (dense Cholesky)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    rank, world = _dist()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1101_5803_gb300 import binding
+    from paper_1101_5803_gb300.problems import ga64_workload
+
+    ctx = binding.Context(local, binding.MIRAGE_FP32)
+    wl = ga64_workload(ctx, N_CAND, N_LAM, seed=1000 + rank)
+    probs = [wl.problem]
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    st = torch.cuda.current_stream()
+
+    def step(out=None, graph=True, timing=False):
+        return ctx.eval_batch(probs, wl.lens, wl.prob_idx, wl.lambdas, wl.n_lam, tol=TOL, use_graph=graph,
+                              out=out, want_kappa=True, phase_timing=timing)
+
+    # untimed: one phase-timed call for the kernel roofline, then graph warm-up
+    out = step(graph=False, timing=True)
+    torch.cuda.synchronize()
+    phase = ctx.phase_ms()
+    iters = out["iters"].cpu().numpy()
+    relres = out["relres"].cpu().numpy()
+    status = out["status"].cpu().numpy()
+    item_status = out["item_status"].cpu().numpy()
+    for _ in range(args.warmup):
+        out = step(out=out)
+    torch.cuda.synchronize()
+    launches_per_step = ctx.launches()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            ev[i][0].record(st)
+            out = step(out=out)
+            ev[i][1].record(st)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    times = [a.elapsed_time(b) for a, b in ev]
+    t_total = sum(times) / 1e3
+    t_max = t_total
+    if world > 1:
+        tt = torch.tensor([t_total], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    value = world * N_CAND * args.steps / t_max
+
+    # end to end through the C ABI with pinned host buffers
+    hp = binding.Problem(wl.geom, wl.problem.d.cpu().pin_memory(), wl.problem.sigma.cpu().pin_memory(),
+                         wl.problem.mask.cpu().pin_memory(), wl.problem.psf.cpu().pin_memory())
+    hl = wl.lens.cpu().pin_memory()
+    hlam = wl.lambdas.cpu().pin_memory()
+    hout = ctx.eval_batch([hp], hl, wl.prob_idx, hlam, wl.n_lam, tol=TOL)
+    e2e_steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        hout = ctx.eval_batch([hp], hl, wl.prob_idx, hlam, wl.n_lam, tol=TOL, out=hout)
+    t_e2e = (time.perf_counter() - t0) / e2e_steps
+    h2d = sum(t.numel() * t.element_size() for t in (hp.d, hp.sigma, hp.mask, hp.psf, hl, hlam))
+    d2h = sum(t.numel() * t.element_size() for t in hout.values())
+
+    # plain evaluator (one candidate per launch sequence) on a sample
+    n_plain = int(os.environ.get("MIRAGE_PLAIN_SAMPLE", "32"))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    pout = ctx.eval_batch(probs, wl.lens[:n_plain].contiguous(), wl.prob_idx[:n_plain],
+                          wl.lambdas[:n_plain].contiguous(), wl.n_lam[:n_plain], tol=TOL,
+                          mode=binding.MIRAGE_MODE_PLAIN)
+    torch.cuda.synchronize()
+    plain = n_plain / (time.perf_counter() - t0)
+    same = bool(torch.equal(pout["chi2"], out["chi2"][:n_plain]))
+
+    # roofline of the CGLS kernel: algorithmic FLOPs / its event-timed duration
+    flops = float(sum(flops_per_item(wl.geom, int(i)) for i in iters.ravel()))
+    t_cgls = phase[1] / 1e3
+    peaks, src = measured_peaks()
+    nsm = torch.cuda.get_device_properties(local).multi_processor_count
+    smax = float(peaks.get("sm_max_mhz", 2070.0))
+    peak = nsm * 128 * 2 * smax * 1e6 / 1e12
+    achieved = flops / t_cgls / 1e12
+    clocks = clk.summary()
+    at_clock = None
+    if clocks.get("sm_mhz"):
+        at_clock = nsm * 128 * 2 * clocks["sm_mhz"] * 1e6 / 1e12
+
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", "cgls_ga64_traffic.json")
+    if os.path.exists(tfile):
+        try:
+            traffic = json.load(open(tfile)).get("bytes_per_launch")
+        except Exception:
+            traffic = None
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        v, done, dt = oracle_evals_per_s(64, seed=7, budget_s=float(os.environ.get("MIRAGE_CPU_BUDGET", "20")))
+        cpu = {"value": v, "unit": UNIT, "cores": _cpu_threads(), "kind": "oracle",
+               "sample": f"{done} candidates x {N_LAM} lambdas of the same workload in {dt:.1f} s "
+                         f"(dense Cholesky FP64)"}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 (f64 reductions)", "data": "synthetic",
+            "config": dict(CONFIG, parallelism=f"replicas{world}" if world > 1 else "single"),
+            "e2e": {"value": N_CAND / t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h)},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "peak_basis": f"FP32 FFMA: {nsm} SMs x 128 lanes x 2 x {smax:.0f} MHz ({src} max clock)",
+                         "frac_at_measured_clock": (achieved / at_clock) if at_clock else None,
+                         "kernel": "k_cgls<float,9,smem>", "kernel_ms": phase[1],
+                         "flops_per_launch": flops},
+            "cpu_baseline": cpu,
+            "plain": {"value": plain, "unit": UNIT, "sample": n_plain, "speedup_batched_vs_plain": value / plain,
+                      "chi2_identical": same},
+            "gpu_launches": int(launches_per_step * args.steps),
+            "clocks": clocks,
+            "cg": {"iters_mean_per_item": float(iters.mean()), "iters_max": int(iters.max()),
+                   "relres_true_max": float(relres.max()), "relres_true_median": float(np.median(relres)),
+                   "items_converged_frac": float(((item_status & 7) == 0).mean()),
+                   "status_bits_any": int(np.bitwise_or.reduce(status))},
+            "phase_ms": {"raytrace": phase[0], "cgls": phase[1], "finalize": phase[2]}}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,188 @@
+/*
+ * mirage.h -- C ABI of the GB300 lens-inversion inner loop.
+ *
+ * For each candidate lens (SIE plus external shear) the library ray-traces
+ * the image pixels to the source plane (Eq. thinlens, Eqs. SIEX/SIEY),
+ * forms the bilinear lens operator L implicitly (Section 2.2), blurs with
+ * the PSF B by direct zero-padded convolution (the operator the paper
+ * applies by FFT, Section 2.2), and solves the regularised normal equations
+ *     (L^T B^T W B L + lambda H^T H) s = L^T B^T W d        (Eqs. eqLS, TKReg)
+ * with W = diag(m / sigma^2), m = mask AND mapped, by matrix-free conjugate
+ * gradient for least squares (CGLS, Section 2.2 and 2.4) over a grid of
+ * lambda values, then picks the L-curve corner by maximum curvature of
+ * natural cubic splines in chord length (Section 2.6).  Neither L nor B is
+ * ever assembled.
+ *
+ * Conventions shared by every entry point:
+ *  - Images are row-major [ny][nx] with x the fast axis; pixel (i, j) has
+ *    centre (cx + (i - (nx-1)/2) pix, cy + (j - (ny-1)/2) pix).
+ *  - The source grid [sy][sx] spans the edges [sxmin, sxmax] x [symin, symax];
+ *    its pixel centres lie half a cell inside.  A ray is mapped when it lies
+ *    in the rectangle of the first and last source-pixel centres.
+ *  - Lens vectors are 7 doubles (b, q, phi, x0, y0, gamma, theta_g): Einstein
+ *    radius b >= 0, axis ratio 0 < q <= 1, major-axis angle phi (rad), lens
+ *    centre, external shear gamma at angle theta_g about the lens centre.
+ *  - "real" is float in MIRAGE_FP32 contexts and double in MIRAGE_FP64
+ *    contexts.  FP32 contexts do the ray trace, interpolation, convolution and
+ *    CG vectors in float and every inner product, norm, chi^2 and curvature
+ *    in double; FP64 contexts do everything in double.
+ *  - Unless a call says otherwise, array arguments are device pointers owned
+ *    by the caller.  Calls are asynchronous on `stream` (a cudaStream_t, NULL
+ *    = legacy default stream) unless MIRAGE_MEM_HOST is requested.
+ *  - Return value: MIRAGE_OK or a negative MIRAGE_ERR_* code.  A bad
+ *    candidate never fails a batch: it gets a status flag instead.
+ *  - A context is not thread-safe: serialise calls that share one.
+ */
+#ifndef MIRAGE_H
+#define MIRAGE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MIRAGE_OK 0
+#define MIRAGE_ERR_ARG (-1)         /* invalid argument (sizes, null pointers, geometry) */
+#define MIRAGE_ERR_CUDA (-2)        /* a CUDA runtime call failed */
+#define MIRAGE_ERR_NOMEM (-3)       /* device allocation of context scratch failed */
+#define MIRAGE_ERR_UNSUPPORTED (-4) /* shape outside what this build supports */
+
+#define MIRAGE_FP32 0
+#define MIRAGE_FP64 1
+
+#define MIRAGE_REG_IDENTITY 0  /* H = I (zeroth order, Section 2.1) */
+#define MIRAGE_REG_GRADIENT 1  /* H = [Dx; Dy], forward differences, zero beyond the grid */
+#define MIRAGE_REG_LAPLACIAN 2 /* H = 5-point Laplacian, zero beyond the grid */
+
+/* per-(candidate, lambda) and per-candidate status bits */
+#define MIRAGE_ST_MAXIT 1        /* CG stopped at maxit above the tolerance */
+#define MIRAGE_ST_STAGNATION 2   /* CG residual stopped decreasing above the tolerance */
+#define MIRAGE_ST_BREAKDOWN 4    /* p^T A p <= 0 or not finite */
+#define MIRAGE_ST_BAD_PARAM 8    /* lens vector not finite, b < 0 or q outside (0, 1] */
+#define MIRAGE_ST_EMPTY_MAP 16   /* no pixel is both masked in and mapped */
+#define MIRAGE_ST_LCURVE_FLAT 32 /* fewer than 3 distinct L-curve points or zero curvature */
+
+#define MIRAGE_MEM_DEVICE 0 /* all arrays of the call are device memory */
+#define MIRAGE_MEM_HOST 1   /* all arrays of the call are host memory; the call
+                               stages them and returns after the results are back */
+
+#define MIRAGE_MODE_BATCHED 0 /* all (candidate, lambda) items in persistent launches */
+#define MIRAGE_MODE_PLAIN 1   /* one candidate per launch sequence, its lambdas in parallel */
+
+typedef struct {
+    int nx, ny;           /* image size in pixels (>= 1) */
+    double pix;           /* pixel size (arcsec, > 0) */
+    double cx, cy;        /* image centre (arcsec) */
+    int sx, sy;           /* source grid size (>= 2 each) */
+    double sxmin, sxmax;  /* source grid edges on x (sxmax > sxmin) */
+    double symin, symax;  /* source grid edges on y */
+    int kpsf;             /* PSF side, odd, 1 <= kpsf <= 31 */
+    int subpix;           /* n: each pixel traced as n x n sub-pixels (1 <= n <= 8) */
+    int reg;              /* MIRAGE_REG_* */
+} mirage_geom_t;
+
+typedef struct {
+    mirage_geom_t geom;          /* host struct */
+    const void* d;               /* [ny*nx] real: observed image */
+    const void* sigma;           /* [ny*nx] real: noise sigma, > 0 where mask != 0 */
+    const uint8_t* mask;         /* [ny*nx]: nonzero = pixel used in chi^2 and the solve */
+    const void* psf;             /* [kpsf*kpsf] real, row-major, centre at (k-1)/2 */
+} mirage_problem_t;
+
+typedef struct {
+    double tol;        /* stop when ||rhs - A s|| <= tol ||rhs|| (recursive residual) */
+    int maxit;         /* CG iteration cap per (candidate, lambda); <= 0: 10 * ns */
+    int mode;          /* MIRAGE_MODE_* */
+    int mem;           /* MIRAGE_MEM_* */
+    int use_graph;     /* 1: capture the batched launch sequence once per argument
+                          set and replay it on identical calls */
+    int threads;       /* 0 = default; < 0 = record per-phase CUDA events on the
+                          stream (non-graph batched calls) for mirage_last_phase_ms */
+    int replace_every; /* true-residual replacement period in iterations; 0 = 50 */
+} mirage_opts_t;
+
+typedef struct mirage_ctx mirage_ctx_t;
+
+/* Create a context on CUDA device `device` with MIRAGE_FP32 or MIRAGE_FP64
+ * arithmetic.  The context owns its scratch memory (grown on demand) and
+ * its captured graphs; *ctx is NULL on failure. */
+int mirage_create(mirage_ctx_t** ctx, int device, int precision);
+
+/* Release every resource of the context.  NULL is accepted. */
+int mirage_destroy(mirage_ctx_t* ctx);
+
+/* Evaluate n_cand candidate lenses (the inner loop of Section 3: ray trace,
+ * CGLS on Eq. TKReg for every lambda of the candidate, L-curve corner).
+ *
+ *  probs[n_probs]      host array of problem descriptors (device data pointers)
+ *  lens[n_cand*7]      lens vectors (double)
+ *  prob_idx[n_cand]    HOST array: problem of each candidate, in [0, n_probs)
+ *  lambdas[n_cand*max_lam]  lambda grid per candidate (double, > 0, ascending)
+ *  n_lam[n_cand]       HOST array: lambdas used per candidate, 1..max_lam
+ *  warm_x              nullable [n_cand*max_lam*max_ns] real: CG start per
+ *                      item (max_ns = the largest sx*sy of the problems);
+ *                      NULL = start from zero (the paper's blank source)
+ * Outputs ([n_cand*max_lam] unless noted; entries beyond n_lam untouched):
+ *  chi2, reg           double: Eq. chi2 of the solution and ||H s||^2
+ *  iters               int: CG iterations used
+ *  relres              double: TRUE ||rhs - A s|| / ||rhs|| at exit (nullable)
+ *  item_status         int: MIRAGE_ST_* bits per item (nullable)
+ *  corner[n_cand]      int: L-curve corner index (the fitness is chi2 there)
+ *  kappa               double: curvature at each knot (nullable)
+ *  s_out               nullable [n_cand*max_ns] real: solution at the corner
+ *  all_x               nullable [n_cand*max_lam*max_ns] real: every solution
+ *  status[n_cand]      int: OR of the candidate's item bits and its own
+ * With opts->mem == MIRAGE_MEM_HOST every array above (and the problem data)
+ * is host memory instead, and the call blocks until the outputs are written.
+ */
+int mirage_eval_batch(mirage_ctx_t* ctx, const mirage_problem_t* probs, int n_probs,
+                      const double* lens, const int* prob_idx, int n_cand,
+                      const double* lambdas, const int* n_lam, int max_lam,
+                      const mirage_opts_t* opts, const void* warm_x,
+                      double* chi2, double* reg, int* iters, double* relres, int* item_status,
+                      int* corner, double* kappa, void* s_out, void* all_x, int* status,
+                      void* stream);
+
+/* L-curve corner (Section 2.6) for n_cand curves of n_lam[c] points each:
+ * points (log10 reg, log10 chi2) in lambda order, chord-length parameter,
+ * natural cubic splines, curvature |x'y'' - y'x''| / (x'^2 + y'^2)^1.5 at
+ * the knots, argmax (ties to the smaller index).  Points within 1e-12 of
+ * the total chord length of their predecessor are merged (kappa 0); with
+ * fewer than 3 distinct points or kappa * chord length <= 1e-9 everywhere
+ * the middle index is returned with MIRAGE_ST_LCURVE_FLAT.
+ *  chi2, reg [n_cand*max_lam] double, n_lam [n_cand] int (all device)
+ *  corner [n_cand] int, kappa [n_cand*max_lam] double (nullable),
+ *  flags [n_cand] int (nullable; receives MIRAGE_ST_LCURVE_FLAT or 0). */
+int mirage_lcurve(const double* chi2, const double* reg, const int* n_lam, int n_cand, int max_lam,
+                  int* corner, double* kappa, int* flags, void* stream);
+
+/* Forward model and chi^2 of n_src source vectors at one lens (the forward
+ * pass of Eq. mapping and Eq. chi2, used by the positivity refinement stage
+ * of Section 3.2):  model_k = B L s_k,  chi2_k = sum_j m_j (model_k - d)_j^2 / sigma_j^2.
+ *  prob      host descriptor (device data)
+ *  lens[7]   device double
+ *  s         [n_src*ns] real (device)
+ *  model     nullable [n_src*npix] real (device)
+ *  chi2      [n_src] double (device)
+ *  status    nullable [1] int (device): MIRAGE_ST_BAD_PARAM / EMPTY_MAP bits */
+int mirage_forward(mirage_ctx_t* ctx, const mirage_problem_t* prob, const double* lens,
+                   const void* s, int n_src, void* model, double* chi2, int* status, void* stream);
+
+/* Number of kernel launches the last eval/forward call of this context
+ * issued (a replayed graph counts its kernels). */
+int mirage_last_launch_count(const mirage_ctx_t* ctx);
+
+/* Device time (ms) of the three phases of the last batched, non-graph call
+ * made with opts->threads < 0: ms[0] ray trace, ms[1] CGLS items, ms[2]
+ * L-curve/finalize.  Waits for those events. */
+int mirage_last_phase_ms(mirage_ctx_t* ctx, double* ms);
+
+/* Text of the last error raised on the calling thread ("" if none). */
+const char* mirage_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MIRAGE_H */

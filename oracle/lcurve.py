@@ -59,7 +59,10 @@ def lcurve_corner(chi2, reg):
     sy = CubicSpline(t, ys, bc_type="natural")
     x1, x2 = sx(t, 1), sx(t, 2)
     y1, y2 = sy(t, 1), sy(t, 2)
-    k = np.abs(x1 * y2 - y1 * x2) / np.power(x1 * x1 + y1 * y1, 1.5)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        k = np.abs(x1 * y2 - y1 * x2) / np.power(x1 * x1 + y1 * y1, 1.5)
+    # a knot where the spline's tangent vanishes has no defined curvature
+    k = np.where(np.isfinite(k), k, 0.0)
     # natural end conditions: the second derivatives vanish at the end knots
     k[0] = 0.0
     k[-1] = 0.0

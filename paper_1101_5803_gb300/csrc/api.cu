@@ -1,0 +1,830 @@
+// C ABI of the lens-inversion inner loop: context, argument checks, scratch
+// management, work-item planning, launches and CUDA-graph replay.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/mirage.h"
+#include "kernels.cuh"
+#include "table.h"
+
+using namespace mirage;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+void set_error(const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+}
+
+#define CK(call)                                                                        \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess) {                                                        \
+            set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
+                      __LINE__);                                                        \
+            return e_ == cudaErrorMemoryAllocation ? MIRAGE_ERR_NOMEM : MIRAGE_ERR_CUDA; \
+        }                                                                               \
+    } while (0)
+
+const KernelTable& table() {
+    static KernelTable t = [] {
+        KernelTable k;
+        std::memset(&k, 0, sizeof(k));
+        fill_f32_k5(k);
+        fill_f32_k7(k);
+        fill_f32_k9(k);
+        fill_f32_k11(k);
+        fill_f32_k15(k);
+        fill_f32_k21(k);
+        fill_f32_gen(k);
+        fill_f64(k);
+        return k;
+    }();
+    return t;
+}
+
+// grow-only device buffer owned by the context
+struct DevBuf {
+    void* p = nullptr;
+    size_t n = 0;
+    int ensure(size_t bytes) {
+        if (bytes <= n) return MIRAGE_OK;
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+        size_t want = std::max<size_t>(bytes, 256);
+        cudaError_t e = cudaMalloc(&p, want);
+        if (e != cudaSuccess) {
+            set_error("cudaMalloc(%zu) failed: %s", want, cudaGetErrorString(e));
+            p = nullptr;
+            return MIRAGE_ERR_NOMEM;
+        }
+        n = want;
+        return MIRAGE_OK;
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+    template <typename U>
+    U* as() const {
+        return reinterpret_cast<U*>(p);
+    }
+};
+
+struct GraphEntry {
+    cudaGraphExec_t exec = nullptr;
+    int launches = 0;
+    DevBuf probs, meta;  // this graph's own copy of the launch metadata
+};
+
+}  // namespace
+
+struct mirage_ctx {
+    int device = 0;
+    int precision = MIRAGE_FP32;
+    int sm_count = 0;
+    int max_smem = 0;
+    int last_launches = 0;
+    // scratch
+    DevBuf E, Etmp, inv, cst, swp, bwp, nent, cstat, X, istat, slab, probs, cand_prob, items, counters;
+    DevBuf stage;  // MIRAGE_MEM_HOST staging
+    DevBuf fE, fEtmp, finv, fcst, fswp, fbwp, fnent, fcstat, fslab, fprob, fcand;
+    std::map<std::string, GraphEntry> graphs;
+    std::map<const void*, int> smem_set;  // kernel -> dynamic smem attribute set
+    cudaStream_t cap_stream = nullptr;   // graphs are captured here and launched on the caller's stream
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // phase timing (opts.threads < 0)
+    int timed = 0;
+    std::vector<void*> scratch_seen;     // scratch pointers the cached graphs were captured with
+};
+
+namespace {
+void drop_graphs(mirage_ctx* ctx) {
+    for (auto& kv : ctx->graphs) {
+        if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+        kv.second.probs.release();
+        kv.second.meta.release();
+    }
+    ctx->graphs.clear();
+}
+}  // namespace
+
+namespace {
+
+template <typename T>
+constexpr int prec_of() {
+    return sizeof(T) == 4 ? 0 : 1;
+}
+
+int check_geom(const mirage_geom_t& g) {
+    if (g.nx < 1 || g.ny < 1 || g.nx > 4096 || g.ny > 4096) return MIRAGE_ERR_ARG;
+    if (g.sx < 2 || g.sy < 2 || (long long)g.sx * g.sy > (1 << 20)) return MIRAGE_ERR_ARG;
+    if (!(g.pix > 0) || !(g.sxmax > g.sxmin) || !(g.symax > g.symin)) return MIRAGE_ERR_ARG;
+    if (g.kpsf < 1 || g.kpsf > 31 || (g.kpsf % 2) == 0) return MIRAGE_ERR_ARG;
+    if (g.subpix < 1 || g.subpix > 8) return MIRAGE_ERR_ARG;
+    if (g.reg < 0 || g.reg > 2) return MIRAGE_ERR_ARG;
+    if (!std::isfinite(g.cx) || !std::isfinite(g.cy)) return MIRAGE_ERR_ARG;
+    return MIRAGE_OK;
+}
+
+template <typename T>
+Prob<T> make_prob(const mirage_problem_t& mp, const void* d, const void* sigma, const void* mask, const void* psf) {
+    const mirage_geom_t& g = mp.geom;
+    Prob<T> P;
+    std::memset(&P, 0, sizeof(P));
+    P.nx = g.nx;
+    P.ny = g.ny;
+    P.npix = g.nx * g.ny;
+    P.sx = g.sx;
+    P.sy = g.sy;
+    P.ns = g.sx * g.sy;
+    P.reg = g.reg;
+    P.nreg = g.reg == MIRAGE_REG_GRADIENT ? 2 * P.ns : P.ns;
+    P.K = g.kpsf;
+    P.hk = (g.kpsf - 1) / 2;
+    P.kp = (g.kpsf + 3) & ~3;
+    P.n_sub = g.subpix;
+    P.Np = g.subpix * g.subpix;
+    P.nrays = P.npix * P.Np;
+    P.ncx = g.sx - 1;
+    P.ncells = (g.sx - 1) * (g.sy - 1);
+    P.tiles_x = (g.nx + TILE - 1) / TILE;
+    P.tiles_y = (g.ny + TILE - 1) / TILE;
+    P.ntiles = P.tiles_x * P.tiles_y;
+    const int VW = 16 / (int)sizeof(T);
+    const int nvw = (TILE + g.kpsf - 1 + VW - 1) / VW * VW;
+    P.Wp = (P.tiles_x - 1) * TILE + nvw;
+    P.Hp = P.tiles_y * TILE + g.kpsf - 1;
+    P.plen = P.Wp * P.Hp;
+    P.pix = (T)g.pix;
+    P.cx = (T)g.cx;
+    P.cy = (T)g.cy;
+    P.sub0 = (T)((0.5 / g.subpix - 0.5) * g.pix);
+    P.subd = (T)(g.pix / g.subpix);
+    const double hx = (g.sxmax - g.sxmin) / g.sx, hy = (g.symax - g.symin) / g.sy;
+    P.c0x = (T)(g.sxmin + 0.5 * hx);
+    P.c0y = (T)(g.symin + 0.5 * hy);
+    P.inv_hx = (T)(1.0 / hx);
+    P.inv_hy = (T)(1.0 / hy);
+    P.invNp = (T)(1.0 / P.Np);
+    P.d = reinterpret_cast<const T*>(d);
+    P.sigma = reinterpret_cast<const T*>(sigma);
+    P.mask = reinterpret_cast<const uint8_t*>(mask);
+    P.psf = reinterpret_cast<const T*>(psf);
+    return P;
+}
+
+int set_smem(mirage_ctx* ctx, const void* fn, size_t bytes) {
+    auto it = ctx->smem_set.find(fn);
+    if (it == ctx->smem_set.end()) {
+        cudaFuncAttributes fa;
+        CK(cudaFuncGetAttributes(&fa, fn));
+        const int dyn_max = ctx->max_smem - (int)fa.sharedSizeBytes;
+        CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max));
+        it = ctx->smem_set.emplace(fn, dyn_max).first;
+    }
+    if ((long long)bytes > it->second) {
+        set_error("work item needs %zu B of dynamic shared memory (limit %d)", bytes, it->second);
+        return MIRAGE_ERR_UNSUPPORTED;
+    }
+    return MIRAGE_OK;
+}
+
+const void* pick_cgls(int prec, bool big, int K) {
+    const KernelTable& t = table();
+    const void* f = t.cgls[prec][big][K];
+    return f ? f : t.cgls[prec][big][0];
+}
+
+const void* pick_fwd(int prec, int K) {
+    const KernelTable& t = table();
+    const void* f = t.fwd[prec][K];
+    return f ? f : t.fwd[prec][0];
+}
+
+template <typename T>
+void fill_scratch(CandScratch<T>& cs, mirage_ctx* ctx, bool fwd, long long sE, long long sInv, long long sCst,
+                  long long sPad) {
+    cs.E = (fwd ? ctx->fE : ctx->E).as<Entry<T>>();
+    cs.Etmp = (fwd ? ctx->fEtmp : ctx->Etmp).as<Entry<T>>();
+    cs.inv = (fwd ? ctx->finv : ctx->inv).as<int>();
+    cs.cst = (fwd ? ctx->fcst : ctx->cst).as<int>();
+    cs.swp = (fwd ? ctx->fswp : ctx->swp).as<T>();
+    cs.bwp = (fwd ? ctx->fbwp : ctx->bwp).as<T>();
+    cs.nent = (fwd ? ctx->fnent : ctx->nent).as<int>();
+    cs.cstat = (fwd ? ctx->fcstat : ctx->cstat).as<int>();
+    cs.sE = sE;
+    cs.sInv = sInv;
+    cs.sCst = sCst;
+    cs.sPad = sPad;
+}
+
+int launch(mirage_ctx* ctx, const void* fn, dim3 grid, dim3 block, void** args, size_t smem, cudaStream_t st) {
+    CK(cudaLaunchKernel(fn, grid, block, args, smem, st));
+    ctx->last_launches++;
+    return MIRAGE_OK;
+}
+
+#define TRY(x)                      \
+    do {                            \
+        int r_ = (x);               \
+        if (r_ != MIRAGE_OK) return r_; \
+    } while (0)
+
+// staging of host arrays into one device block (MIRAGE_MEM_HOST)
+struct Stager {
+    std::vector<std::pair<size_t, std::pair<const void*, size_t>>> in;  // offset, (host ptr, bytes)
+    std::vector<std::pair<size_t, std::pair<void*, size_t>>> out;
+    size_t total = 0;
+    size_t add_in(const void* h, size_t bytes) {
+        const size_t o = total;
+        total += (bytes + 255) / 256 * 256;
+        if (h && bytes) in.push_back({o, {h, bytes}});
+        return o;
+    }
+    size_t add_out(void* h, size_t bytes) {
+        const size_t o = total;
+        total += (bytes + 255) / 256 * 256;
+        if (h && bytes) out.push_back({o, {h, bytes}});
+        return o;
+    }
+};
+
+template <typename T>
+int eval_impl(mirage_ctx* ctx, const mirage_problem_t* probs, int n_probs, const double* lens, const int* prob_idx,
+              int n_cand, const double* lambdas, const int* n_lam, int max_lam, const mirage_opts_t* opts,
+              const void* warm_x, double* chi2, double* reg, int* iters, double* relres, int* item_status,
+              int* corner, double* kappa, void* s_out, void* all_x, int* status, cudaStream_t st) {
+    constexpr int prec = prec_of<T>();
+    ctx->last_launches = 0;
+    if (n_cand == 0) return MIRAGE_OK;
+    if (!probs || n_probs < 1 || !lens || !prob_idx || !lambdas || !n_lam || !chi2 || !reg || !iters || !corner ||
+        !status || max_lam < 1 || max_lam > MAX_LAM || n_cand < 0) {
+        set_error("eval_batch: null pointer or size out of range");
+        return MIRAGE_ERR_ARG;
+    }
+    const mirage_opts_t o = *opts;
+    if (!(o.tol >= 0) || o.mode < 0 || o.mode > 1 || o.mem < 0 || o.mem > 1) {
+        set_error("eval_batch: bad options");
+        return MIRAGE_ERR_ARG;
+    }
+    for (int p = 0; p < n_probs; ++p) {
+        if (check_geom(probs[p].geom) != MIRAGE_OK) {
+            set_error("eval_batch: bad geometry of problem %d", p);
+            return MIRAGE_ERR_ARG;
+        }
+        if (!probs[p].d || !probs[p].sigma || !probs[p].mask || !probs[p].psf) {
+            set_error("eval_batch: null data pointer in problem %d", p);
+            return MIRAGE_ERR_ARG;
+        }
+    }
+    for (int c = 0; c < n_cand; ++c) {
+        if (prob_idx[c] < 0 || prob_idx[c] >= n_probs || n_lam[c] < 1 || n_lam[c] > max_lam) {
+            set_error("eval_batch: bad prob_idx / n_lam of candidate %d", c);
+            return MIRAGE_ERR_ARG;
+        }
+    }
+    const bool host = o.mem == MIRAGE_MEM_HOST;
+
+    // sizes over the problems
+    std::vector<Prob<T>> hp(n_probs);
+    long long max_rays = 0, max_cells = 0, max_plen = 0, max_ns = 0;
+    for (int p = 0; p < n_probs; ++p) {
+        hp[p] = make_prob<T>(probs[p], probs[p].d, probs[p].sigma, probs[p].mask, probs[p].psf);
+        max_rays = std::max<long long>(max_rays, hp[p].nrays);
+        max_cells = std::max<long long>(max_cells, hp[p].ncells);
+        max_plen = std::max<long long>(max_plen, hp[p].plen);
+        max_ns = std::max<long long>(max_ns, hp[p].ns);
+    }
+    if ((long long)max_cells * 4 > ctx->max_smem - 2048) {
+        set_error("source grid too large for the ray-trace kernel");
+        return MIRAGE_ERR_UNSUPPORTED;
+    }
+    const long long sE = max_rays, sInv = max_rays, sCst = (max_cells + 1 + 3) / 4 * 4, sPad = (max_plen + 3) / 4 * 4;
+    const long long nitems_all = (long long)n_cand * max_lam;
+
+    // host staging: every array of the call goes through one device block
+    const double* d_lens = lens;
+    const double* d_lambdas = lambdas;
+    const T* d_warm = reinterpret_cast<const T*>(warm_x);
+    double *d_chi2 = chi2, *d_reg = reg, *d_relres = relres, *d_kappa = kappa;
+    int *d_iters = iters, *d_istat = item_status, *d_corner = corner, *d_status = status;
+    T *d_sout = reinterpret_cast<T*>(s_out), *d_allx = reinterpret_cast<T*>(all_x);
+    if (host) {
+        Stager sg;
+        std::vector<size_t> po(4 * n_probs);
+        for (int p = 0; p < n_probs; ++p) {
+            const mirage_geom_t& g = probs[p].geom;
+            const size_t np = (size_t)g.nx * g.ny;
+            po[4 * p + 0] = sg.add_in(probs[p].d, np * sizeof(T));
+            po[4 * p + 1] = sg.add_in(probs[p].sigma, np * sizeof(T));
+            po[4 * p + 2] = sg.add_in(probs[p].mask, np);
+            po[4 * p + 3] = sg.add_in(probs[p].psf, (size_t)g.kpsf * g.kpsf * sizeof(T));
+        }
+        const size_t o_lens = sg.add_in(lens, sizeof(double) * 7 * n_cand);
+        const size_t o_lam = sg.add_in(lambdas, sizeof(double) * max_lam * n_cand);
+        const size_t o_warm = sg.add_in(warm_x, warm_x ? sizeof(T) * nitems_all * max_ns : 0);
+        const size_t o_chi2 = sg.add_out(chi2, sizeof(double) * nitems_all);
+        const size_t o_reg = sg.add_out(reg, sizeof(double) * nitems_all);
+        const size_t o_it = sg.add_out(iters, sizeof(int) * nitems_all);
+        const size_t o_rr = sg.add_out(relres, relres ? sizeof(double) * nitems_all : 0);
+        const size_t o_is = sg.add_out(item_status, item_status ? sizeof(int) * nitems_all : 0);
+        const size_t o_cn = sg.add_out(corner, sizeof(int) * n_cand);
+        const size_t o_kp = sg.add_out(kappa, kappa ? sizeof(double) * nitems_all : 0);
+        const size_t o_so = sg.add_out(s_out, s_out ? sizeof(T) * n_cand * max_ns : 0);
+        const size_t o_ax = sg.add_out(all_x, all_x ? sizeof(T) * nitems_all * max_ns : 0);
+        const size_t o_st = sg.add_out(status, sizeof(int) * n_cand);
+        TRY(ctx->stage.ensure(sg.total));
+        char* base = ctx->stage.as<char>();
+        for (auto& e : sg.in) CK(cudaMemcpyAsync(base + e.first, e.second.first, e.second.second, cudaMemcpyHostToDevice, st));
+        for (int p = 0; p < n_probs; ++p)
+            hp[p] = make_prob<T>(probs[p], base + po[4 * p], base + po[4 * p + 1], base + po[4 * p + 2],
+                                 base + po[4 * p + 3]);
+        d_lens = reinterpret_cast<const double*>(base + o_lens);
+        d_lambdas = reinterpret_cast<const double*>(base + o_lam);
+        d_warm = warm_x ? reinterpret_cast<const T*>(base + o_warm) : nullptr;
+        d_chi2 = reinterpret_cast<double*>(base + o_chi2);
+        d_reg = reinterpret_cast<double*>(base + o_reg);
+        d_iters = reinterpret_cast<int*>(base + o_it);
+        d_relres = relres ? reinterpret_cast<double*>(base + o_rr) : nullptr;
+        d_istat = item_status ? reinterpret_cast<int*>(base + o_is) : nullptr;
+        d_corner = reinterpret_cast<int*>(base + o_cn);
+        d_kappa = kappa ? reinterpret_cast<double*>(base + o_kp) : nullptr;
+        d_sout = s_out ? reinterpret_cast<T*>(base + o_so) : nullptr;
+        d_allx = all_x ? reinterpret_cast<T*>(base + o_ax) : nullptr;
+        d_status = reinterpret_cast<int*>(base + o_st);
+        // run on device buffers, then copy back
+        mirage_opts_t o2 = o;
+        o2.mem = MIRAGE_MEM_DEVICE;
+        o2.use_graph = 0;
+        std::vector<mirage_problem_t> dp(probs, probs + n_probs);
+        for (int p = 0; p < n_probs; ++p) {
+            dp[p].d = base + po[4 * p];
+            dp[p].sigma = base + po[4 * p + 1];
+            dp[p].mask = reinterpret_cast<const uint8_t*>(base + po[4 * p + 2]);
+            dp[p].psf = base + po[4 * p + 3];
+        }
+        TRY(eval_impl<T>(ctx, dp.data(), n_probs, d_lens, prob_idx, n_cand, d_lambdas, n_lam, max_lam, &o2, d_warm,
+                         d_chi2, d_reg, d_iters, d_relres, d_istat, d_corner, d_kappa, d_sout, d_allx, d_status,
+                         st));
+        const int nl = ctx->last_launches;
+        for (auto& e : sg.out) CK(cudaMemcpyAsync(e.second.first, base + e.first, e.second.second, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        ctx->last_launches = nl;
+        return MIRAGE_OK;
+    }
+
+    // ---- device path
+    TRY(ctx->E.ensure(sizeof(Entry<T>) * n_cand * sE));
+    TRY(ctx->Etmp.ensure(sizeof(Entry<T>) * n_cand * sE));
+    TRY(ctx->inv.ensure(sizeof(int) * n_cand * sInv));
+    TRY(ctx->cst.ensure(sizeof(int) * n_cand * sCst));
+    TRY(ctx->swp.ensure(sizeof(T) * n_cand * sPad));
+    TRY(ctx->bwp.ensure(sizeof(T) * n_cand * sPad));
+    TRY(ctx->nent.ensure(sizeof(int) * n_cand));
+    TRY(ctx->cstat.ensure(sizeof(int) * n_cand));
+    if (!d_allx) TRY(ctx->X.ensure(sizeof(T) * nitems_all * max_ns));
+    if (!d_istat) TRY(ctx->istat.ensure(sizeof(int) * nitems_all));
+    T* dX = d_allx ? d_allx : ctx->X.as<T>();
+    int* dIst = d_istat ? d_istat : ctx->istat.as<int>();
+
+    // per-candidate kernel class and work items
+    std::vector<int> cls_of(n_probs);
+    struct Group {
+        const void* fn;
+        bool big;
+        size_t smem;
+        long long slab;
+        std::vector<std::pair<double, int>> items;  // (sort key, packed)
+    };
+    std::map<std::pair<const void*, int>, Group> groups;
+    std::vector<double> hlam;  // lambdas are device data: sort by index instead (ascending lambda = costlier)
+    for (int c = 0; c < n_cand; ++c) {
+        const Prob<T>& P = hp[prob_idx[c]];
+        const size_t sm = smem_bytes<T>(P, false);
+        const bool big = sm > (size_t)ctx->max_smem;
+        const void* fn = pick_cgls(prec, big, P.K);
+        if (!fn) {
+            set_error("no kernel for this PSF size");
+            return MIRAGE_ERR_UNSUPPORTED;
+        }
+        auto key = std::make_pair(fn, (int)big);
+        Group& g = groups[key];
+        g.fn = fn;
+        g.big = big;
+        g.smem = std::max(g.smem, smem_bytes<T>(P, big));
+        g.slab = std::max<long long>(g.slab, (long long)slab_elems<T>(P));
+        const double work = (double)P.plen * P.K * P.K + 8.0 * P.nrays;
+        for (int k = 0; k < n_lam[c]; ++k) {
+            // lambda grids ascend: smaller k = smaller lambda = more CG iterations
+            const double key2 = work * (double)(n_lam[c] - k + 4);
+            g.items.push_back({-key2, c * MAX_LAM + k});
+        }
+    }
+    std::vector<int> all_items;
+    std::vector<size_t> g_off;
+    std::vector<Group*> glist;
+    for (auto& kv : groups) {
+        Group& g = kv.second;
+        std::stable_sort(g.items.begin(), g.items.end(),
+                         [](const std::pair<double, int>& a, const std::pair<double, int>& b) { return a.first < b.first; });
+        g_off.push_back(all_items.size());
+        for (auto& it : g.items) all_items.push_back(it.second);
+        glist.push_back(&g);
+    }
+    // plain mode: one candidate per launch sequence, items grouped per candidate
+    std::vector<int> plain_items;
+    std::vector<int> plain_off(n_cand + 1, 0);
+    if (o.mode == MIRAGE_MODE_PLAIN) {
+        for (int c = 0; c < n_cand; ++c) {
+            plain_off[c] = (int)plain_items.size();
+            for (int k = n_lam[c] - 1 + 0; k >= 0; --k) plain_items.push_back(c * MAX_LAM + k);
+        }
+        plain_off[n_cand] = (int)plain_items.size();
+    }
+    const std::vector<int>& items_v = o.mode == MIRAGE_MODE_PLAIN ? plain_items : all_items;
+
+    const size_t n_counters = std::max<size_t>(glist.size(), (size_t)n_cand) + 1;
+    // device metadata block: cand_prob[n_cand] | n_lam[n_cand] | items[...]
+    std::vector<int> meta;
+    meta.reserve(2 * n_cand + items_v.size());
+    meta.insert(meta.end(), prob_idx, prob_idx + n_cand);
+    meta.insert(meta.end(), n_lam, n_lam + n_cand);
+    meta.insert(meta.end(), items_v.begin(), items_v.end());
+    TRY(ctx->counters.ensure(sizeof(int) * n_counters));
+    long long slab_stride = 0;
+    int nbig_grid = 0;
+    for (Group* g : glist)
+        if (g->big) {
+            slab_stride = std::max(slab_stride, (g->slab + 63) / 64 * 64);
+            nbig_grid = std::max<int>(nbig_grid, (int)std::min<long long>(ctx->sm_count, (long long)g->items.size()));
+        }
+    if (o.mode == MIRAGE_MODE_PLAIN && slab_stride) nbig_grid = std::max(nbig_grid, max_lam);
+    if (slab_stride) TRY(ctx->slab.ensure(sizeof(T) * slab_stride * std::max(nbig_grid, 1)));
+
+    // graph key: everything that shapes the launch sequence
+    std::string key;
+    const bool graph = o.use_graph && o.mode == MIRAGE_MODE_BATCHED;
+    if (graph) {
+        // a grown scratch buffer invalidates every captured graph
+        std::vector<void*> now = {ctx->E.p, ctx->Etmp.p, ctx->inv.p, ctx->cst.p, ctx->swp.p, ctx->bwp.p,
+                                  ctx->nent.p, ctx->cstat.p, ctx->X.p, ctx->istat.p, ctx->slab.p, ctx->counters.p};
+        if (now != ctx->scratch_seen) {
+            drop_graphs(ctx);
+            ctx->scratch_seen = now;
+        }
+        auto addb = [&](const void* p, size_t n) { key.append(reinterpret_cast<const char*>(p), n); };
+        addb(&n_cand, sizeof(n_cand));
+        addb(&max_lam, sizeof(max_lam));
+        addb(hp.data(), sizeof(Prob<T>) * hp.size());
+        addb(meta.data(), sizeof(int) * meta.size());
+        const void* ptrs[] = {d_lens, d_lambdas, d_warm, d_chi2, d_reg, d_relres, d_kappa, d_iters, d_istat,
+                              d_corner, d_status, d_sout, d_allx, st};
+        addb(ptrs, sizeof(ptrs));
+        addb(&o.tol, sizeof(o.tol));
+        addb(&o.maxit, sizeof(o.maxit));
+        addb(&o.replace_every, sizeof(o.replace_every));
+        auto it = ctx->graphs.find(key);
+        if (it != ctx->graphs.end()) {
+            CK(cudaGraphLaunch(it->second.exec, st));
+            ctx->last_launches = it->second.launches;
+            return MIRAGE_OK;
+        }
+        if (!ctx->cap_stream) CK(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+    }
+    GraphEntry ge;
+    DevBuf& probs_buf = graph ? ge.probs : ctx->probs;
+    DevBuf& meta_buf = graph ? ge.meta : ctx->items;
+    TRY(probs_buf.ensure(sizeof(Prob<T>) * n_probs));
+    TRY(meta_buf.ensure(sizeof(int) * meta.size()));
+
+    // uploads (before any capture)
+    CK(cudaMemcpyAsync(probs_buf.p, hp.data(), sizeof(Prob<T>) * n_probs, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(meta_buf.p, meta.data(), sizeof(int) * meta.size(), cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));  // the uploads' host buffers die with this call
+
+    CandScratch<T> cs;
+    fill_scratch<T>(cs, ctx, false, sE, sInv, sCst, sPad);
+    const Prob<T>* dprobs = probs_buf.as<Prob<T>>();
+    const int* dcand = meta_buf.as<int>();
+    const int* dnlam = dcand + n_cand;
+    const int* ditems = dcand + 2 * n_cand;
+    int* dcnt = ctx->counters.as<int>();
+    const KernelTable& tb = table();
+
+    for (Group* g : glist) TRY(set_smem(ctx, g->fn, g->smem));
+    TRY(set_smem(ctx, tb.raytrace[prec], (size_t)max_cells * 4));
+
+    CglsArgs<T> A;
+    std::memset(&A, 0, sizeof(A));
+    A.probs = dprobs;
+    A.cand_prob = dcand;
+    A.lens = d_lens;
+    A.lambdas = d_lambdas;
+    A.tol = o.tol;
+    A.maxit = o.maxit;
+    A.replace_every = o.replace_every;
+    A.max_lam = max_lam;
+    A.max_ns = (int)max_ns;
+    A.warm_x = d_warm;
+    A.cs = cs;
+    A.slab = ctx->slab.as<T>();
+    A.slab_stride = slab_stride;
+    A.X = dX;
+    A.chi2 = d_chi2;
+    A.reg = d_reg;
+    A.iters = d_iters;
+    A.relres = d_relres;
+    A.istat = dIst;
+
+    const cudaStream_t launch_st = st;
+    if (graph) {
+        st = ctx->cap_stream;
+        CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    }
+    int rc = MIRAGE_OK;
+    do {
+        const bool timing = !graph && o.threads < 0;
+        ctx->timed = 0;
+        if (timing && !ctx->ev[0])
+            for (int e = 0; e < 4; ++e) cudaEventCreate(&ctx->ev[e]);
+        if (o.mode == MIRAGE_MODE_BATCHED) {
+            if (timing) cudaEventRecord(ctx->ev[0], st);
+            // 1) ray trace every candidate
+            {
+                int cand0 = 0, nc = n_cand;
+                void* args[] = {(void*)&dprobs, (void*)&dcand, (void*)&d_lens, &cand0, &nc, &cs};
+                rc = launch(ctx, tb.raytrace[prec], dim3(n_cand), dim3(NTHREADS), args, (size_t)max_cells * 4, st);
+                if (rc) break;
+            }
+            // 2) CGLS items, one persistent launch per kernel class
+            if (cudaMemsetAsync(dcnt, 0, sizeof(int) * n_counters, st) != cudaSuccess) {
+                set_error("cudaMemsetAsync failed");
+                rc = MIRAGE_ERR_CUDA;
+                break;
+            }
+            if (timing) cudaEventRecord(ctx->ev[1], st);
+            for (size_t gi = 0; gi < glist.size() && !rc; ++gi) {
+                Group* g = glist[gi];
+                A.items = ditems + g_off[gi];
+                A.n_items = (int)g->items.size();
+                A.counter = dcnt + gi;
+                const int grid = (int)std::min<long long>(ctx->sm_count, (long long)g->items.size());
+                void* args[] = {&A};
+                rc = launch(ctx, g->fn, dim3(grid), dim3(NTHREADS), args, g->smem, st);
+            }
+            if (rc) break;
+            if (timing) cudaEventRecord(ctx->ev[2], st);
+            // 3) L-curve corner, status, s_out
+            {
+                int nc = n_cand, ml = max_lam, mns = (int)max_ns, c0 = 0;
+                const int* ist = dIst;
+                const int* cst = cs.cstat;
+                const T* Xc = dX;
+                void* args[] = {&c0, &nc, &ml, &mns, (void*)&dnlam, (void*)&dcand, (void*)&dprobs, (void*)&d_chi2,
+                                (void*)&d_reg, (void*)&ist, (void*)&cst, (void*)&Xc, &d_corner, &d_kappa, &d_sout,
+                                &d_status};
+                rc = launch(ctx, tb.finalize[prec], dim3(n_cand), dim3(128), args, 0, st);
+            }
+            if (timing) {
+                cudaEventRecord(ctx->ev[3], st);
+                ctx->timed = 1;
+            }
+        } else {
+            // plain: per candidate, ray trace (1 CTA), its lambdas (1 CTA each), finalize
+            if (cudaMemsetAsync(dcnt, 0, sizeof(int) * n_counters, st) != cudaSuccess) {
+                set_error("cudaMemsetAsync failed");
+                rc = MIRAGE_ERR_CUDA;
+                break;
+            }
+            for (int c = 0; c < n_cand && !rc; ++c) {
+                const Prob<T>& P = hp[prob_idx[c]];
+                const bool big = smem_bytes<T>(P, false) > (size_t)ctx->max_smem;
+                const void* fn = pick_cgls(prec, big, P.K);
+                TRY(set_smem(ctx, fn, smem_bytes<T>(P, big)));
+                int cand0 = c, nc = 1;
+                void* a1[] = {(void*)&dprobs, (void*)&dcand, (void*)&d_lens, &cand0, &nc, &cs};
+                rc = launch(ctx, tb.raytrace[prec], dim3(1), dim3(NTHREADS), a1, (size_t)max_cells * 4, st);
+                if (rc) break;
+                A.items = ditems + plain_off[c];
+                A.n_items = plain_off[c + 1] - plain_off[c];
+                A.counter = dcnt + c;
+                void* a2[] = {&A};
+                rc = launch(ctx, fn, dim3(A.n_items), dim3(NTHREADS), a2, smem_bytes<T>(P, big), st);
+                if (rc) break;
+                int ml = max_lam, mns = (int)max_ns;
+                const int* ist = dIst;
+                const int* cst = cs.cstat;
+                const T* Xc = dX;
+                void* a3[] = {&cand0, &nc, &ml, &mns, (void*)&dnlam, (void*)&dcand, (void*)&dprobs, (void*)&d_chi2,
+                              (void*)&d_reg, (void*)&ist, (void*)&cst, (void*)&Xc, &d_corner, &d_kappa, &d_sout,
+                              &d_status};
+                rc = launch(ctx, tb.finalize[prec], dim3(1), dim3(128), a3, 0, st);
+            }
+        }
+    } while (0);
+
+    if (graph) {
+        cudaGraph_t gr = nullptr;
+        cudaError_t e = cudaStreamEndCapture(st, &gr);
+        if (rc != MIRAGE_OK) {
+            if (gr) cudaGraphDestroy(gr);
+            ge.probs.release();
+            ge.meta.release();
+            return rc;
+        }
+        if (e != cudaSuccess) {
+            set_error("cudaStreamEndCapture failed: %s", cudaGetErrorString(e));
+            if (gr) cudaGraphDestroy(gr);
+            return MIRAGE_ERR_CUDA;
+        }
+        e = cudaGraphInstantiate(&ge.exec, gr, 0);
+        cudaGraphDestroy(gr);
+        if (e != cudaSuccess) {
+            set_error("cudaGraphInstantiate failed: %s", cudaGetErrorString(e));
+            ge.probs.release();
+            ge.meta.release();
+            return MIRAGE_ERR_CUDA;
+        }
+        ge.launches = ctx->last_launches;
+        GraphEntry& slot = ctx->graphs[key];
+        slot = ge;
+        ge.probs.p = nullptr;  // ownership moved to the cache entry
+        ge.meta.p = nullptr;
+        CK(cudaGraphLaunch(slot.exec, launch_st));
+    }
+    return rc;
+}
+
+template <typename T>
+int forward_impl(mirage_ctx* ctx, const mirage_problem_t* prob, const double* lens, const void* s, int n_src,
+                 void* model, double* chi2, int* status, cudaStream_t st) {
+    constexpr int prec = prec_of<T>();
+    ctx->last_launches = 0;
+    if (!prob || !lens || !s || !chi2 || n_src < 0) {
+        set_error("forward: null pointer");
+        return MIRAGE_ERR_ARG;
+    }
+    if (check_geom(prob->geom) != MIRAGE_OK || !prob->d || !prob->sigma || !prob->mask || !prob->psf) {
+        set_error("forward: bad problem");
+        return MIRAGE_ERR_ARG;
+    }
+    if (n_src == 0) return MIRAGE_OK;
+    Prob<T> P = make_prob<T>(*prob, prob->d, prob->sigma, prob->mask, prob->psf);
+    if ((long long)P.ncells * 4 > ctx->max_smem - 2048) {
+        set_error("source grid too large for the ray-trace kernel");
+        return MIRAGE_ERR_UNSUPPORTED;
+    }
+    const long long sE = P.nrays, sInv = P.nrays, sCst = (P.ncells + 1 + 3) / 4 * 4, sPad = (P.plen + 3) / 4 * 4;
+    TRY(ctx->fE.ensure(sizeof(Entry<T>) * sE));
+    TRY(ctx->fEtmp.ensure(sizeof(Entry<T>) * sE));
+    TRY(ctx->finv.ensure(sizeof(int) * sInv));
+    TRY(ctx->fcst.ensure(sizeof(int) * sCst));
+    TRY(ctx->fswp.ensure(sizeof(T) * sPad));
+    TRY(ctx->fbwp.ensure(sizeof(T) * sPad));
+    TRY(ctx->fnent.ensure(sizeof(int)));
+    TRY(ctx->fcstat.ensure(sizeof(int)));
+    TRY(ctx->fprob.ensure(sizeof(Prob<T>) + sizeof(int)));
+    const int grid = std::min(n_src, 2 * ctx->sm_count);
+    const long long stride = (P.plen + 63) / 64 * 64;
+    TRY(ctx->fslab.ensure(sizeof(T) * stride * grid));
+    std::vector<char> up(sizeof(Prob<T>) + sizeof(int), 0);
+    std::memcpy(up.data(), &P, sizeof(P));
+    CK(cudaMemcpyAsync(ctx->fprob.p, up.data(), up.size(), cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));
+    const Prob<T>* dprob = ctx->fprob.as<Prob<T>>();
+    const int* dcand = reinterpret_cast<const int*>(ctx->fprob.as<char>() + sizeof(Prob<T>));
+    CandScratch<T> cs;
+    fill_scratch<T>(cs, ctx, true, sE, sInv, sCst, sPad);
+    const KernelTable& tb = table();
+    TRY(set_smem(ctx, tb.raytrace[prec], (size_t)P.ncells * 4));
+    int cand0 = 0, nc = 1;
+    void* a1[] = {(void*)&dprob, (void*)&dcand, (void*)&lens, &cand0, &nc, &cs};
+    TRY(launch(ctx, tb.raytrace[prec], dim3(1), dim3(NTHREADS), a1, (size_t)P.ncells * 4, st));
+    const void* fn = pick_fwd(prec, P.K);
+    const size_t smem = align_up<T>(sizeof(T) * 2 * P.K * P.kp, 16) + 2 * 33 * sizeof(double) + 16;
+    TRY(set_smem(ctx, fn, smem));
+    const T* S = reinterpret_cast<const T*>(s);
+    T* M = reinterpret_cast<T*>(model);
+    T* slab = ctx->fslab.as<T>();
+    long long sstr = stride;
+    void* a2[] = {(void*)&dprob, &cs, (void*)&S, &n_src, &M, &chi2, &slab, &sstr, &status};
+    TRY(launch(ctx, fn, dim3(grid), dim3(NTHREADS), a2, smem, st));
+    return MIRAGE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mirage_create(mirage_ctx_t** out, int device, int precision) {
+    if (!out) return MIRAGE_ERR_ARG;
+    *out = nullptr;
+    if (precision != MIRAGE_FP32 && precision != MIRAGE_FP64) {
+        set_error("precision must be MIRAGE_FP32 or MIRAGE_FP64");
+        return MIRAGE_ERR_ARG;
+    }
+    CK(cudaSetDevice(device));
+    mirage_ctx* c = new mirage_ctx();
+    c->device = device;
+    c->precision = precision;
+    cudaError_t e1 = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
+    cudaError_t e2 = cudaDeviceGetAttribute(&c->max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    if (e1 != cudaSuccess || e2 != cudaSuccess) {
+        set_error("cudaDeviceGetAttribute failed");
+        delete c;
+        return MIRAGE_ERR_CUDA;
+    }
+    (void)table();
+    *out = c;
+    return MIRAGE_OK;
+}
+
+int mirage_destroy(mirage_ctx_t* ctx) {
+    if (!ctx) return MIRAGE_OK;
+    cudaSetDevice(ctx->device);
+    drop_graphs(ctx);
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+    for (int e = 0; e < 4; ++e)
+        if (ctx->ev[e]) cudaEventDestroy(ctx->ev[e]);
+    DevBuf* bufs[] = {&ctx->E, &ctx->Etmp, &ctx->inv, &ctx->cst, &ctx->swp, &ctx->bwp, &ctx->nent, &ctx->cstat,
+                      &ctx->X, &ctx->istat, &ctx->slab, &ctx->probs, &ctx->cand_prob, &ctx->items, &ctx->counters,
+                      &ctx->stage, &ctx->fE, &ctx->fEtmp, &ctx->finv, &ctx->fcst, &ctx->fswp, &ctx->fbwp,
+                      &ctx->fnent, &ctx->fcstat, &ctx->fslab, &ctx->fprob, &ctx->fcand};
+    for (DevBuf* b : bufs) b->release();
+    delete ctx;
+    return MIRAGE_OK;
+}
+
+int mirage_eval_batch(mirage_ctx_t* ctx, const mirage_problem_t* probs, int n_probs, const double* lens,
+                      const int* prob_idx, int n_cand, const double* lambdas, const int* n_lam, int max_lam,
+                      const mirage_opts_t* opts, const void* warm_x, double* chi2, double* reg, int* iters,
+                      double* relres, int* item_status, int* corner, double* kappa, void* s_out, void* all_x,
+                      int* status, void* stream) {
+    if (!ctx || !opts) return MIRAGE_ERR_ARG;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return MIRAGE_ERR_CUDA;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (ctx->precision == MIRAGE_FP32)
+        return eval_impl<float>(ctx, probs, n_probs, lens, prob_idx, n_cand, lambdas, n_lam, max_lam, opts, warm_x,
+                                chi2, reg, iters, relres, item_status, corner, kappa, s_out, all_x, status, st);
+    return eval_impl<double>(ctx, probs, n_probs, lens, prob_idx, n_cand, lambdas, n_lam, max_lam, opts, warm_x,
+                             chi2, reg, iters, relres, item_status, corner, kappa, s_out, all_x, status, st);
+}
+
+int mirage_lcurve(const double* chi2, const double* reg, const int* n_lam, int n_cand, int max_lam, int* corner,
+                  double* kappa, int* flags, void* stream) {
+    if (n_cand == 0) return MIRAGE_OK;
+    if (!chi2 || !reg || !n_lam || !corner || n_cand < 0 || max_lam < 1 || max_lam > MAX_LAM) {
+        set_error("lcurve: bad argument");
+        return MIRAGE_ERR_ARG;
+    }
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    k_lcurve<0><<<(n_cand + 127) / 128, 128, 0, st>>>(chi2, reg, n_lam, n_cand, max_lam, corner, kappa, flags);
+    CK(cudaGetLastError());
+    return MIRAGE_OK;
+}
+
+int mirage_forward(mirage_ctx_t* ctx, const mirage_problem_t* prob, const double* lens, const void* s, int n_src,
+                   void* model, double* chi2, int* status, void* stream) {
+    if (!ctx) return MIRAGE_ERR_ARG;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return MIRAGE_ERR_CUDA;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (ctx->precision == MIRAGE_FP32) return forward_impl<float>(ctx, prob, lens, s, n_src, model, chi2, status, st);
+    return forward_impl<double>(ctx, prob, lens, s, n_src, model, chi2, status, st);
+}
+
+int mirage_last_launch_count(const mirage_ctx_t* ctx) { return ctx ? ctx->last_launches : 0; }
+
+int mirage_last_phase_ms(mirage_ctx_t* ctx, double* ms) {
+    if (!ctx || !ms) return MIRAGE_ERR_ARG;
+    if (!ctx->timed) {
+        set_error("no timed batched call on this context");
+        return MIRAGE_ERR_ARG;
+    }
+    for (int i = 0; i < 3; ++i) {
+        float t = 0.f;
+        CK(cudaEventSynchronize(ctx->ev[i + 1]));
+        CK(cudaEventElapsedTime(&t, ctx->ev[i], ctx->ev[i + 1]));
+        ms[i] = t;
+    }
+    return MIRAGE_OK;
+}
+
+const char* mirage_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,14 @@
+// float kernels: runtime-K fallbacks, forward batch, ray trace, finalize
+#include "kernels.cuh"
+#include "table.h"
+
+namespace mirage {
+void fill_f32_gen(KernelTable& t) {
+    t.cgls[0][0][0] = (const void*)k_cgls<float, 0, false>;
+    t.cgls[0][1][0] = (const void*)k_cgls<float, 0, true>;
+    t.fwd[0][0] = (const void*)k_forward<float, 0>;
+    t.fwd[0][9] = (const void*)k_forward<float, 9>;
+    t.raytrace[0] = (const void*)k_raytrace<float>;
+    t.finalize[0] = (const void*)k_finalize<float>;
+}
+}  // namespace mirage

@@ -1,0 +1,11 @@
+// float kernels, 15x15 PSF
+#include "kernels.cuh"
+#include "table.h"
+
+namespace mirage {
+void fill_f32_k15(KernelTable& t) {
+    t.cgls[0][0][15] = (const void*)k_cgls<float, 15, false>;
+    t.cgls[0][1][15] = (const void*)k_cgls<float, 15, true>;
+
+}
+}  // namespace mirage

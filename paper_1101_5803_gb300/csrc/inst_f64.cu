@@ -1,0 +1,14 @@
+// double kernels (FP64 mode)
+#include "kernels.cuh"
+#include "table.h"
+
+namespace mirage {
+void fill_f64(KernelTable& t) {
+    t.cgls[1][0][5] = (const void*)k_cgls<double, 5, false>;
+    t.cgls[1][0][0] = (const void*)k_cgls<double, 0, false>;
+    t.cgls[1][1][0] = (const void*)k_cgls<double, 0, true>;
+    t.fwd[1][0] = (const void*)k_forward<double, 0>;
+    t.raytrace[1] = (const void*)k_raytrace<double>;
+    t.finalize[1] = (const void*)k_finalize<double>;
+}
+}  // namespace mirage

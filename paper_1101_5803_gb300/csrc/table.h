@@ -1,0 +1,26 @@
+// Registry of the compiled kernel instantiations (filled by the inst_*.cu
+// translation units, which are compiled in parallel).
+#pragma once
+
+namespace mirage {
+
+constexpr int MAX_K = 32;  // tap sides 1..31 (odd); index 0 = runtime-K kernel
+
+struct KernelTable {
+    // cgls[prec][big][K], prec 0 = float, 1 = double; nullptr = not compiled
+    const void* cgls[2][2][MAX_K];
+    const void* fwd[2][MAX_K];
+    const void* raytrace[2];
+    const void* finalize[2];
+};
+
+void fill_f32_k5(KernelTable& t);
+void fill_f32_k7(KernelTable& t);
+void fill_f32_k9(KernelTable& t);
+void fill_f32_k11(KernelTable& t);
+void fill_f32_k15(KernelTable& t);
+void fill_f32_k21(KernelTable& t);
+void fill_f32_gen(KernelTable& t);
+void fill_f64(KernelTable& t);
+
+}  // namespace mirage

@@ -1,0 +1,297 @@
+"""GPU parity of the CUDA path (through the C ABI) against the CPU oracle.
+
+Tolerances (derivation in DESIGN.md, "Parity tolerances"):
+  FP64 context, CG to 1e-12: |ds|/|s| <= 1e-10 and |dchi2|/chi2 <= 1e-10.
+  FP32 context (FP32 matvecs, FP64 reductions), CG to 1e-6:
+    * chi2: |dchi2|/chi2 <= 1e-5 on every (candidate, lambda);
+    * the oracle's FP64 normal-equation residual of the GPU solution is
+      <= 10 tol (FP32 matvec rounding bounds how far below tol the true
+      residual can be pushed);
+    * s: |ds|/|s| <= 1e-4 where the oracle's kappa_2(A) <= 1e2, and
+      <= 2 kappa_2(A) r + 1e-5 elsewhere, r the oracle-measured residual.
+"""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle.lcurve import lcurve_corner
+from oracle.solve import build_operators, eval_candidate, forward_chi2, solve_lambda
+from synth import Geometry, REG_GRADIENT, REG_IDENTITY, REG_LAPLACIAN
+
+from .helpers import device_problem, host_problem, make_problem, rel
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mods():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1101_5803_gb300 import binding
+    assert torch.cuda.is_available()
+    return binding
+
+
+@pytest.fixture(scope="module")
+def ctx32(mods):
+    c = mods.Context(0, mods.MIRAGE_FP32)
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def ctx64(mods):
+    c = mods.Context(0, mods.MIRAGE_FP64)
+    yield c
+    c.close()
+
+
+def _lens_t(lenses):
+    return torch.as_tensor(np.asarray(lenses, dtype=np.float64).reshape(-1, 7), device="cuda")
+
+
+def _lam_t(lams, n):
+    return torch.as_tensor(np.tile(np.asarray(lams, dtype=np.float64), (n, 1)), device="cuda")
+
+
+# ---------------------------------------------------------------------------
+# forward operator B L (ray trace, interpolation, blur) and Eq. chi2
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+@pytest.mark.parametrize("geom", [
+    Geometry(24, 20, 0.1, 12, 10, -0.8, 0.8, -0.7, 0.7, 5, 1, REG_LAPLACIAN),
+    Geometry(30, 27, 0.09, 11, 13, -0.9, 0.7, -0.8, 0.9, 7, 2, REG_GRADIENT),   # ragged, sub-pixels
+    Geometry(64, 64, 0.05, 32, 32, -0.8, 0.8, -0.8, 0.8, 9, 1, REG_LAPLACIAN),
+])
+def test_forward_matches_oracle(mods, ctx32, ctx64, precision, geom):
+    ctx = ctx32 if precision == "fp32" else ctx64
+    dt = torch.float32 if precision == "fp32" else torch.float64
+    prob = make_problem(geom, seed=3)
+    lens = [1.05, 0.65, 0.3, 0.03, -0.02, 0.04, 0.7]
+    S = np.random.default_rng(4).uniform(0, 1, (5, geom.ns))
+    m_o, c_o = forward_chi2(prob, lens, S)
+    m_g, c_g, st = ctx.forward(device_problem(prob, dt), _lens_t(lens)[0], torch.as_tensor(S, dtype=dt,
+                                                                                             device="cuda"))
+    m_g = m_g.double().cpu().numpy()
+    c_g = c_g.cpu().numpy()
+    tol = 2e-6 if precision == "fp32" else 1e-12
+    assert int(st.item()) == 0
+    assert np.abs(m_g - m_o).max() <= tol * np.abs(m_o).max()
+    np.testing.assert_allclose(c_g, c_o, rtol=50 * tol)
+
+
+def test_forward_delta_psf_identity_lens(mods, ctx64):
+    # b = 0, no shear, source centres on the image centres, delta PSF: model = s.
+    # Dyadic grid values keep every coordinate exact, so the edge pixels sit
+    # exactly on the first/last source centres on both sides.
+    g = Geometry(12, 8, 0.25, 12, 8, -1.5, 1.5, -1.0, 1.0, 3, 1, REG_IDENTITY)
+    psf = np.zeros((3, 3))
+    psf[1, 1] = 1.0
+    from oracle.solve import Problem
+    prob = Problem(g, np.zeros((8, 12)), np.ones((8, 12)), np.ones((8, 12), np.uint8), psf)
+    S = np.random.default_rng(0).standard_normal((2, 96))
+    m_g, c_g, _ = ctx64.forward(device_problem(prob, torch.float64), _lens_t([0, 0.8, 0, 0, 0, 0, 0])[0],
+                                torch.as_tensor(S, device="cuda"))
+    np.testing.assert_allclose(m_g.cpu().numpy(), S, atol=1e-13)
+    np.testing.assert_allclose(c_g.cpu().numpy(), (S ** 2).sum(axis=1), rtol=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# full evaluation: CGLS over the lambda grid + L-curve corner
+# ---------------------------------------------------------------------------
+def test_eval_fp64_small_single_lambda(mods, ctx64):
+    # 32x32 image at 0.1", 16x16 source over +-0.8", 5x5 PSF sigma 1 px,
+    # gradient H, lambda = 1e-2, CG to 1e-10 (checked at 1e-12 here)
+    g = synth.geom_small_fp64()
+    prob = make_problem(g, seed=0, psf_sigma=1.0, fixed_source=True)
+    lens = synth.TRUE_LENS
+    ops = build_operators(prob, lens)
+    s_o = solve_lambda(ops, 1e-2)
+    out = ctx64.eval_batch([device_problem(prob, torch.float64)], _lens_t(lens), [0], _lam_t([1e-2], 1), [1],
+                           tol=1e-12)
+    s_g = out["s"][0].cpu().numpy()
+    assert rel(s_g, s_o) <= 1e-10
+    from oracle.solve import chi2_of
+    c_o = chi2_of(ops, prob.d, s_o)
+    assert abs(out["chi2"][0, 0].item() - c_o) <= 1e-10 * c_o
+    assert int(out["status"][0].item()) & ~mods.ST_LCURVE_FLAT == 0
+
+
+def test_eval_fp64_grid_and_corner(mods, ctx64):
+    g = synth.geom_small_fp64()
+    prob = make_problem(g, seed=1, psf_sigma=1.0)
+    lams = synth.lambda_grid(10)
+    lenses = [synth.TRUE_LENS, [0.95, 0.75, 0.4, 0.02, -0.03, 0.03, 0.8]]
+    out = ctx64.eval_batch([device_problem(prob, torch.float64)], _lens_t(lenses), [0, 0], _lam_t(lams, 2),
+                           [10, 10], tol=1e-12, want_all_x=True)
+    for c, lens in enumerate(lenses):
+        r = eval_candidate(prob, lens, lams)
+        np.testing.assert_allclose(out["chi2"][c].cpu().numpy(), r.chi2, rtol=1e-10)
+        np.testing.assert_allclose(out["reg"][c].cpu().numpy(), r.reg, rtol=1e-9)
+        X = out["all_x"][c].cpu().numpy()
+        for k in range(10):
+            assert rel(X[k, :g.ns], r.s[k]) <= 1e-10
+        assert int(out["corner"][c].item()) == r.corner
+        np.testing.assert_allclose(out["kappa"][c].cpu().numpy(), r.kappa, rtol=1e-6, atol=1e-9)
+
+
+def _fp32_checks(out, prob, lenses, lams, tol):
+    for c, lens in enumerate(lenses):
+        ops = build_operators(prob, lens)
+        r = eval_candidate(prob, lens, lams)
+        X = out["all_x"][c].double().cpu().numpy()
+        ns = prob.geom.ns
+        for k, lam in enumerate(lams):
+            A = ops.FtWF + lam * ops.HtH
+            s_g = X[k, :ns]
+            rr = np.linalg.norm(ops.rhs - A @ s_g) / np.linalg.norm(ops.rhs)
+            st = int(out["item_status"][c, k].item())
+            assert rr <= 10 * tol, (c, k, rr, st)
+            chi_g = out["chi2"][c, k].item()
+            assert abs(chi_g - r.chi2[k]) <= 1e-5 * r.chi2[k], (c, k)
+            ev = np.linalg.eigvalsh(A)
+            kap = ev[-1] / ev[0]
+            err = rel(s_g, r.s[k])
+            bound = 1e-4 if kap <= 1e2 else 2 * kap * rr + 1e-5
+            assert err <= bound, (c, k, err, kap, rr)
+            # the library's reported true residual agrees with the oracle's
+            assert abs(out["relres"][c, k].item() - rr) <= 0.2 * rr + 1e-7
+        cg = int(out["corner"][c].item())
+        if cg != r.corner:
+            # only a near-tie of the curvature may move the corner
+            kk = r.kappa
+            assert abs(kk[cg] - kk[r.corner]) <= 1e-3 * kk[r.corner], (cg, r.corner)
+
+
+def test_eval_fp32_64px(mods, ctx32):
+    # 64x64 at 0.05", 32x32 source, 9x9 PSF sigma 1.5, Laplacian, 16 lambdas, tol 1e-6
+    g = synth.geom_ga64()
+    prob = make_problem(g, seed=2)
+    lams = synth.lambda_grid(16)
+    rng = np.random.default_rng(5)
+    lenses = np.vstack([synth.TRUE_LENS, synth.lens_population(rng, 2)])
+    out = ctx32.eval_batch([device_problem(prob)], _lens_t(lenses), [0] * 3, _lam_t(lams, 3), [16] * 3,
+                           tol=1e-6, want_all_x=True)
+    _fp32_checks(out, prob, lenses, lams, 1e-6)
+
+
+def test_eval_fp32_ragged_subpix_gradient(mods, ctx32):
+    g = Geometry(30, 26, 0.09, 14, 12, -0.8, 0.8, -0.7, 0.7, 7, 2, REG_GRADIENT)
+    prob = make_problem(g, seed=6)
+    lams = synth.lambda_grid(8, 1e-3, 1e1)
+    lenses = [synth.TRUE_LENS, [1.1, 0.55, 2.0, -0.05, 0.04, 0.08, 2.5]]
+    out = ctx32.eval_batch([device_problem(prob)], _lens_t(lenses), [0, 0], _lam_t(lams, 2), [8, 8],
+                           tol=1e-6, want_all_x=True)
+    _fp32_checks(out, prob, lenses, lams, 1e-6)
+
+
+def test_eval_fp32_global_memory_variant(mods, ctx32):
+    # a 128x128 image with an 11x11 PSF does not fit in shared memory: the
+    # work buffers live in global memory
+    g = synth.geom_e2e128()
+    prob = make_problem(g, seed=7)
+    lams = synth.lambda_grid(4, 1e-2, 1e1)
+    lenses = [synth.TRUE_LENS]
+    out = ctx32.eval_batch([device_problem(prob)], _lens_t(lenses), [0], _lam_t(lams, 1), [4], tol=1e-6,
+                           want_all_x=True)
+    _fp32_checks(out, prob, lenses, lams, 1e-6)
+
+
+def test_uneven_batch_two_problems(mods, ctx32):
+    # two problems of different image, source and PSF sizes in one call
+    g1 = Geometry(48, 48, 6.4 / 48, 16, 16, -0.8, 0.8, -0.8, 0.8, 7, 1, REG_LAPLACIAN)
+    g2 = Geometry(64, 64, 0.1, 24, 24, -0.8, 0.8, -0.8, 0.8, 11, 1, REG_LAPLACIAN)
+    m1 = synth.annular_mask(g1, 0.4, 2.0)
+    p1 = make_problem(g1, seed=8, psf_sigma=7 / 6, mask=m1)
+    p2 = make_problem(g2, seed=9, psf_sigma=11 / 6)
+    lams = synth.lambda_grid(8)
+    lens = [synth.TRUE_LENS, [0.9, 0.8, 1.0, 0.05, 0.0, 0.02, 0.1]]
+    out = ctx32.eval_batch([device_problem(p1), device_problem(p2)], _lens_t(lens), [0, 1], _lam_t(lams, 2),
+                           [8, 6], tol=1e-6, want_all_x=True)
+    for c, prob in enumerate([p1, p2]):
+        n = [8, 6][c]
+        r = eval_candidate(prob, lens[c], lams[:n])
+        np.testing.assert_allclose(out["chi2"][c, :n].cpu().numpy(), r.chi2, rtol=1e-5)
+
+
+# ---------------------------------------------------------------------------
+# L-curve kernel
+# ---------------------------------------------------------------------------
+def test_lcurve_kernel_matches_oracle(mods):
+    rng = np.random.default_rng(11)
+    n, ml = 40, 20
+    chi2 = np.zeros((n, ml))
+    reg = np.zeros((n, ml))
+    nl = rng.integers(3, ml + 1, n)
+    for c in range(n):
+        lam = np.logspace(-4, 2, nl[c])
+        a, b = rng.uniform(0.5, 2), rng.uniform(0.5, 2)
+        chi2[c, :nl[c]] = 1e3 * (1 + a * lam / (1 + lam)) * (1 + 0.01 * rng.standard_normal(nl[c]) ** 2)
+        reg[c, :nl[c]] = 1e2 / (1 + b * lam) ** 2
+    chi2[0, :] = 5.0  # collinear -> flat
+    reg[0, :] = np.logspace(3, 1, ml)
+    nl[0] = ml
+    corner, kappa, flags = mods.mirage_lcurve(torch.as_tensor(chi2, device="cuda"),
+                                              torch.as_tensor(reg, device="cuda"),
+                                              torch.as_tensor(nl.astype(np.int32), device="cuda"))
+    for c in range(n):
+        co, ko, flat = lcurve_corner(chi2[c, :nl[c]], reg[c, :nl[c]])
+        kg = kappa[c, :nl[c]].cpu().numpy()
+        np.testing.assert_allclose(kg, ko, rtol=1e-8, atol=1e-12)
+        assert int(corner[c].item()) == co
+        assert bool(flags[c].item()) == flat
+
+
+# ---------------------------------------------------------------------------
+# statuses, modes, determinism
+# ---------------------------------------------------------------------------
+def test_status_flags(mods, ctx32):
+    g = Geometry(32, 32, 0.1, 16, 16, -0.8, 0.8, -0.8, 0.8, 5, 1, REG_LAPLACIAN)
+    prob = make_problem(g, seed=12)
+    empty = make_problem(g, seed=12, mask=np.zeros((32, 32), np.uint8))
+    lenses = [synth.TRUE_LENS, [np.nan, 0.7, 0, 0, 0, 0, 0], [1.0, 1.5, 0, 0, 0, 0, 0], synth.TRUE_LENS]
+    lams = synth.lambda_grid(4)
+    out = ctx32.eval_batch([device_problem(prob), device_problem(empty)], _lens_t(lenses), [0, 0, 0, 1],
+                           _lam_t(lams, 4), [4] * 4, tol=1e-6)
+    st = out["status"].cpu().numpy()
+    assert st[0] & (mods.ST_BAD_PARAM | mods.ST_EMPTY_MAP) == 0
+    assert st[1] & mods.ST_BAD_PARAM and st[2] & mods.ST_BAD_PARAM
+    assert np.all(np.isinf(out["chi2"][1].cpu().numpy()))
+    assert st[3] & mods.ST_EMPTY_MAP
+    out2 = ctx32.eval_batch([device_problem(prob)], _lens_t(lenses[:1]), [0], _lam_t(lams, 1), [4], tol=1e-9,
+                            maxit=1)
+    assert int(out2["status"][0].item()) & mods.ST_MAXIT
+    assert np.all(out2["iters"][0].cpu().numpy() <= 1)
+
+
+def test_plain_batched_graph_host_agree_bitwise(mods, ctx32):
+    g = synth.geom_ga64()
+    prob = make_problem(g, seed=13)
+    dp = device_problem(prob)
+    rng = np.random.default_rng(14)
+    lenses = synth.lens_population(rng, 5)
+    lams = synth.lambda_grid(6, 1e-2, 1e2)
+    L, Lm = _lens_t(lenses), _lam_t(lams, 5)
+    a = ctx32.eval_batch([dp], L, [0] * 5, Lm, [6] * 5, tol=1e-6)
+    b = ctx32.eval_batch([dp], L, [0] * 5, Lm, [6] * 5, tol=1e-6, mode=mods.MIRAGE_MODE_PLAIN)
+    c1 = ctx32.eval_batch([dp], L, [0] * 5, Lm, [6] * 5, tol=1e-6, use_graph=True)
+    c2 = ctx32.eval_batch([dp], L, [0] * 5, Lm, [6] * 5, tol=1e-6, use_graph=True, out=c1)
+    hp = host_problem(prob)
+    h = ctx32.eval_batch([hp], L.cpu(), [0] * 5, Lm.cpu(), [6] * 5, tol=1e-6)
+    for key in ("chi2", "reg", "iters", "corner", "status", "s"):
+        ref = a[key].cpu()
+        for other in (b, c2, h):
+            assert torch.equal(other[key].cpu(), ref), key
+
+
+def test_warm_start_converges_faster(mods, ctx32):
+    g = synth.geom_ga64()
+    prob = make_problem(g, seed=15)
+    dp = device_problem(prob)
+    lams = synth.lambda_grid(8, 1e-2, 1e2)
+    L, Lm = _lens_t([synth.TRUE_LENS]), _lam_t(lams, 1)
+    cold = ctx32.eval_batch([dp], L, [0], Lm, [8], tol=1e-6, want_all_x=True)
+    warm = ctx32.eval_batch([dp], L, [0], Lm, [8], tol=1e-6, warm_x=cold["all_x"].contiguous())
+    assert warm["iters"].sum().item() < 0.2 * cold["iters"].sum().item()
+    np.testing.assert_allclose(warm["chi2"].cpu().numpy(), cold["chi2"].cpu().numpy(), rtol=1e-5)

@@ -1,0 +1,39 @@
+"""CPU checks of the C-ABI library: it builds for sm_103a, loads, and exports
+every function include/mirage.h declares (no compute calls without a GPU)."""
+import ctypes
+import os
+
+import pytest
+
+from paper_1101_5803_gb300 import binding
+from paper_1101_5803_gb300.build import build
+
+
+@pytest.fixture(scope="module")
+def lib():
+    path = build()
+    assert os.path.exists(path)
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_entry_points():
+    names = binding.header_functions()
+    for n in ("mirage_create", "mirage_destroy", "mirage_eval_batch", "mirage_lcurve", "mirage_forward"):
+        assert n in names
+
+
+def test_exports_every_declared_symbol(lib):
+    for name in binding.header_functions():
+        assert hasattr(lib, name), name
+
+
+def test_binding_loads(lib):
+    l2 = binding.load_library()
+    assert l2.mirage_eval_batch is not None
+
+
+def test_struct_layouts_match_header():
+    # mirage_geom_t: 2 ints, 3 doubles, 2 ints, 4 doubles, 3 ints (natural alignment)
+    assert ctypes.sizeof(binding.mirage_geom_t) == 88
+    assert ctypes.sizeof(binding.mirage_opts_t) == 32
+    assert ctypes.sizeof(binding.mirage_problem_t) == 88 + 32

@@ -92,15 +92,17 @@ typedef struct {
 } mirage_problem_t;
 
 typedef struct {
-    double tol;        /* stop when ||rhs - A s|| <= tol ||rhs|| (recursive residual) */
-    int maxit;         /* CG iteration cap per (candidate, lambda); <= 0: 10 * ns */
+    double tol;        /* stop when ||rhs - A s|| <= tol ||rhs||, the residual of the
+                          solution evaluated in FP64 */
+    int maxit;         /* CG iteration cap per (candidate, lambda), summed over the
+                          refinement's inner solves; <= 0: 25 * ns */
     int mode;          /* MIRAGE_MODE_* */
     int mem;           /* MIRAGE_MEM_* */
     int use_graph;     /* 1: capture the batched launch sequence once per argument
                           set and replay it on identical calls */
     int threads;       /* 0 = default; < 0 = record per-phase CUDA events on the
                           stream (non-graph batched calls) for mirage_last_phase_ms */
-    int replace_every; /* true-residual replacement period in iterations; 0 = 50 */
+    int replace_every; /* reserved (0) */
 } mirage_opts_t;
 
 typedef struct mirage_ctx mirage_ctx_t;

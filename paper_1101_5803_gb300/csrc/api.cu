@@ -102,9 +102,9 @@ struct mirage_ctx {
     int max_smem = 0;
     int last_launches = 0;
     // scratch
-    DevBuf E, Etmp, inv, cst, swp, bwp, nent, cstat, X, istat, slab, probs, cand_prob, items, counters;
+    DevBuf E, E64, Etmp, inv, cst, swp, dpad, nent, cstat, X, istat, slab, probs, cand_prob, items, counters;
     DevBuf stage;  // MIRAGE_MEM_HOST staging
-    DevBuf fE, fEtmp, finv, fcst, fswp, fbwp, fnent, fcstat, fslab, fprob, fcand;
+    DevBuf fE, fE64, fEtmp, finv, fcst, fswp, fdpad, fnent, fcstat, fslab, fprob, fcand;
     std::map<std::string, GraphEntry> graphs;
     std::map<const void*, int> smem_set;  // kernel -> dynamic smem attribute set
     cudaStream_t cap_stream = nullptr;   // graphs are captured here and launched on the caller's stream
@@ -167,20 +167,22 @@ Prob<T> make_prob(const mirage_problem_t& mp, const void* d, const void* sigma, 
     P.tiles_y = (g.ny + TILE - 1) / TILE;
     P.ntiles = P.tiles_x * P.tiles_y;
     const int VW = 16 / (int)sizeof(T);
-    const int nvw = (TILE + g.kpsf - 1 + VW - 1) / VW * VW;
-    P.Wp = (P.tiles_x - 1) * TILE + nvw;
+    P.xoff = (P.hk + VW - 1) / VW * VW;
+    const int sh = P.xoff - P.hk;
+    const int nvw = (TILE + g.kpsf - 1 + sh + VW - 1) / VW * VW;
+    P.Wp = std::max((P.tiles_x - 1) * TILE + nvw, P.xoff + g.nx + P.hk);
+    P.Wp = (P.Wp + VW - 1) / VW * VW;
     P.Hp = P.tiles_y * TILE + g.kpsf - 1;
     P.plen = P.Wp * P.Hp;
-    P.pix = (T)g.pix;
-    P.cx = (T)g.cx;
-    P.cy = (T)g.cy;
-    P.sub0 = (T)((0.5 / g.subpix - 0.5) * g.pix);
-    P.subd = (T)(g.pix / g.subpix);
-    const double hx = (g.sxmax - g.sxmin) / g.sx, hy = (g.symax - g.symin) / g.sy;
-    P.c0x = (T)(g.sxmin + 0.5 * hx);
-    P.c0y = (T)(g.symin + 0.5 * hy);
-    P.inv_hx = (T)(1.0 / hx);
-    P.inv_hy = (T)(1.0 / hy);
+    P.pix = g.pix;
+    P.cx = g.cx;
+    P.cy = g.cy;
+    P.sub0 = (0.5 / g.subpix - 0.5) * g.pix;
+    P.subd = g.pix / g.subpix;
+    P.hx = (g.sxmax - g.sxmin) / g.sx;
+    P.hy = (g.symax - g.symin) / g.sy;
+    P.c0x = g.sxmin + 0.5 * P.hx;
+    P.c0y = g.symin + 0.5 * P.hy;
     P.invNp = (T)(1.0 / P.Np);
     P.d = reinterpret_cast<const T*>(d);
     P.sigma = reinterpret_cast<const T*>(sigma);
@@ -221,11 +223,12 @@ template <typename T>
 void fill_scratch(CandScratch<T>& cs, mirage_ctx* ctx, bool fwd, long long sE, long long sInv, long long sCst,
                   long long sPad) {
     cs.E = (fwd ? ctx->fE : ctx->E).as<Entry<T>>();
-    cs.Etmp = (fwd ? ctx->fEtmp : ctx->Etmp).as<Entry<T>>();
+    cs.E64 = sizeof(T) == 8 ? reinterpret_cast<Entry<double>*>(cs.E) : (fwd ? ctx->fE64 : ctx->E64).as<Entry<double>>();
+    cs.Etmp = (fwd ? ctx->fEtmp : ctx->Etmp).as<Entry<double>>();
     cs.inv = (fwd ? ctx->finv : ctx->inv).as<int>();
     cs.cst = (fwd ? ctx->fcst : ctx->cst).as<int>();
     cs.swp = (fwd ? ctx->fswp : ctx->swp).as<T>();
-    cs.bwp = (fwd ? ctx->fbwp : ctx->bwp).as<T>();
+    cs.dpad = (fwd ? ctx->fdpad : ctx->dpad).as<T>();
     cs.nent = (fwd ? ctx->fnent : ctx->nent).as<int>();
     cs.cstat = (fwd ? ctx->fcstat : ctx->cstat).as<int>();
     cs.sE = sE;
@@ -391,11 +394,12 @@ int eval_impl(mirage_ctx* ctx, const mirage_problem_t* probs, int n_probs, const
 
     // ---- device path
     TRY(ctx->E.ensure(sizeof(Entry<T>) * n_cand * sE));
-    TRY(ctx->Etmp.ensure(sizeof(Entry<T>) * n_cand * sE));
+    if (sizeof(T) == 4) TRY(ctx->E64.ensure(sizeof(Entry<double>) * n_cand * sE));
+    TRY(ctx->Etmp.ensure(sizeof(Entry<double>) * n_cand * sE));
     TRY(ctx->inv.ensure(sizeof(int) * n_cand * sInv));
     TRY(ctx->cst.ensure(sizeof(int) * n_cand * sCst));
     TRY(ctx->swp.ensure(sizeof(T) * n_cand * sPad));
-    TRY(ctx->bwp.ensure(sizeof(T) * n_cand * sPad));
+    TRY(ctx->dpad.ensure(sizeof(T) * n_cand * sPad));
     TRY(ctx->nent.ensure(sizeof(int) * n_cand));
     TRY(ctx->cstat.ensure(sizeof(int) * n_cand));
     if (!d_allx) TRY(ctx->X.ensure(sizeof(T) * nitems_all * max_ns));
@@ -428,7 +432,7 @@ int eval_impl(mirage_ctx* ctx, const mirage_problem_t* probs, int n_probs, const
         g.fn = fn;
         g.big = big;
         g.smem = std::max(g.smem, smem_bytes<T>(P, big));
-        g.slab = std::max<long long>(g.slab, (long long)slab_elems<T>(P));
+        g.slab = std::max<long long>(g.slab, (long long)slab_bytes<T>(P, big));
         const double work = (double)P.plen * P.K * P.K + 8.0 * P.nrays;
         for (int k = 0; k < n_lam[c]; ++k) {
             // lambda grids ascend: smaller k = smaller lambda = more CG iterations
@@ -467,22 +471,23 @@ int eval_impl(mirage_ctx* ctx, const mirage_problem_t* probs, int n_probs, const
     meta.insert(meta.end(), n_lam, n_lam + n_cand);
     meta.insert(meta.end(), items_v.begin(), items_v.end());
     TRY(ctx->counters.ensure(sizeof(int) * n_counters));
+    // per-CTA global slab (bytes): FP64 refinement buffers, plus all work
+    // buffers for items that do not fit in shared memory
     long long slab_stride = 0;
-    int nbig_grid = 0;
-    for (Group* g : glist)
-        if (g->big) {
-            slab_stride = std::max(slab_stride, (g->slab + 63) / 64 * 64);
-            nbig_grid = std::max<int>(nbig_grid, (int)std::min<long long>(ctx->sm_count, (long long)g->items.size()));
-        }
-    if (o.mode == MIRAGE_MODE_PLAIN && slab_stride) nbig_grid = std::max(nbig_grid, max_lam);
-    if (slab_stride) TRY(ctx->slab.ensure(sizeof(T) * slab_stride * std::max(nbig_grid, 1)));
+    int slab_grid = 0;
+    for (Group* g : glist) {
+        slab_stride = std::max(slab_stride, (g->slab + 255) / 256 * 256);
+        slab_grid = std::max<int>(slab_grid, (int)std::min<long long>(ctx->sm_count, (long long)g->items.size()));
+    }
+    if (o.mode == MIRAGE_MODE_PLAIN) slab_grid = std::max(slab_grid, max_lam);
+    TRY(ctx->slab.ensure((size_t)slab_stride * std::max(slab_grid, 1)));
 
     // graph key: everything that shapes the launch sequence
     std::string key;
     const bool graph = o.use_graph && o.mode == MIRAGE_MODE_BATCHED;
     if (graph) {
         // a grown scratch buffer invalidates every captured graph
-        std::vector<void*> now = {ctx->E.p, ctx->Etmp.p, ctx->inv.p, ctx->cst.p, ctx->swp.p, ctx->bwp.p,
+        std::vector<void*> now = {ctx->E.p, ctx->E64.p, ctx->Etmp.p, ctx->inv.p, ctx->cst.p, ctx->swp.p, ctx->dpad.p,
                                   ctx->nent.p, ctx->cstat.p, ctx->X.p, ctx->istat.p, ctx->slab.p, ctx->counters.p};
         if (now != ctx->scratch_seen) {
             drop_graphs(ctx);
@@ -543,7 +548,7 @@ int eval_impl(mirage_ctx* ctx, const mirage_problem_t* probs, int n_probs, const
     A.max_ns = (int)max_ns;
     A.warm_x = d_warm;
     A.cs = cs;
-    A.slab = ctx->slab.as<T>();
+    A.slab = ctx->slab.p;
     A.slab_stride = slab_stride;
     A.X = dX;
     A.chi2 = d_chi2;
@@ -692,11 +697,12 @@ int forward_impl(mirage_ctx* ctx, const mirage_problem_t* prob, const double* le
     }
     const long long sE = P.nrays, sInv = P.nrays, sCst = (P.ncells + 1 + 3) / 4 * 4, sPad = (P.plen + 3) / 4 * 4;
     TRY(ctx->fE.ensure(sizeof(Entry<T>) * sE));
-    TRY(ctx->fEtmp.ensure(sizeof(Entry<T>) * sE));
+    if (sizeof(T) == 4) TRY(ctx->fE64.ensure(sizeof(Entry<double>) * sE));
+    TRY(ctx->fEtmp.ensure(sizeof(Entry<double>) * sE));
     TRY(ctx->finv.ensure(sizeof(int) * sInv));
     TRY(ctx->fcst.ensure(sizeof(int) * sCst));
     TRY(ctx->fswp.ensure(sizeof(T) * sPad));
-    TRY(ctx->fbwp.ensure(sizeof(T) * sPad));
+    TRY(ctx->fdpad.ensure(sizeof(T) * sPad));
     TRY(ctx->fnent.ensure(sizeof(int)));
     TRY(ctx->fcstat.ensure(sizeof(int)));
     TRY(ctx->fprob.ensure(sizeof(Prob<T>) + sizeof(int)));
@@ -717,7 +723,7 @@ int forward_impl(mirage_ctx* ctx, const mirage_problem_t* prob, const double* le
     void* a1[] = {(void*)&dprob, (void*)&dcand, (void*)&lens, &cand0, &nc, &cs};
     TRY(launch(ctx, tb.raytrace[prec], dim3(1), dim3(NTHREADS), a1, (size_t)P.ncells * 4, st));
     const void* fn = pick_fwd(prec, P.K);
-    const size_t smem = align_up<T>(sizeof(T) * 2 * P.K * P.kp, 16) + 2 * 33 * sizeof(double) + 16;
+    const size_t smem = align_up<T>(sizeof(T) * P.K * P.kp, 16) + 2 * 33 * sizeof(double) + 16;
     TRY(set_smem(ctx, fn, smem));
     const T* S = reinterpret_cast<const T*>(s);
     T* M = reinterpret_cast<T*>(model);
@@ -762,9 +768,9 @@ int mirage_destroy(mirage_ctx_t* ctx) {
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     for (int e = 0; e < 4; ++e)
         if (ctx->ev[e]) cudaEventDestroy(ctx->ev[e]);
-    DevBuf* bufs[] = {&ctx->E, &ctx->Etmp, &ctx->inv, &ctx->cst, &ctx->swp, &ctx->bwp, &ctx->nent, &ctx->cstat,
+    DevBuf* bufs[] = {&ctx->E, &ctx->E64, &ctx->Etmp, &ctx->inv, &ctx->cst, &ctx->swp, &ctx->dpad, &ctx->nent, &ctx->cstat,
                       &ctx->X, &ctx->istat, &ctx->slab, &ctx->probs, &ctx->cand_prob, &ctx->items, &ctx->counters,
-                      &ctx->stage, &ctx->fE, &ctx->fEtmp, &ctx->finv, &ctx->fcst, &ctx->fswp, &ctx->fbwp,
+                      &ctx->stage, &ctx->fE, &ctx->fE64, &ctx->fEtmp, &ctx->finv, &ctx->fcst, &ctx->fswp, &ctx->fdpad,
                       &ctx->fnent, &ctx->fcstat, &ctx->fslab, &ctx->fprob, &ctx->fcand};
     for (DevBuf* b : bufs) b->release();
     delete ctx;

@@ -11,7 +11,8 @@
 //                Eq. TKReg, one (candidate, lambda) work item per CTA pass,
 //                items pulled from a queue by a persistent grid.  L, B, B^T,
 //                L^T and H are applied matrix-free; B and B^T are direct
-//                zero-padded convolutions on 4x4 register tiles.
+//                zero-padded convolutions on 4x4 register tiles.  FP32
+//                inner solves sit inside an FP64 residual refinement.
 //   k_finalize   L-curve corner (Section 2.6) per candidate, status, s_out.
 //   k_forward    B L s and Eq. chi2 for a batch of sources at one lens.
 #pragma once
@@ -43,8 +44,9 @@ struct alignas(2 * sizeof(T) > 8 ? 2 * sizeof(T) : 16) Entry {
 template <typename T>
 struct Prob {
     int nx, ny, npix, sx, sy, ns, nreg, K, hk, n_sub, Np, nrays, ncx, ncells, reg;
-    int Wp, Hp, plen, tiles_x, tiles_y, ntiles, kp;  // padded layout, tap row pitch
-    T pix, cx, cy, sub0, subd, c0x, c0y, inv_hx, inv_hy, invNp;
+    int Wp, Hp, plen, tiles_x, tiles_y, ntiles, kp, xoff;  // padded layout, tap row pitch, left pad
+    double pix, cx, cy, sub0, subd, c0x, c0y, hx, hy;  // ray-trace geometry (always FP64)
+    T invNp;
     const T* d;
     const T* sigma;
     const uint8_t* mask;
@@ -54,12 +56,13 @@ struct Prob {
 // Per-candidate scratch written by k_raytrace (strides in elements).
 template <typename T>
 struct CandScratch {
-    Entry<T>* E;      // [n_cand][sE]  sorted mapped rays
-    Entry<T>* Etmp;   // [n_cand][sE]  rays in ray order (build only)
+    Entry<T>* E;      // [n_cand][sE]  sorted mapped rays (weights in T)
+    Entry<double>* E64;   // [n_cand][sE] the same rays with FP64 weights (aliases E when T = double)
+    Entry<double>* Etmp;  // [n_cand][sE] rays in ray order (build only)
     int* inv;         // [n_cand][sInv] ray -> sorted position, -1 unmapped
     int* cst;         // [n_cand][sCst] cell start offsets (ncells + 1)
     T* swp;           // [n_cand][sPad] m / sigma in padded layout
-    T* bwp;           // [n_cand][sPad] m d / sigma in padded layout
+    T* dpad;          // [n_cand][sPad] observed image in padded layout
     int* nent;        // [n_cand]
     int* cstat;       // [n_cand]
     long long sE, sInv, sCst, sPad;
@@ -80,8 +83,8 @@ struct CglsArgs {
     int max_lam, max_ns;
     const T* warm_x;        // nullable [n_cand][max_lam][max_ns]
     CandScratch<T> cs;
-    T* slab;                // BIG variant: per-CTA global work buffers
-    long long slab_stride;
+    void* slab;             // per-CTA global work buffers (FP64 refinement; all buffers if BIG)
+    long long slab_stride;  // bytes
     T* X;                   // [n_cand][max_lam][max_ns]
     double* chi2;           // [n_cand][max_lam]
     double* reg;
@@ -247,17 +250,21 @@ __global__ void __launch_bounds__(NTHREADS) k_raytrace(const Prob<T>* __restrict
     __shared__ int s_active, s_chunk[NTHREADS];
 
     Entry<T>* E = cs.E + (long long)c * cs.sE;
-    Entry<T>* Et = cs.Etmp + (long long)c * cs.sE;
+    Entry<double>* E64 = cs.E64 + (long long)c * cs.sE;
+    Entry<double>* Et = cs.Etmp + (long long)c * cs.sE;
     int* inv = cs.inv + (long long)c * cs.sInv;
     int* cst = cs.cst + (long long)c * cs.sCst;
     T* swp = cs.swp + (long long)c * cs.sPad;
-    T* bwp = cs.bwp + (long long)c * cs.sPad;
+    T* dpad = cs.dpad + (long long)c * cs.sPad;
     const int tid = threadIdx.x, bs = blockDim.x;
-    const LensT<T> L = make_lens<T>(lens + 7LL * c);
+    // rays are traced in FP64 whatever T is: the refinement residual uses
+    // these weights, and FP32-rounded weights would perturb the operator by
+    // ~1e-7, which the conditioning of small-lambda systems amplifies
+    const LensT<double> L = make_lens<double>(lens + 7LL * c);
 
     for (int i = tid; i < P.plen; i += bs) {
         swp[i] = 0;
-        bwp[i] = 0;
+        dpad[i] = 0;
     }
     for (int i = tid; i < P.ncells; i += bs) sh_counts[i] = 0;
     if (tid == 0) s_active = 0;
@@ -274,30 +281,30 @@ __global__ void __launch_bounds__(NTHREADS) k_raytrace(const Prob<T>* __restrict
     }
 
     // pass 1: trace every ray once, count rays per cell, build sqrt(W)
-    const T half_x = (T)0.5 * (T)(P.nx - 1), half_y = (T)0.5 * (T)(P.ny - 1);
-    const T fxmax = (T)(P.sx - 1), fymax = (T)(P.sy - 1);
+    const double half_x = 0.5 * (double)(P.nx - 1), half_y = 0.5 * (double)(P.ny - 1);
+    const double fxmax = (double)(P.sx - 1), fymax = (double)(P.sy - 1);
     int my_active = 0;
     for (int j = tid; j < P.npix; j += bs) {
         const int x = j % P.nx, y = j / P.nx;
-        const T tx = P.cx + ((T)x - half_x) * P.pix;
-        const T ty = P.cy + ((T)y - half_y) * P.pix;
-        const int pp = (y + P.hk) * P.Wp + x + P.hk;
+        const double tx = P.cx + ((double)x - half_x) * P.pix;
+        const double ty = P.cy + ((double)y - half_y) * P.pix;
+        const int pp = (y + P.hk) * P.Wp + x + P.xoff;
         bool any = false;
         for (int a = 0; a < P.Np; ++a) {
             const int ax = a % P.n_sub, ay = a / P.n_sub;
-            T bx, by;
-            trace_ray(L, tx + P.sub0 + (T)ax * P.subd, ty + P.sub0 + (T)ay * P.subd, bx, by);
-            const T fx = (bx - P.c0x) * P.inv_hx;
-            const T fy = (by - P.c0y) * P.inv_hy;
-            const bool m = (fx >= (T)0) && (fx <= fxmax) && (fy >= (T)0) && (fy <= fymax);
-            Entry<T> e;
+            double bx, by;
+            trace_ray(L, tx + P.sub0 + (double)ax * P.subd, ty + P.sub0 + (double)ay * P.subd, bx, by);
+            const double fx = (bx - P.c0x) / P.hx;
+            const double fy = (by - P.c0y) / P.hy;
+            const bool m = (fx >= 0.0) && (fx <= fxmax) && (fy >= 0.0) && (fy <= fymax);
+            Entry<double> e;
             e.ppos = pp;
             if (m) {
                 const int ix0 = min((int)m_floor(fx), P.sx - 2);
                 const int iy0 = min((int)m_floor(fy), P.sy - 2);
                 e.base = iy0 * P.sx + ix0;
-                e.u = fx - (T)ix0;
-                e.v = fy - (T)iy0;
+                e.u = fx - (double)ix0;
+                e.v = fy - (double)iy0;
                 atomicAdd(&sh_counts[iy0 * P.ncx + ix0], 1);
                 any = true;
             } else {
@@ -309,7 +316,7 @@ __global__ void __launch_bounds__(NTHREADS) k_raytrace(const Prob<T>* __restrict
         }
         const T w = (any && P.mask[j]) ? (T)1 / P.sigma[j] : (T)0;
         swp[pp] = w;
-        bwp[pp] = w * P.d[j];
+        dpad[pp] = P.d[j];
         my_active += (w != (T)0);
     }
     if (my_active) atomicAdd(&s_active, my_active);
@@ -349,7 +356,7 @@ __global__ void __launch_bounds__(NTHREADS) k_raytrace(const Prob<T>* __restrict
         const unsigned lt = (1u << lane) - 1u;
         for (int r0 = 0; r0 < P.nrays; r0 += 32) {
             const int r = r0 + lane;
-            Entry<T> e;
+            Entry<double> e;
             e.base = -1;
             if (r < P.nrays) e = Et[r];
             int cell = -1;
@@ -361,7 +368,15 @@ __global__ void __launch_bounds__(NTHREADS) k_raytrace(const Prob<T>* __restrict
             const int rank = __popc(peers & lt);
             if (cell >= 0) {
                 const int pos = sh_counts[cell] + rank;
-                E[pos] = e;
+                E64[pos] = e;
+                if ((void*)E != (void*)E64) {
+                    Entry<T> et;
+                    et.ppos = e.ppos;
+                    et.base = e.base;
+                    et.u = (T)e.u;
+                    et.v = (T)e.v;
+                    E[pos] = et;
+                }
                 inv[r] = pos;
             } else if (r < P.nrays) {
                 inv[r] = -1;
@@ -374,19 +389,43 @@ __global__ void __launch_bounds__(NTHREADS) k_raytrace(const Prob<T>* __restrict
 }
 
 // ---------------------------------------------------------------------------
-// convolution on a TILE x TILE output tile:
-//   out[r][c] = sum_{a,b} taps[a][b] * Pb[(y0 + r + a) * Wp + x0 + c + b]
-// taps = flipped PSF gives B, taps = PSF gives B^T (Section 2.2 operator).
+// Padded image layout.  Image pixel (x, y) lives at
+//     pp(x, y) = (y + hk) * Wp + x + xoff,   xoff = hk rounded up to VW,
+// so every 4-pixel tile row starts on a 16-byte boundary (conflict-free
+// vector access) and a K x K window never leaves the zero-filled frame.
+// Convolution of one TILE x TILE output tile at tile origin (X, Y):
+//   out[r][c] = sum_{a,b} taps[a][b] * Pb[(Y + r + a) * Wp + X + c + b + sh]
+// with Pb = buffer + 0, sh = xoff - hk.  taps = flipped PSF gives B,
+// taps = PSF gives B^T (the blur operator of Section 2.2).
 // ---------------------------------------------------------------------------
+template <typename T>
+__host__ __device__ constexpr int vec_width() {
+    return 16 / (int)sizeof(T);
+}
+template <typename T>
+__host__ __device__ constexpr int xoff_of(int hk) {
+    return (hk + vec_width<T>() - 1) / vec_width<T>() * vec_width<T>();
+}
+
 template <typename T, int K, bool SH>
 __device__ __forceinline__ void conv_tile(const T* __restrict__ Pb, int Wp, const T* __restrict__ taps,
                                           T (&acc)[TILE][TILE]) {
-    constexpr int VW = Vec16<T>::n;
-    constexpr int W = TILE + K - 1;
+    constexpr int VW = vec_width<T>();
+    constexpr int HK = (K - 1) / 2;
+    constexpr int SHF = xoff_of<T>(HK) - HK;
+    constexpr int W = TILE + K - 1 + SHF;
     constexpr int NVW = (W + VW - 1) / VW * VW;
     constexpr int KP = (K + 3) & ~3;
+    constexpr bool TAPREG = (K <= 9);
     const unsigned tap_a = smem_addr(taps);
     const unsigned src_a = SH ? smem_addr(Pb) : 0u;
+    T tw[TAPREG ? K : 1][TAPREG ? K : 1];
+    if constexpr (TAPREG) {
+#pragma unroll
+        for (int a = 0; a < K; ++a)
+#pragma unroll
+            for (int b = 0; b < K; ++b) tw[a][b] = lds_one(tap_a + (unsigned)((a * KP + b) * sizeof(T)), T(0));
+    }
 #pragma unroll
     for (int r = 0; r < TILE; ++r)
 #pragma unroll
@@ -401,35 +440,42 @@ __device__ __forceinline__ void conv_tile(const T* __restrict__ Pb, int Wp, cons
             else
                 vload(Pb + i * Wp + v, in + v);
         }
+        // b outer, r inner: consecutive updates of one accumulator are up to
+        // 16 FMAs apart, which hides the FMA latency within one warp
 #pragma unroll
-        for (int r = 0; r < TILE; ++r) {
-            const int a = i - r;
-            if (a >= 0 && a < K) {
+        for (int b = 0; b < K; ++b) {
 #pragma unroll
-                for (int b = 0; b < K; ++b) {
-                    const T t = lds_one(tap_a + (unsigned)((a * KP + b) * sizeof(T)), T(0));
+            for (int r = 0; r < TILE; ++r) {
+                const int a = i - r;
+                if (a >= 0 && a < K) {
+                    T t;
+                    if constexpr (TAPREG)
+                        t = tw[a][b];
+                    else
+                        t = lds_one(tap_a + (unsigned)((a * KP + b) * sizeof(T)), T(0));
 #pragma unroll
-                    for (int c = 0; c < TILE; ++c) acc[r][c] = fma(t, in[c + b], acc[r][c]);
+                    for (int c = 0; c < TILE; ++c) acc[r][c] = fma(t, in[c + b + SHF], acc[r][c]);
                 }
             }
         }
     }
 }
 
-// runtime-K fallback
-template <typename T>
-__device__ __forceinline__ void conv_tile_rt(const T* __restrict__ Pb, int Wp, const T* __restrict__ taps,
-                                             int K, int KP, T (&acc)[TILE][TILE]) {
+// runtime-K tile (any type, any address space); also the FP64 path of the
+// mixed-precision refinement
+template <typename S, typename U>
+__device__ __forceinline__ void conv_tile_rt(const S* __restrict__ Pb, int Wp, const U* __restrict__ taps, int K,
+                                             int KP, int sh, S (&acc)[TILE][TILE]) {
 #pragma unroll
     for (int r = 0; r < TILE; ++r)
 #pragma unroll
         for (int c = 0; c < TILE; ++c) acc[r][c] = 0;
     for (int a = 0; a < K; ++a) {
         for (int b = 0; b < K; ++b) {
-            const T t = taps[a * KP + b];
+            const S t = (S)taps[a * KP + b];
 #pragma unroll
             for (int r = 0; r < TILE; ++r) {
-                const T* row = Pb + (r + a) * Wp + b;
+                const S* row = Pb + (r + a) * Wp + b + sh;
 #pragma unroll
                 for (int c = 0; c < TILE; ++c) acc[r][c] = fma(t, row[c], acc[r][c]);
             }
@@ -437,235 +483,321 @@ __device__ __forceinline__ void conv_tile_rt(const T* __restrict__ Pb, int Wp, c
     }
 }
 
-template <typename T, int K, bool SH>
-__device__ __forceinline__ void conv_any(const T* Pb, int Wp, const T* taps, int Krt, int KP,
-                                         T (&acc)[TILE][TILE]) {
-    if constexpr (K > 0) {
-        conv_tile<T, K, SH>(Pb, Wp, taps, acc);
-    } else {
-        conv_tile_rt<T>(Pb, Wp, taps, Krt, KP, acc);
-    }
-}
-
-// ---------------------------------------------------------------------------
-// work-item state: pointers into shared memory (or the per-CTA global slab)
-// ---------------------------------------------------------------------------
+// geometry needed inside the solver loops (passed by value)
 template <typename T>
-struct Work {
-    T* taps;      // [2][K][KP]: flipped PSF (B), PSF (B^T)
-    T* swp;       // [plen] sqrt(W)
-    T* rimg;      // [plen] image-space residual r = sqrt(W)(d - B L x)
-    T* qimg;      // [plen] sqrt(W) B L p, later reused for u = B^T sqrt(W) r
-    T* P1;        // [plen] padded conv input (L p)
-    T* P2;        // [plen] padded conv input (sqrt(W) r)
-    const Entry<T>* E;
-    const int* inv;
-    const int* cst;
-    T* x;         // [ns]
-    T* p;         // [ns]
-    T* s;         // [ns]
-    T* rreg;      // [nreg]
-    T* qreg;      // [nreg]
+struct Geo {
+    int nx, ny, sx, sy, ns, nreg, K, hk, kp, xoff, sh, Np, ncx, Wp, plen, tiles_x, ntiles, reg, nent;
+    T invNp;
 };
 
-// P1 <- L v on the tiles owned by this thread (Section 2.2: interpolation of
-// the back-traced rays on the source grid, averaged over sub-pixels)
 template <typename T>
-__device__ __forceinline__ void apply_L(const Prob<T>& P, const Work<T>& w, const T* __restrict__ v) {
-    for (int t = threadIdx.x; t < P.ntiles; t += blockDim.x) {
-        const int ty = t / P.tiles_x, tx = t - ty * P.tiles_x;
-#pragma unroll
-        for (int r = 0; r < TILE; ++r) {
-            const int y = ty * TILE + r;
-#pragma unroll
-            for (int cc = 0; cc < TILE; ++cc) {
-                const int x = tx * TILE + cc;
-                if (y < P.ny && x < P.nx) {
-                    const int j = y * P.nx + x;
-                    T val = 0;
-                    for (int a = 0; a < P.Np; ++a) {
-                        const int e = w.inv[j * P.Np + a];
-                        if (e >= 0) {
-                            const Entry<T> en = w.E[e];
-                            const T u = en.u, vv = en.v;
-                            const T* s0 = v + en.base;
-                            val += ((T)1 - vv) * (((T)1 - u) * s0[0] + u * s0[1]) +
-                                   vv * (((T)1 - u) * s0[P.sx] + u * s0[P.sx + 1]);
-                        }
-                    }
-                    w.P1[(y + P.hk) * P.Wp + x + P.hk] = val * P.invNp;
-                }
+__device__ __forceinline__ Geo<T> geo_of(const Prob<T>& P, int nent) {
+    Geo<T> g;
+    g.nx = P.nx;
+    g.ny = P.ny;
+    g.sx = P.sx;
+    g.sy = P.sy;
+    g.ns = P.ns;
+    g.nreg = P.nreg;
+    g.K = P.K;
+    g.hk = P.hk;
+    g.kp = P.kp;
+    g.xoff = P.xoff;
+    g.sh = P.xoff - P.hk;
+    g.Np = P.Np;
+    g.ncx = P.ncx;
+    g.Wp = P.Wp;
+    g.plen = P.plen;
+    g.tiles_x = P.tiles_x;
+    g.ntiles = P.ntiles;
+    g.reg = P.reg;
+    g.nent = nent;
+    g.invNp = P.invNp;
+    return g;
+}
+
+// work buffers of one item
+template <typename T>
+struct Work {
+    T* taps;          // [2][K][kp]: flipped PSF (B), PSF (B^T)
+    double* taps64;   // same taps in double (refinement path)
+    T* swp;           // [plen] sqrt(W) = m / sigma
+    const T* dpad;    // [plen] observed image (padded, global)
+    T* rimg;          // [plen] inner residual (image part)
+    T* qimg;          // [plen] sqrt(W) B L p, then u = B^T sqrt(W) r
+    T* P1;            // [plen] L p (zero frame)
+    T* P2;            // [plen] sqrt(W) r (zero frame)
+    const Entry<T>* E;
+    const Entry<double>* E64;  // FP64-weight copy (global) for the refinement
+    const int* inv;   // only for sub-pixel problems
+    const int* cst;
+    T* x;             // [ns] inner iterate (correction)
+    T* p;
+    T* s;
+    T* rreg;          // [nreg]
+    T* qreg;
+    double* x64;      // [ns] solution accumulator (refinement)
+    double* h64;      // [nreg] H x64
+    double* Pa;       // [plen] L x64
+    double* Pb;       // [plen] sqrt(W) r64
+    double* Pc;       // [plen] B^T sqrt(W) r64
+};
+
+// dst <- L v (Section 2.2: bilinear interpolation of the back-traced rays,
+// averaged over sub-pixels).  Only mapped pixels are written; the rest of
+// dst must hold zeros.
+template <typename T, typename ET, typename V, typename D>
+__device__ __forceinline__ void apply_L(const Geo<T>& g, const Entry<ET>* __restrict__ Ent, const int* __restrict__ inv,
+                                        const V* __restrict__ v, D* __restrict__ dst) {
+    if (g.Np == 1) {
+        for (int k = threadIdx.x; k < g.nent; k += blockDim.x) {
+            const Entry<ET> en = Ent[k];
+            const V u = (V)en.u, vv = (V)en.v;
+            const V* s0 = v + en.base;
+            dst[en.ppos] = (D)(((V)1 - vv) * (((V)1 - u) * s0[0] + u * s0[1]) +
+                               vv * (((V)1 - u) * s0[g.sx] + u * s0[g.sx + 1]));
+        }
+        return;
+    }
+    const int npix = g.nx * g.ny;
+    for (int j = threadIdx.x; j < npix; j += blockDim.x) {
+        V val = 0;
+        int pp = -1;
+        for (int a = 0; a < g.Np; ++a) {
+            const int e = inv[j * g.Np + a];
+            if (e >= 0) {
+                const Entry<ET> en = Ent[e];
+                const V u = (V)en.u, vv = (V)en.v;
+                const V* s0 = v + en.base;
+                val += ((V)1 - vv) * (((V)1 - u) * s0[0] + u * s0[1]) + vv * (((V)1 - u) * s0[g.sx] + u * s0[g.sx + 1]);
+                pp = en.ppos;
             }
         }
+        if (pp >= 0) dst[pp] = (D)(val * (V)g.invNp);
     }
 }
 
-// (L^T u)_i for source pixel i: gather over the rays of the (up to) four
-// cells that have i as a corner, in sorted (deterministic) order.
-template <typename T>
-__device__ __forceinline__ T apply_LT_at(const Prob<T>& P, const Work<T>& w, const T* __restrict__ U, int i,
-                                         int ia, int ib) {
-    T acc = 0;
+// (L^T U)_i: gather over the rays of the (up to) four cells having source
+// pixel (ia, ib) as a corner, in sorted (deterministic) order
+template <typename T, typename ET, typename V>
+__device__ __forceinline__ V apply_LT_at(const Geo<T>& g, const Entry<ET>* __restrict__ Ent,
+                                         const int* __restrict__ cst, const V* __restrict__ U, int ia, int ib) {
+    V acc = 0;
 #pragma unroll
     for (int dy = 0; dy < 2; ++dy) {
         const int iy0 = ib - dy;
-        if (iy0 < 0 || iy0 > P.sy - 2) continue;
+        if (iy0 < 0 || iy0 > g.sy - 2) continue;
 #pragma unroll
         for (int dx = 0; dx < 2; ++dx) {
             const int ix0 = ia - dx;
-            if (ix0 < 0 || ix0 > P.sx - 2) continue;
-            const int cell = iy0 * P.ncx + ix0;
-            const int k1 = w.cst[cell + 1];
-            for (int k = w.cst[cell]; k < k1; ++k) {
-                const Entry<T> en = w.E[k];
-                const T wu = dx ? en.u : (T)1 - en.u;
-                const T wv = dy ? en.v : (T)1 - en.v;
+            if (ix0 < 0 || ix0 > g.sx - 2) continue;
+            const int cell = iy0 * g.ncx + ix0;
+            const int k1 = cst[cell + 1];
+            for (int k = cst[cell]; k < k1; ++k) {
+                const Entry<ET> en = Ent[k];
+                const V wu = dx ? (V)en.u : (V)1 - (V)en.u;
+                const V wv = dy ? (V)en.v : (V)1 - (V)en.v;
                 acc += wu * wv * U[en.ppos];
             }
         }
     }
-    (void)i;
-    return acc * P.invNp;
+    return acc * (V)g.invNp;
 }
 
-// (H v) at row `row` of H (rows 0..ns-1, and ns..2ns-1 for Dy of the gradient)
-template <typename T>
-__device__ __forceinline__ T apply_H_row(const Prob<T>& P, const T* __restrict__ v, int row) {
-    if (P.reg == 0) return v[row];
-    if (P.reg == 2) {
-        const int ib = row / P.sx, ia = row - ib * P.sx;
-        T acc = (T)4 * v[row];
+// row `row` of H v (rows ns..2ns-1 are Dy for the gradient); zero beyond the grid
+template <typename T, typename V>
+__device__ __forceinline__ V apply_H_row(const Geo<T>& g, const V* __restrict__ v, int row) {
+    if (g.reg == 0) return v[row];
+    if (g.reg == 2) {
+        const int ib = row / g.sx, ia = row - ib * g.sx;
+        V acc = (V)4 * v[row];
         if (ia > 0) acc -= v[row - 1];
-        if (ia < P.sx - 1) acc -= v[row + 1];
-        if (ib > 0) acc -= v[row - P.sx];
-        if (ib < P.sy - 1) acc -= v[row + P.sx];
+        if (ia < g.sx - 1) acc -= v[row + 1];
+        if (ib > 0) acc -= v[row - g.sx];
+        if (ib < g.sy - 1) acc -= v[row + g.sx];
         return acc;
     }
-    // gradient: Dx rows then Dy rows, zero beyond the grid
-    if (row < P.ns) {
-        const int ib = row / P.sx, ia = row - ib * P.sx;
-        return (ia < P.sx - 1 ? v[row + 1] : (T)0) - v[row];
+    if (row < g.ns) {
+        const int ib = row / g.sx, ia = row - ib * g.sx;
+        (void)ib;
+        return (ia < g.sx - 1 ? v[row + 1] : (V)0) - v[row];
     }
-    const int i = row - P.ns;
-    const int ib = i / P.sx;
-    return (ib < P.sy - 1 ? v[i + P.sx] : (T)0) - v[i];
+    const int i = row - g.ns;
+    const int ib = i / g.sx;
+    return (ib < g.sy - 1 ? v[i + g.sx] : (V)0) - v[i];
 }
 
 // (H^T r)_i
-template <typename T>
-__device__ __forceinline__ T apply_HT_at(const Prob<T>& P, const T* __restrict__ r, int i, int ia, int ib) {
-    if (P.reg == 0) return r[i];
-    if (P.reg == 2) {  // symmetric
-        T acc = (T)4 * r[i];
+template <typename T, typename V>
+__device__ __forceinline__ V apply_HT_at(const Geo<T>& g, const V* __restrict__ r, int i, int ia, int ib) {
+    if (g.reg == 0) return r[i];
+    if (g.reg == 2) {
+        V acc = (V)4 * r[i];
         if (ia > 0) acc -= r[i - 1];
-        if (ia < P.sx - 1) acc -= r[i + 1];
-        if (ib > 0) acc -= r[i - P.sx];
-        if (ib < P.sy - 1) acc -= r[i + P.sx];
+        if (ia < g.sx - 1) acc -= r[i + 1];
+        if (ib > 0) acc -= r[i - g.sx];
+        if (ib < g.sy - 1) acc -= r[i + g.sx];
         return acc;
     }
-    // Dx^T rx: rx[i-1] (if ia > 0) - rx[i];  Dy^T ry: ry[i-sx] (if ib > 0) - ry[i]
-    const T* ry = r + P.ns;
-    T acc = -r[i] - ry[i];
+    const V* ry = r + g.ns;
+    V acc = -r[i] - ry[i];
     if (ia > 0) acc += r[i - 1];
-    if (ib > 0) acc += ry[i - P.sx];
+    if (ib > 0) acc += ry[i - g.sx];
     return acc;
 }
 
-// One convolution over all owned tiles with a mode-dependent epilogue (one
-// inlined copy of the unrolled tile code per kernel):
-//   CONV_Q   : dst = sqrt(W) * conv                 returns sum dst^2
-//   CONV_RAW : dst = conv
-//   CONV_RES : res = sqrt(W) d - sqrt(W) * conv; rimg = res; P2 = sqrt(W) res
-//              returns sum res^2  (per-pixel terms in FP64)
-enum : int { CONV_Q = 0, CONV_RAW = 1, CONV_RES = 2 };
+// 4-wide vector helpers for one tile row (float: one 16-byte access;
+// double: two)
+template <typename T>
+struct V4 {
+    T v[4];
+};
+template <typename T>
+__device__ __forceinline__ V4<T> ld4(const T* p) {
+    V4<T> o;
+    vload(p, o.v);
+    if (sizeof(T) == 8) vload(p + 2, o.v + 2);
+    return o;
+}
+__device__ __forceinline__ void st4(float* p, const V4<float>& o) {
+    *reinterpret_cast<float4*>(p) = make_float4(o.v[0], o.v[1], o.v[2], o.v[3]);
+}
+__device__ __forceinline__ void st4(double* p, const V4<double>& o) {
+    *reinterpret_cast<double2*>(p) = make_double2(o.v[0], o.v[1]);
+    *reinterpret_cast<double2*>(p + 2) = make_double2(o.v[2], o.v[3]);
+}
 
+enum : int { CONV_Q = 0, CONV_RAW = 1 };
+
+// One convolution over all owned tiles (one non-inlined copy of the
+// unrolled tile code per kernel):
+//   CONV_Q   : dst = sqrt(W) * conv, returns sum dst^2
+//   CONV_RAW : dst = conv
 template <typename T, int K, bool SH>
-__device__ __noinline__ double conv_pass(const Prob<T>& P, const Work<T>& w, const T* __restrict__ src,
-                                         const T* __restrict__ taps, T* __restrict__ dst,
-                                         const T* __restrict__ bwp, int mode) {
+__device__ __noinline__ double conv_pass(const T* __restrict__ src, const T* __restrict__ taps,
+                                         const T* __restrict__ swp, T* __restrict__ dst, Geo<T> g, int mode) {
     T ss = 0;
-    double sd = 0;
-    for (int t = threadIdx.x; t < P.ntiles; t += blockDim.x) {
-        const int ty = t / P.tiles_x, tx = t - ty * P.tiles_x;
+    for (int t = threadIdx.x; t < g.ntiles; t += blockDim.x) {
+        const int ty = t / g.tiles_x, tx = t - ty * g.tiles_x;
         T acc[TILE][TILE];
-        conv_any<T, K, SH>(src + (ty * TILE) * P.Wp + tx * TILE, P.Wp, taps, P.K, P.kp, acc);
+        const T* base = src + (ty * TILE) * g.Wp + tx * TILE;
+        if constexpr (K > 0)
+            conv_tile<T, K, SH>(base, g.Wp, taps, acc);
+        else
+            conv_tile_rt<T, T>(base, g.Wp, taps, g.K, g.kp, g.sh, acc);
 #pragma unroll
         for (int r = 0; r < TILE; ++r) {
-            const int pp = (ty * TILE + r + P.hk) * P.Wp + tx * TILE + P.hk;
+            const int pp = (ty * TILE + r + g.hk) * g.Wp + tx * TILE + g.xoff;
+            V4<T> o;
+            if (mode == CONV_Q) {
+                const V4<T> sw = ld4(swp + pp);
 #pragma unroll
-            for (int cc = 0; cc < TILE; ++cc) {
-                if (mode == CONV_Q) {
-                    const T q = w.swp[pp + cc] * acc[r][cc];
-                    dst[pp + cc] = q;
-                    ss = fma(q, q, ss);
-                } else if (mode == CONV_RAW) {
-                    dst[pp + cc] = acc[r][cc];
+                for (int c = 0; c < 4; ++c) {
+                    o.v[c] = sw.v[c] * acc[r][c];
+                    ss = fma(o.v[c], o.v[c], ss);
+                }
+            } else {
+#pragma unroll
+                for (int c = 0; c < 4; ++c) o.v[c] = acc[r][c];
+            }
+            st4(dst + pp, o);
+        }
+    }
+    return (double)ss;
+}
+
+// FP64 convolution pass of the refinement:
+//   mode 0: res = sqrt(W)(d - conv(Pa)); rimg = (T)res; Pb = sqrt(W) res; returns sum res^2
+//   mode 1: Pc = conv(Pb)
+template <typename T>
+__device__ __noinline__ double conv64_pass(const Work<T> w, Geo<T> g, int mode) {
+    double ss = 0;
+    const double* src = mode == 0 ? w.Pa : w.Pb;
+    const double* taps = w.taps64 + (mode == 0 ? 0 : g.K * g.kp);
+    for (int t = threadIdx.x; t < g.ntiles; t += blockDim.x) {
+        const int ty = t / g.tiles_x, tx = t - ty * g.tiles_x;
+        double acc[TILE][TILE];
+        conv_tile_rt<double, double>(src + (ty * TILE) * g.Wp + tx * TILE, g.Wp, taps, g.K, g.kp, g.sh, acc);
+#pragma unroll
+        for (int r = 0; r < TILE; ++r) {
+            const int pp = (ty * TILE + r + g.hk) * g.Wp + tx * TILE + g.xoff;
+#pragma unroll
+            for (int c = 0; c < TILE; ++c) {
+                if (mode == 0) {
+                    const double sw = (double)w.swp[pp + c];
+                    const double res = sw * ((double)w.dpad[pp + c] - acc[r][c]);
+                    w.rimg[pp + c] = (T)res;
+                    w.Pb[pp + c] = sw * res;
+                    ss += res * res;
                 } else {
-                    const T sw = w.swp[pp + cc];
-                    const T res = bwp[pp + cc] - sw * acc[r][cc];
-                    w.rimg[pp + cc] = res;
-                    w.P2[pp + cc] = sw * res;
-                    sd += (double)res * (double)res;
+                    w.Pc[pp + c] = acc[r][c];
                 }
             }
         }
     }
-    return (double)ss + sd;
+    return ss;
 }
 
-// s = A~^T r = L^T B^T (sqrt(W) r_img) + sqrt(lam) H^T r_reg, given
-// P2 = sqrt(W) r_img already in place.  Returns ||s||^2 (block-reduced).
-template <typename T, int K, bool SH>
-__device__ __forceinline__ double normal_residual(const Prob<T>& P, const Work<T>& w, T sl, bool with_reg,
-                                                  double* red, int& which) {
-    __syncthreads();  // P2 complete
-    conv_pass<T, K, SH>(P, w, w.P2, w.taps + P.K * P.kp, w.qimg, nullptr, CONV_RAW);
-    __syncthreads();  // u complete
-    T ss = 0;  // per-thread partial in T, cross-thread sum in FP64
-    for (int i = threadIdx.x; i < P.ns; i += blockDim.x) {
-        const int ib = i / P.sx, ia = i - ib * P.sx;
-        T v = apply_LT_at(P, w, w.qimg, i, ia, ib);
-        if (with_reg) v += sl * apply_HT_at(P, w.rreg, i, ia, ib);
-        w.s[i] = v;
-        ss = fma(v, v, ss);
+// FP64 residual of the current solution x64 (the refinement step):
+//   r = [sqrt(W)(d - B L x64); -sqrt(lam) H x64],  s = A~^T r = rhs - A x64.
+// Writes the inner-solve start: rimg, rreg, s (type T).  Returns chi2 =
+// ||r_img||^2 and sets reg2 = ||H x64||^2 and g64 = ||s||^2.
+template <typename T>
+__device__ __forceinline__ double residual64(const Work<T>& w, const Geo<T>& g, double lam, double* red,
+                                             int& which, double& reg2, double& g64) {
+    apply_L<T, double, double, double>(g, w.E64, w.inv, w.x64, w.Pa);
+    const double sl = sqrt(lam);
+    double rg = 0;
+    for (int i = threadIdx.x; i < g.nreg; i += blockDim.x) {
+        const double h = apply_H_row<T, double>(g, w.x64, i);
+        w.h64[i] = h;
+        w.rreg[i] = (T)(-sl * h);
+        rg += h * h;
     }
-    const double r = block_sum((double)ss, red, which);
-    which ^= 1;
-    return r;
-}
-
-// r_img = sqrt(W)(d - B L x), r_reg = -sqrt(lam) H x; returns chi2 = ||r_img||^2.
-// Leaves P2 = sqrt(W) r_img (no trailing barrier).
-template <typename T, int K, bool SH>
-__device__ __forceinline__ double true_residual(const Prob<T>& P, const Work<T>& w, const T* __restrict__ bwp,
-                                                T sl, double* red, int& which) {
-    apply_L(P, w, w.x);
-    for (int i = threadIdx.x; i < P.nreg; i += blockDim.x) w.rreg[i] = -sl * apply_H_row(P, w.x, i);
     __syncthreads();
-    const double chi = conv_pass<T, K, SH>(P, w, w.P1, w.taps, nullptr, bwp, CONV_RES);
-    const double c = block_sum(chi, red, which);
+    const double chi2 = block_sum(conv64_pass<T>(w, g, 0), red, which);
     which ^= 1;
-    return c;
+    conv64_pass<T>(w, g, 1);
+    __syncthreads();
+    double ss = 0;
+    for (int i = threadIdx.x; i < g.ns; i += blockDim.x) {
+        const int ib = i / g.sx, ia = i - ib * g.sx;
+        const double v = apply_LT_at<T, double, double>(g, w.E64, w.cst, w.Pc, ia, ib) -
+                         lam * apply_HT_at<T, double>(g, w.h64, i, ia, ib);
+        w.s[i] = (T)v;
+        ss += v * v;
+    }
+    g64 = block_sum(ss, red, which);
+    which ^= 1;
+    reg2 = block_sum(rg, red, which);
+    which ^= 1;
+    return chi2;
 }
 
 // ---------------------------------------------------------------------------
-// k_cgls: persistent CTAs, one (candidate, lambda) item at a time
+// k_cgls: persistent CTAs, one (candidate, lambda) item at a time.
+// Each item solves min ||sqrt(W)(B L s - d)||^2 + lam ||H s||^2 by
+// iterative refinement: an FP64 residual r = b~ - A~ x (Eq. chi2 and the
+// regulariser of Eq. TKReg, with x the FP64 solution), then CGLS in type T
+// on A~ dx = r (inner solve, Section 2.2 / 2.4 CGLS started from a blank
+// correction), x += dx; until ||A~^T r|| <= tol ||A~^T b~||.  In T = double
+// contexts the first inner solve normally reaches the tolerance.
 // ---------------------------------------------------------------------------
 template <typename T>
 __host__ __device__ inline size_t align_up(size_t v, size_t a) {
     return (v + a - 1) / a * a;
 }
 
-// Shared-memory footprint of the SMEM-resident layout of one problem.
+// Shared-memory footprint of one problem (big = work buffers in global memory).
 template <typename T>
 __host__ __device__ inline size_t smem_bytes(const Prob<T>& P, bool big) {
-    size_t o = 0;
-    o += align_up<T>(sizeof(T) * 2 * P.K * P.kp, 16);  // taps
-    o += 2 * 33 * sizeof(double) + 16;                  // reductions + item slot
+    size_t o = 16 + 2 * 33 * sizeof(double);                       // item slot + reductions
+    o += align_up<T>(sizeof(T) * 2 * P.K * P.kp, 16);              // taps
+    o += align_up<T>(sizeof(double) * 2 * P.K * P.kp, 16);         // taps64
     if (!big) {
         o += 5 * align_up<T>(sizeof(T) * P.plen, 16);                  // swp rimg qimg P1 P2
         o += align_up<T>(sizeof(Entry<T>) * (size_t)P.nrays, 16);      // E
-        o += align_up<T>(sizeof(int) * (size_t)P.nrays, 16);           // inv
+        if (P.Np > 1) o += align_up<T>(sizeof(int) * (size_t)P.nrays, 16);  // inv
         o += align_up<T>(sizeof(int) * (size_t)(P.ncells + 1), 16);    // cst
         o += 3 * align_up<T>(sizeof(T) * P.ns, 16);                    // x p s
         o += 2 * align_up<T>(sizeof(T) * P.nreg, 16);                  // rreg qreg
@@ -673,27 +805,25 @@ __host__ __device__ inline size_t smem_bytes(const Prob<T>& P, bool big) {
     return o;
 }
 
+// per-CTA global slab: [double part][T part (big only)], in bytes
 template <typename T>
-__host__ __device__ inline size_t slab_elems(const Prob<T>& P) {
-    // BIG variant: rimg qimg P1 P2 + x p s + rreg qreg in global memory
-    return 4 * align_up<T>(P.plen, 4) + 3 * align_up<T>(P.ns, 4) + 2 * align_up<T>(P.nreg, 4);
+__host__ __device__ inline size_t slab_bytes(const Prob<T>& P, bool big) {
+    size_t o = sizeof(double) * (3 * align_up<T>(P.plen, 4) + align_up<T>(P.ns, 4) + align_up<T>(P.nreg, 4));
+    if (big) o += sizeof(T) * (4 * align_up<T>(P.plen, 4) + 3 * align_up<T>(P.ns, 4) + 2 * align_up<T>(P.nreg, 4));
+    return align_up<T>(o, 256);
 }
 
 template <typename T, int K, bool BIG>
 __global__ void __launch_bounds__(NTHREADS, 1) k_cgls(CglsArgs<T> A) {
     extern __shared__ __align__(16) unsigned char smem[];
+    constexpr bool SH = !BIG;
     const int tid = threadIdx.x, bs = blockDim.x;
-    int last_c = -1, last_prob = -1;
-    Work<T> w;
+    int last_c = -1;
     int which = 0;
+    int* slot = reinterpret_cast<int*>(smem);
+    double* red = reinterpret_cast<double*>(smem + 16);
 
     while (true) {
-        unsigned char* sp = smem;
-        const Prob<T>* Pp;
-        // --- fetch the next item
-        int* slot = reinterpret_cast<int*>(smem + 0);
-        // carve: item slot (16 B) first so it never moves
-        sp += 16;
         __syncthreads();
         if (tid == 0) slot[0] = atomicAdd(A.counter, 1);
         __syncthreads();
@@ -701,24 +831,37 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_cgls(CglsArgs<T> A) {
         if (it_idx >= A.n_items) break;
         const int packed = A.items[it_idx];
         const int c = packed / MAX_LAM, k = packed - c * MAX_LAM;
-        const int pi = A.cand_prob[c];
-        Pp = A.probs + pi;
-        const Prob<T> P = *Pp;
-
-        double* red = reinterpret_cast<double*>(sp);
-        sp += 2 * 33 * sizeof(double);
-        w.taps = reinterpret_cast<T*>(sp);
-        sp += align_up<T>(sizeof(T) * 2 * P.K * P.kp, 16);
-
+        const Prob<T>& P = A.probs[A.cand_prob[c]];
         const CandScratch<T>& cs = A.cs;
+        const int nent = cs.nent[c];
+        const Geo<T> g = geo_of(P, nent);
+
+        // ---- carve buffers
+        Work<T> w;
+        unsigned char* sp = smem + 16 + 2 * 33 * sizeof(double);
+        w.taps = reinterpret_cast<T*>(sp);
+        sp += align_up<T>(sizeof(T) * 2 * g.K * g.kp, 16);
+        w.taps64 = reinterpret_cast<double*>(sp);
+        sp += align_up<T>(sizeof(double) * 2 * g.K * g.kp, 16);
         const T* g_swp = cs.swp + (long long)c * cs.sPad;
-        const T* g_bwp = cs.bwp + (long long)c * cs.sPad;
+        w.dpad = cs.dpad + (long long)c * cs.sPad;
         const Entry<T>* g_E = cs.E + (long long)c * cs.sE;
+        w.E64 = cs.E64 + (long long)c * cs.sE;
         const int* g_inv = cs.inv + (long long)c * cs.sInv;
         const int* g_cst = cs.cst + (long long)c * cs.sCst;
-
+        unsigned char* slab = reinterpret_cast<unsigned char*>(A.slab) + (long long)blockIdx.x * A.slab_stride;
+        w.Pa = reinterpret_cast<double*>(slab);
+        slab += sizeof(double) * align_up<T>(g.plen, 4);
+        w.Pb = reinterpret_cast<double*>(slab);
+        slab += sizeof(double) * align_up<T>(g.plen, 4);
+        w.Pc = reinterpret_cast<double*>(slab);
+        slab += sizeof(double) * align_up<T>(g.plen, 4);
+        w.x64 = reinterpret_cast<double*>(slab);
+        slab += sizeof(double) * align_up<T>(g.ns, 4);
+        w.h64 = reinterpret_cast<double*>(slab);
+        slab += sizeof(double) * align_up<T>(g.nreg, 4);
         if constexpr (!BIG) {
-            const size_t pl = align_up<T>(sizeof(T) * P.plen, 16);
+            const size_t pl = align_up<T>(sizeof(T) * g.plen, 16);
             w.swp = reinterpret_cast<T*>(sp); sp += pl;
             w.rimg = reinterpret_cast<T*>(sp); sp += pl;
             w.qimg = reinterpret_cast<T*>(sp); sp += pl;
@@ -726,12 +869,15 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_cgls(CglsArgs<T> A) {
             w.P2 = reinterpret_cast<T*>(sp); sp += pl;
             Entry<T>* sE = reinterpret_cast<Entry<T>*>(sp);
             sp += align_up<T>(sizeof(Entry<T>) * (size_t)P.nrays, 16);
-            int* sInv = reinterpret_cast<int*>(sp);
-            sp += align_up<T>(sizeof(int) * (size_t)P.nrays, 16);
+            int* sInv = nullptr;
+            if (g.Np > 1) {
+                sInv = reinterpret_cast<int*>(sp);
+                sp += align_up<T>(sizeof(int) * (size_t)P.nrays, 16);
+            }
             int* sCst = reinterpret_cast<int*>(sp);
             sp += align_up<T>(sizeof(int) * (size_t)(P.ncells + 1), 16);
-            const size_t ps = align_up<T>(sizeof(T) * P.ns, 16);
-            const size_t pr = align_up<T>(sizeof(T) * P.nreg, 16);
+            const size_t ps = align_up<T>(sizeof(T) * g.ns, 16);
+            const size_t pr = align_up<T>(sizeof(T) * g.nreg, 16);
             w.x = reinterpret_cast<T*>(sp); sp += ps;
             w.p = reinterpret_cast<T*>(sp); sp += ps;
             w.s = reinterpret_cast<T*>(sp); sp += ps;
@@ -742,52 +888,54 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_cgls(CglsArgs<T> A) {
             w.cst = sCst;
             if (c != last_c) {
                 // stage the candidate's lens operator and weights in shared memory
-                const int ne = A.cs.nent[c];
-                for (int i = tid; i < ne; i += bs) sE[i] = g_E[i];
-                for (int i = tid; i < P.nrays; i += bs) sInv[i] = g_inv[i];
+                for (int i = tid; i < nent; i += bs) sE[i] = g_E[i];
+                if (g.Np > 1)
+                    for (int i = tid; i < P.nrays; i += bs) sInv[i] = g_inv[i];
                 for (int i = tid; i <= P.ncells; i += bs) sCst[i] = g_cst[i];
-                for (int i = tid; i < P.plen; i += bs) w.swp[i] = g_swp[i];
+                for (int i = tid; i < g.plen; i += bs) w.swp[i] = g_swp[i];
             }
         } else {
-            T* slab = A.slab + (long long)blockIdx.x * A.slab_stride;
-            const size_t pl = align_up<T>(P.plen, 4);
-            w.rimg = slab; slab += pl;
-            w.qimg = slab; slab += pl;
-            w.P1 = slab; slab += pl;
-            w.P2 = slab; slab += pl;
-            w.x = slab; slab += align_up<T>(P.ns, 4);
-            w.p = slab; slab += align_up<T>(P.ns, 4);
-            w.s = slab; slab += align_up<T>(P.ns, 4);
-            w.rreg = slab; slab += align_up<T>(P.nreg, 4);
-            w.qreg = slab; slab += align_up<T>(P.nreg, 4);
+            T* ts = reinterpret_cast<T*>(slab);
+            const size_t pl = align_up<T>(g.plen, 4);
+            w.rimg = ts; ts += pl;
+            w.qimg = ts; ts += pl;
+            w.P1 = ts; ts += pl;
+            w.P2 = ts; ts += pl;
+            w.x = ts; ts += align_up<T>(g.ns, 4);
+            w.p = ts; ts += align_up<T>(g.ns, 4);
+            w.s = ts; ts += align_up<T>(g.ns, 4);
+            w.rreg = ts; ts += align_up<T>(g.nreg, 4);
+            w.qreg = ts; ts += align_up<T>(g.nreg, 4);
             w.swp = const_cast<T*>(g_swp);
             w.E = g_E;
             w.inv = g_inv;
             w.cst = g_cst;
         }
-        if (pi != last_prob || c != last_c) {
+        if (c != last_c) {
             // taps: [0] flipped PSF for B, [1] PSF for B^T; rows padded to kp
-            for (int i = tid; i < 2 * P.K * P.kp; i += bs) {
-                const int h = i / (P.K * P.kp), rem = i - h * P.K * P.kp;
-                const int a = rem / P.kp, b = rem - a * P.kp;
+            for (int i = tid; i < 2 * g.K * g.kp; i += bs) {
+                const int h = i / (g.K * g.kp), rem = i - h * g.K * g.kp;
+                const int a = rem / g.kp, b = rem - a * g.kp;
                 T v = 0;
-                if (b < P.K) v = h == 0 ? P.psf[(P.K - 1 - a) * P.K + (P.K - 1 - b)] : P.psf[a * P.K + b];
+                if (b < g.K) v = h == 0 ? P.psf[(g.K - 1 - a) * g.K + (g.K - 1 - b)] : P.psf[a * g.K + b];
                 w.taps[i] = v;
+                w.taps64[i] = (double)v;
             }
         }
         last_c = c;
-        last_prob = pi;
-        for (int i = tid; i < P.plen; i += bs) {
+        for (int i = tid; i < g.plen; i += bs) {
             w.P1[i] = 0;
             w.P2[i] = 0;
+            w.Pa[i] = 0;
+            w.Pb[i] = 0;
         }
         __syncthreads();
 
-        const int cstat = A.cs.cstat[c];
+        const int cstat = cs.cstat[c];
         const long long ok = (long long)c * A.max_lam + k;
         T* X = A.X + ok * A.max_ns;
         if (cstat & (ST_BADPARAM | ST_EMPTY)) {
-            for (int i = tid; i < P.ns; i += bs) X[i] = 0;
+            for (int i = tid; i < g.ns; i += bs) X[i] = 0;
             if (tid == 0) {
                 A.chi2[ok] = (cstat & ST_BADPARAM) ? __longlong_as_double(0x7ff0000000000000LL) : 0.0;
                 A.reg[ok] = 0.0;
@@ -800,125 +948,176 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_cgls(CglsArgs<T> A) {
 
         const double lam = A.lambdas[(long long)c * A.max_lam + k];
         const T sl = (T)sqrt(lam);
-        const int maxit = A.maxit > 0 ? A.maxit : 10 * P.ns;
-        const int rep = A.replace_every > 0 ? A.replace_every : 50;
+        const int maxit = A.maxit > 0 ? A.maxit : 25 * g.ns;
 
-        // ||rhs|| = ||L^T B^T sqrt(W) (sqrt(W) d)||
-        for (int t = tid; t < P.ntiles; t += bs) {
-            const int ty = t / P.tiles_x, tx = t - ty * P.tiles_x;
+        // ---- ||rhs|| = ||L^T B^T W d|| in FP64 (Pb = sqrt(W) sqrt(W) d)
+        for (int t = tid; t < g.ntiles; t += bs) {
+            const int ty = t / g.tiles_x, tx = t - ty * g.tiles_x;
 #pragma unroll
             for (int r = 0; r < TILE; ++r) {
-                const int pp = (ty * TILE + r + P.hk) * P.Wp + tx * TILE + P.hk;
+                const int pp = (ty * TILE + r + g.hk) * g.Wp + tx * TILE + g.xoff;
 #pragma unroll
-                for (int cc = 0; cc < TILE; ++cc) w.P2[pp + cc] = w.swp[pp + cc] * g_bwp[pp + cc];
+                for (int cc = 0; cc < TILE; ++cc) {
+                    const double sw = (double)w.swp[pp + cc];
+                    w.Pb[pp + cc] = sw * sw * (double)w.dpad[pp + cc];
+                }
             }
         }
-        const double rhs2 = normal_residual<T, K, !BIG>(P, w, sl, false, red, which);
-        const double rhsn = sqrt(rhs2);
+        __syncthreads();
+        conv64_pass<T>(w, g, 1);
+        __syncthreads();
+        double rs = 0;
+        for (int i = tid; i < g.ns; i += bs) {
+            const int ib = i / g.sx, ia = i - ib * g.sx;
+            const double v = apply_LT_at<T, double, double>(g, w.E64, w.cst, w.Pc, ia, ib);
+            rs += v * v;
+        }
+        const double rhsn = sqrt(block_sum(rs, red, which));
+        which ^= 1;
 
-        double gam;
+        // ---- starting point
         if (A.warm_x) {
             const T* x0 = A.warm_x + ok * A.max_ns;
-            for (int i = tid; i < P.ns; i += bs) w.x[i] = x0[i];
-            __syncthreads();
-            true_residual<T, K, !BIG>(P, w, g_bwp, sl, red, which);
-            gam = normal_residual<T, K, !BIG>(P, w, sl, true, red, which);
+            for (int i = tid; i < g.ns; i += bs) w.x64[i] = (double)x0[i];
         } else {
-            // x = 0: r_img = sqrt(W) d, r_reg = 0, s = rhs (already in w.s)
-            for (int i = tid; i < P.ns; i += bs) w.x[i] = 0;
-            for (int i = tid; i < P.nreg; i += bs) w.rreg[i] = 0;
-            for (int i = tid; i < P.plen; i += bs) w.rimg[i] = g_bwp[i];
-            gam = rhs2;
+            for (int i = tid; i < g.ns; i += bs) w.x64[i] = 0.0;
         }
-        for (int i = tid; i < P.ns; i += bs) w.p[i] = w.s[i];
         __syncthreads();
 
-        int status = 0, it = 0;
-        double best = (rhsn > 0) ? sqrt(gam) / rhsn : 0.0;
-        int best_it = 0;
-        const int stag_window = max(2000, P.ns);
-        for (it = 0;; ++it) {
-            if (!isfinite(gam)) {
+        int status = 0, total_it = 0, slow = 0;
+        double chi2 = 0, reg2 = 0, g64 = 0, rel64 = 0, prev_rel = 1e300;
+        constexpr int MAX_OUTER = 16;
+        // inner target: a 30x reduction per FP32 inner solve keeps each inner
+        // solve short (FP32 loses orthogonality on long ones) at few FP64 passes
+        const double eta_min = sizeof(T) == 4 ? 0.03 : 0.3 * A.tol;
+        for (int outer = 0;; ++outer) {
+            chi2 = residual64<T>(w, g, lam, red, which, reg2, g64);
+            rel64 = rhsn > 0 ? sqrt(g64) / rhsn : 0.0;
+            if (!isfinite(rel64)) {
                 status |= ST_BREAK;
                 break;
             }
-            const double rel = (rhsn > 0) ? sqrt(gam) / rhsn : 0.0;
-            if (!(rel > A.tol)) break;  // converged (or rhs = 0)
-            if (it >= maxit) {
+            if (!(rel64 > A.tol)) break;  // converged (or rhs = 0)
+            if (total_it >= maxit || outer >= MAX_OUTER) {
                 status |= ST_MAXIT;
                 break;
             }
-            if (rel < 0.5 * best) {
-                best = rel;
-                best_it = it;
-            } else if (it - best_it > stag_window) {
+            // two refinement steps in a row that gain less than 10% each: stop
+            slow = (outer > 0 && rel64 > 0.9 * prev_rel) ? slow + 1 : 0;
+            if (slow >= 2) {
                 status |= ST_STAG;
                 break;
             }
-            // q = A~ p: image part sqrt(W) B L p, regulariser part sqrt(lam) H p
-            apply_L(P, w, w.p);
-            T dqr = 0;
-            for (int i = tid; i < P.nreg; i += bs) {
-                const T q = sl * apply_H_row(P, w.p, i);
-                w.qreg[i] = q;
-                dqr = fma(q, q, dqr);
+            prev_rel = rel64;
+            // ---- inner CGLS on the correction, started from zero
+            const double target = fmax(eta_min, 0.3 * A.tol / rel64);
+            for (int i = tid; i < g.ns; i += bs) {
+                w.x[i] = 0;
+                w.p[i] = w.s[i];
             }
-            __syncthreads();
-            const double dq = (double)dqr + conv_pass<T, K, !BIG>(P, w, w.P1, w.taps, w.qimg, nullptr, CONV_Q);
-            const double delta = block_sum(dq, red, which);
-            which ^= 1;
-            if (!(delta > 0.0) || !isfinite(delta)) {
-                status |= ST_BREAK;
-                break;
+            for (int t = tid; t < g.ntiles; t += bs) {
+                const int ty = t / g.tiles_x, tx = t - ty * g.tiles_x;
+#pragma unroll
+                for (int r = 0; r < TILE; ++r) {
+                    const int pp = (ty * TILE + r + g.hk) * g.Wp + tx * TILE + g.xoff;
+                    const V4<T> rv = ld4(w.rimg + pp), sw = ld4(w.swp + pp);
+                    V4<T> o;
+#pragma unroll
+                    for (int cc = 0; cc < 4; ++cc) o.v[cc] = sw.v[cc] * rv.v[cc];
+                    st4(w.P2 + pp, o);
+                }
             }
-            const double alpha = gam / delta;
-            const T a = (T)alpha;
-            for (int i = tid; i < P.ns; i += bs) w.x[i] = fma(a, w.p[i], w.x[i]);
-            for (int i = tid; i < P.nreg; i += bs) w.rreg[i] = fma(-a, w.qreg[i], w.rreg[i]);
-            const bool replace = ((it + 1) % rep) == 0;
-            if (!replace) {
-                for (int t = tid; t < P.ntiles; t += bs) {
-                    const int ty = t / P.tiles_x, tx = t - ty * P.tiles_x;
+            double gam = 0;
+            {
+                T gs = 0;
+                for (int i = tid; i < g.ns; i += bs) gs = fma(w.s[i], w.s[i], gs);
+                gam = block_sum((double)gs, red, which);
+                which ^= 1;
+            }
+            const double g0 = gam;
+            double best = 1.0;
+            int best_it = 0;
+            const int stag_window = max(4000, 2 * g.ns);
+            for (int it = 0;; ++it) {
+                if (!isfinite(gam)) {
+                    status |= ST_BREAK;
+                    break;
+                }
+                const double rel = sqrt(gam / g0);
+                if (!(rel > target)) break;
+                if (total_it >= maxit) break;
+                if (rel < 0.5 * best) {
+                    best = rel;
+                    best_it = it;
+                } else if (it - best_it > stag_window) {
+                    break;
+                }
+                ++total_it;
+                // q = A~ p: image part sqrt(W) B L p, regulariser part sqrt(lam) H p
+                apply_L<T, T, T, T>(g, w.E, w.inv, w.p, w.P1);
+                T dqr = 0;
+                for (int i = tid; i < g.nreg; i += bs) {
+                    const T q = sl * apply_H_row<T, T>(g, w.p, i);
+                    w.qreg[i] = q;
+                    dqr = fma(q, q, dqr);
+                }
+                __syncthreads();
+                const double dq = (double)dqr + conv_pass<T, K, SH>(w.P1, w.taps, w.swp, w.qimg, g, CONV_Q);
+                const double delta = block_sum(dq, red, which);
+                which ^= 1;
+                if (!(delta > 0.0) || !isfinite(delta)) {
+                    status |= ST_BREAK;
+                    break;
+                }
+                const T a = (T)(gam / delta);
+                for (int i = tid; i < g.ns; i += bs) w.x[i] = fma(a, w.p[i], w.x[i]);
+                for (int i = tid; i < g.nreg; i += bs) w.rreg[i] = fma(-a, w.qreg[i], w.rreg[i]);
+                for (int t = tid; t < g.ntiles; t += bs) {
+                    const int ty = t / g.tiles_x, tx = t - ty * g.tiles_x;
 #pragma unroll
                     for (int r = 0; r < TILE; ++r) {
-                        const int pp = (ty * TILE + r + P.hk) * P.Wp + tx * TILE + P.hk;
+                        const int pp = (ty * TILE + r + g.hk) * g.Wp + tx * TILE + g.xoff;
+                        V4<T> rv = ld4(w.rimg + pp);
+                        const V4<T> qv = ld4(w.qimg + pp), sw = ld4(w.swp + pp);
+                        V4<T> o;
 #pragma unroll
-                        for (int cc = 0; cc < TILE; ++cc) {
-                            const T rv = fma(-a, w.qimg[pp + cc], w.rimg[pp + cc]);
-                            w.rimg[pp + cc] = rv;
-                            w.P2[pp + cc] = w.swp[pp + cc] * rv;
+                        for (int cc = 0; cc < 4; ++cc) {
+                            rv.v[cc] = fma(-a, qv.v[cc], rv.v[cc]);
+                            o.v[cc] = sw.v[cc] * rv.v[cc];
                         }
+                        st4(w.rimg + pp, rv);
+                        st4(w.P2 + pp, o);
                     }
                 }
-            } else {
-                __syncthreads();  // x complete
-                true_residual<T, K, !BIG>(P, w, g_bwp, sl, red, which);
+                __syncthreads();  // P2 complete
+                conv_pass<T, K, SH>(w.P2, w.taps + g.K * g.kp, nullptr, w.qimg, g, CONV_RAW);
+                __syncthreads();  // u complete
+                T gs = 0;
+                for (int i = tid; i < g.ns; i += bs) {
+                    const int ib = i / g.sx, ia = i - ib * g.sx;
+                    const T v = apply_LT_at<T, T, T>(g, w.E, w.cst, w.qimg, ia, ib) +
+                                sl * apply_HT_at<T, T>(g, w.rreg, i, ia, ib);
+                    w.s[i] = v;
+                    gs = fma(v, v, gs);
+                }
+                const double gnew = block_sum((double)gs, red, which);
+                which ^= 1;
+                const T bt = (T)(gnew / gam);
+                gam = gnew;
+                for (int i = tid; i < g.ns; i += bs) w.p[i] = fma(bt, w.p[i], w.s[i]);
+                __syncthreads();
             }
-            const double gnew = normal_residual<T, K, !BIG>(P, w, sl, true, red, which);
-            const double beta = gnew / gam;
-            gam = gnew;
-            const T bt = (T)beta;
-            for (int i = tid; i < P.ns; i += bs) w.p[i] = fma(bt, w.p[i], w.s[i]);
+            if (status & ST_BREAK) break;
+            for (int i = tid; i < g.ns; i += bs) w.x64[i] += (double)w.x[i];
             __syncthreads();
         }
 
-        // outputs: chi2 from the true residual, ||H x||^2, true relative residual
-        __syncthreads();
-        const double chi2 = true_residual<T, K, !BIG>(P, w, g_bwp, sl, red, which);
-        double hx = 0;
-        for (int i = tid; i < P.nreg; i += bs) {
-            const double v = (double)apply_H_row(P, w.x, i);
-            hx += v * v;
-        }
-        const double reg2 = block_sum(hx, red, which);
-        which ^= 1;
-        const double tr = normal_residual<T, K, !BIG>(P, w, sl, true, red, which);
-        for (int i = tid; i < P.ns; i += bs) X[i] = w.x[i];
+        for (int i = tid; i < g.ns; i += bs) X[i] = (T)w.x64[i];
         if (tid == 0) {
             A.chi2[ok] = chi2;
             A.reg[ok] = reg2;
-            A.iters[ok] = it;
-            if (A.relres) A.relres[ok] = rhsn > 0 ? sqrt(tr) / rhsn : 0.0;
+            A.iters[ok] = total_it;
+            if (A.relres) A.relres[ok] = rel64;
             if (A.istat) A.istat[ok] = status | cstat;
         }
     }
@@ -1055,8 +1254,9 @@ __global__ void k_lcurve(const double* __restrict__ chi2, const double* __restri
 }
 
 // ---------------------------------------------------------------------------
-// k_forward: model = B L s and chi2 for a batch of sources at one lens
-// (candidate scratch of index 0).  One CTA per source (grid-stride).
+// k_forward: model = B L s and Eq. chi2 for a batch of sources at one lens
+// (candidate scratch of index 0).  One CTA per source (grid-stride); the
+// L s image lives in a per-CTA global slab.
 // ---------------------------------------------------------------------------
 template <typename T, int K>
 __global__ void __launch_bounds__(NTHREADS, 1) k_forward(const Prob<T>* __restrict__ probs, CandScratch<T> cs,
@@ -1064,27 +1264,21 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_forward(const Prob<T>* __restri
                                                          double* chi2, T* slab, long long slab_stride,
                                                          int* status) {
     extern __shared__ __align__(16) unsigned char smem[];
-    const Prob<T> P = probs[0];
-    unsigned char* sp = smem;
-    double* red = reinterpret_cast<double*>(sp);
-    sp += 2 * 33 * sizeof(double) + 16;
+    const Prob<T>& P = probs[0];
+    const Geo<T> g = geo_of(P, cs.nent[0]);
+    double* red = reinterpret_cast<double*>(smem + 16);
+    T* taps = reinterpret_cast<T*>(smem + 16 + 2 * 33 * sizeof(double));
     Work<T> w;
-    w.taps = reinterpret_cast<T*>(sp);
-    sp += align_up<T>(sizeof(T) * 2 * P.K * P.kp, 16);
-    w.P1 = slab + (long long)blockIdx.x * slab_stride;
-    w.swp = cs.swp;
     w.E = cs.E;
     w.inv = cs.inv;
     w.cst = cs.cst;
+    T* P1 = slab + (long long)blockIdx.x * slab_stride;
     const int tid = threadIdx.x;
-    for (int i = tid; i < 2 * P.K * P.kp; i += blockDim.x) {
-        const int h = i / (P.K * P.kp), rem = i - h * P.K * P.kp;
-        const int a = rem / P.kp, b = rem - a * P.kp;
-        T v = 0;
-        if (b < P.K) v = h == 0 ? P.psf[(P.K - 1 - a) * P.K + (P.K - 1 - b)] : P.psf[a * P.K + b];
-        w.taps[i] = v;
+    for (int i = tid; i < g.K * g.kp; i += blockDim.x) {
+        const int a = i / g.kp, b = i - a * g.kp;
+        taps[i] = b < g.K ? P.psf[(g.K - 1 - a) * g.K + (g.K - 1 - b)] : (T)0;
     }
-    for (int i = tid; i < P.plen; i += blockDim.x) w.P1[i] = 0;
+    for (int i = tid; i < g.plen; i += blockDim.x) P1[i] = 0;
     if (blockIdx.x == 0 && tid == 0 && status) status[0] = cs.cstat[0];
     int which = 0;
     const bool bad = (cs.cstat[0] & ST_BADPARAM) != 0;
@@ -1094,23 +1288,28 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_forward(const Prob<T>* __restri
             if (tid == 0) chi2[k] = __longlong_as_double(0x7ff0000000000000LL);
             continue;
         }
-        apply_L(P, w, S + (long long)k * P.ns);
+        apply_L<T, T, T, T>(g, w.E, w.inv, S + (long long)k * g.ns, P1);
         __syncthreads();
         double chi = 0;
-        for (int t = tid; t < P.ntiles; t += blockDim.x) {
-            const int ty = t / P.tiles_x, tx = t - ty * P.tiles_x;
+        for (int t = tid; t < g.ntiles; t += blockDim.x) {
+            const int ty = t / g.tiles_x, tx = t - ty * g.tiles_x;
             T acc[TILE][TILE];
-            conv_any<T, K, false>(w.P1 + (ty * TILE) * P.Wp + tx * TILE, P.Wp, w.taps, P.K, P.kp, acc);
+            const T* base = P1 + (ty * TILE) * g.Wp + tx * TILE;
+            if constexpr (K > 0)
+                conv_tile<T, K, false>(base, g.Wp, taps, acc);
+            else
+                conv_tile_rt<T, T>(base, g.Wp, taps, g.K, g.kp, g.sh, acc);
 #pragma unroll
             for (int r = 0; r < TILE; ++r) {
                 const int y = ty * TILE + r;
-                const int pp = (y + P.hk) * P.Wp + tx * TILE + P.hk;
+                const int pp = (y + g.hk) * g.Wp + tx * TILE + g.xoff;
 #pragma unroll
                 for (int cc = 0; cc < TILE; ++cc) {
                     const int x = tx * TILE + cc;
-                    const T res = cs.bwp[pp + cc] - cs.swp[pp + cc] * acc[r][cc];
-                    chi += (double)res * (double)res;
-                    if (model && y < P.ny && x < P.nx) model[(long long)k * P.npix + y * P.nx + x] = acc[r][cc];
+                    const double sw = (double)cs.swp[pp + cc];
+                    const double res = sw * ((double)cs.dpad[pp + cc] - (double)acc[r][cc]);
+                    chi += res * res;
+                    if (model && y < g.ny && x < g.nx) model[(long long)k * g.nx * g.ny + y * g.nx + x] = acc[r][cc];
                 }
             }
         }

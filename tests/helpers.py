@@ -22,11 +22,16 @@ def host_problem(prob: Problem, dtype=torch.float32):
 
 
 def make_problem(geom, seed=0, psf_sigma=1.5, lens=synth.TRUE_LENS, mask=None, fixed_source=False):
-    """Synthetic observation through the oracle (S/N 20, 4x4 sub-pixel data)."""
+    """Synthetic observation through the oracle (S/N 20, 4x4 sub-pixel data).
+
+    The image, noise map and PSF are rounded to float32 values, so that the
+    FP32 library and the FP64 oracle are handed the very same problem."""
     rng = np.random.default_rng(seed)
     comps = synth.two_gaussian_source() if fixed_source else synth.drawn_source(rng)
     psf = synth.gaussian_psf(geom.kpsf, psf_sigma)
-    return observe(geom, lens, comps, psf, synth.standard_normal(rng, (geom.ny, geom.nx)), mask=mask)
+    prob = observe(geom, lens, comps, psf, synth.standard_normal(rng, (geom.ny, geom.nx)), mask=mask)
+    f32 = lambda a: np.asarray(a, dtype=np.float32).astype(np.float64)
+    return Problem(prob.geom, f32(prob.d), f32(prob.sigma), prob.mask, f32(prob.psf))
 
 
 def rel(a, b):

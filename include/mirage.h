@@ -100,8 +100,10 @@ typedef struct {
     int mem;           /* MIRAGE_MEM_* */
     int use_graph;     /* 1: capture the batched launch sequence once per argument
                           set and replay it on identical calls */
-    int threads;       /* 0 = default; < 0 = record per-phase CUDA events on the
-                          stream (non-graph batched calls) for mirage_last_phase_ms */
+    int threads;       /* 0 = default; -1 = record per-phase CUDA events on the
+                          stream (non-graph batched calls) for mirage_last_phase_ms;
+                          -2 = also accumulate per-phase SM clocks inside the
+                          fast CGLS kernel for mirage_last_phase_clocks */
     int replace_every; /* reserved (0) */
 } mirage_opts_t;
 
@@ -180,6 +182,12 @@ int mirage_last_launch_count(const mirage_ctx_t* ctx);
  * made with opts->threads < 0: ms[0] ray trace, ms[1] CGLS items, ms[2]
  * L-curve/finalize.  Waits for those events. */
 int mirage_last_phase_ms(mirage_ctx_t* ctx, double* ms);
+
+/* Per-phase SM clock totals (summed over CTAs) of the last call made with
+ * opts->threads == -2: [0] L p and H p, [1] B conv and reduction, [2]
+ * vector updates, [3] B^T conv, [4] L^T, reduction and p update, [5] FP64
+ * refinement residuals, [6] item set-up, [7] unused.  Synchronous. */
+int mirage_last_phase_clocks(mirage_ctx_t* ctx, unsigned long long* clk8);
 
 /* Text of the last error raised on the calling thread ("" if none). */
 const char* mirage_last_error(void);

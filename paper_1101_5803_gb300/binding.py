@@ -79,6 +79,8 @@ def load_library():
     lib.mirage_forward.restype = ip
     lib.mirage_last_launch_count.argtypes = [vp]
     lib.mirage_last_launch_count.restype = ip
+    lib.mirage_last_phase_clocks.argtypes = [vp, vp]
+    lib.mirage_last_phase_clocks.restype = ip
     lib.mirage_last_phase_ms.argtypes = [vp, vp]
     lib.mirage_last_phase_ms.restype = ip
     lib.mirage_last_error.argtypes = []
@@ -148,7 +150,7 @@ def mirage_last_launch_count(ctx) -> int:
 def mirage_eval_batch(ctx, probs, lens, prob_idx, lambdas, n_lam, *, tol=1e-6, maxit=0,
                       mode=MIRAGE_MODE_BATCHED, use_graph=False, replace_every=0, warm_x=None,
                       want_s=True, want_all_x=False, want_kappa=True, out=None, stream=None, real=torch.float32,
-                      phase_timing=False):
+                      phase_timing=False, phase_clocks=False):
     """Evaluate candidates; returns a dict of output tensors (see mirage.h).
 
     ``lens`` [n,7] float64 and ``lambdas`` [n,max_lam] float64 are device
@@ -179,7 +181,8 @@ def mirage_eval_batch(ctx, probs, lens, prob_idx, lambdas, n_lam, *, tol=1e-6, m
             out["all_x"] = mk((n, max_lam, max_ns), real)
     arr = (mirage_problem_t * len(probs))(*[p.c_struct() for p in probs])
     opts = mirage_opts_t(float(tol), int(maxit), int(mode), MIRAGE_MEM_HOST if host else MIRAGE_MEM_DEVICE,
-                         int(bool(use_graph)), -1 if phase_timing else 0, int(replace_every))
+                         int(bool(use_graph)), -2 if phase_clocks else (-1 if phase_timing else 0),
+                         int(replace_every))
     rc = lib.mirage_eval_batch(
         ctx, arr, len(probs), _ptr(lens.contiguous()), pidx.ctypes.data_as(ctypes.c_void_p), n,
         _ptr(lambdas.contiguous()), nl.ctypes.data_as(ctypes.c_void_p), max_lam, ctypes.byref(opts),
@@ -194,6 +197,13 @@ def mirage_last_phase_ms(ctx):
     """[ray trace, CGLS, finalize] device ms of the last phase-timed call."""
     buf = (ctypes.c_double * 3)()
     _check(load_library().mirage_last_phase_ms(ctx, buf), "mirage_last_phase_ms")
+    return list(buf)
+
+
+def mirage_last_phase_clocks(ctx):
+    """Per-phase SM clock totals of the last phase-clocked call (see mirage.h)."""
+    buf = (ctypes.c_ulonglong * 8)()
+    _check(load_library().mirage_last_phase_clocks(ctx, buf), "mirage_last_phase_clocks")
     return list(buf)
 
 
@@ -245,6 +255,9 @@ class Context:
 
     def phase_ms(self):
         return mirage_last_phase_ms(self.handle)
+
+    def phase_clocks(self):
+        return mirage_last_phase_clocks(self.handle)
 
     def close(self):
         if self.handle is not None:

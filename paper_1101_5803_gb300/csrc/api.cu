@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "../../include/mirage.h"
+#include "fast.cuh"
 #include "kernels.cuh"
 #include "table.h"
 
@@ -52,6 +53,7 @@ const KernelTable& table() {
         fill_f32_k21(k);
         fill_f32_gen(k);
         fill_f64(k);
+        fill_fast(k);
         return k;
     }();
     return t;
@@ -100,6 +102,7 @@ struct mirage_ctx {
     int precision = MIRAGE_FP32;
     int sm_count = 0;
     int max_smem = 0;
+    int max_smem_sm = 0;
     int last_launches = 0;
     // scratch
     DevBuf E, E64, Etmp, inv, cst, swp, dpad, nent, cstat, X, istat, slab, probs, cand_prob, items, counters;
@@ -109,6 +112,7 @@ struct mirage_ctx {
     std::map<const void*, int> smem_set;  // kernel -> dynamic smem attribute set
     cudaStream_t cap_stream = nullptr;   // graphs are captured here and launched on the caller's stream
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // phase timing (opts.threads < 0)
+    DevBuf clk;                                                  // per-phase SM clocks (opts.threads == -2)
     int timed = 0;
     std::vector<void*> scratch_seen;     // scratch pointers the cached graphs were captured with
 };
@@ -198,6 +202,7 @@ int set_smem(mirage_ctx* ctx, const void* fn, size_t bytes) {
         CK(cudaFuncGetAttributes(&fa, fn));
         const int dyn_max = ctx->max_smem - (int)fa.sharedSizeBytes;
         CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max));
+        CK(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared));
         it = ctx->smem_set.emplace(fn, dyn_max).first;
     }
     if ((long long)bytes > it->second) {
@@ -217,6 +222,18 @@ const void* pick_fwd(int prec, int K) {
     const KernelTable& t = table();
     const void* f = t.fwd[prec][K];
     return f ? f : t.fwd[prec][0];
+}
+
+// two-CTA-per-SM kernel when the problem qualifies (FP32 contexts only)
+template <typename T>
+const void* pick_fast(mirage_ctx* ctx, const Prob<T>& P) {
+    if (sizeof(T) != 4) return nullptr;
+    const Prob<float>& Pf = *reinterpret_cast<const Prob<float>*>(&P);
+    const size_t b = fast_smem_bytes(Pf);
+    if (b == 0 || (long long)b > ctx->max_smem_sm / 2 - 1024 || Pf.K >= MAX_K) return nullptr;
+    const int v = Pf.ns <= 4 * NTHREADS ? 0 : (Pf.ns <= 9 * NTHREADS ? 1 : -1);
+    if (v < 0) return nullptr;
+    return table().fast[Pf.K][v];
 }
 
 template <typename T>
@@ -412,8 +429,9 @@ int eval_impl(mirage_ctx* ctx, const mirage_problem_t* probs, int n_probs, const
     struct Group {
         const void* fn;
         bool big;
-        size_t smem;
-        long long slab;
+        int per_sm = 1;  // resident CTAs per SM
+        size_t smem = 0;
+        long long slab = 0;
         std::vector<std::pair<double, int>> items;  // (sort key, packed)
     };
     std::map<std::pair<const void*, int>, Group> groups;
@@ -423,6 +441,15 @@ int eval_impl(mirage_ctx* ctx, const mirage_problem_t* probs, int n_probs, const
         const size_t sm = smem_bytes<T>(P, false);
         const bool big = sm > (size_t)ctx->max_smem;
         const void* fn = pick_cgls(prec, big, P.K);
+        size_t item_smem = smem_bytes<T>(P, big);
+        long long item_slab = (long long)slab_bytes<T>(P, big);
+        int per_sm = 1;
+        if (const void* ff = pick_fast<T>(ctx, P)) {
+            fn = ff;
+            item_smem = fast_smem_bytes(*reinterpret_cast<const Prob<float>*>(&P));
+            item_slab = (long long)fast_slab_bytes(*reinterpret_cast<const Prob<float>*>(&P));
+            per_sm = 2;
+        }
         if (!fn) {
             set_error("no kernel for this PSF size");
             return MIRAGE_ERR_UNSUPPORTED;
@@ -431,8 +458,9 @@ int eval_impl(mirage_ctx* ctx, const mirage_problem_t* probs, int n_probs, const
         Group& g = groups[key];
         g.fn = fn;
         g.big = big;
-        g.smem = std::max(g.smem, smem_bytes<T>(P, big));
-        g.slab = std::max<long long>(g.slab, (long long)slab_bytes<T>(P, big));
+        g.per_sm = per_sm;
+        g.smem = std::max(g.smem, item_smem);
+        g.slab = std::max<long long>(g.slab, item_slab);
         const double work = (double)P.plen * P.K * P.K + 8.0 * P.nrays;
         for (int k = 0; k < n_lam[c]; ++k) {
             // lambda grids ascend: smaller k = smaller lambda = more CG iterations
@@ -477,7 +505,8 @@ int eval_impl(mirage_ctx* ctx, const mirage_problem_t* probs, int n_probs, const
     int slab_grid = 0;
     for (Group* g : glist) {
         slab_stride = std::max(slab_stride, (g->slab + 255) / 256 * 256);
-        slab_grid = std::max<int>(slab_grid, (int)std::min<long long>(ctx->sm_count, (long long)g->items.size()));
+        slab_grid = std::max<int>(slab_grid,
+                                  (int)std::min<long long>((long long)g->per_sm * ctx->sm_count, (long long)g->items.size()));
     }
     if (o.mode == MIRAGE_MODE_PLAIN) slab_grid = std::max(slab_grid, max_lam);
     TRY(ctx->slab.ensure((size_t)slab_stride * std::max(slab_grid, 1)));
@@ -556,6 +585,12 @@ int eval_impl(mirage_ctx* ctx, const mirage_problem_t* probs, int n_probs, const
     A.iters = d_iters;
     A.relres = d_relres;
     A.istat = dIst;
+    A.phase_clk = nullptr;
+    if (!graph && o.threads == -2) {
+        TRY(ctx->clk.ensure(8 * sizeof(unsigned long long)));
+        CK(cudaMemsetAsync(ctx->clk.p, 0, 8 * sizeof(unsigned long long), st));
+        A.phase_clk = ctx->clk.as<unsigned long long>();
+    }
 
     const cudaStream_t launch_st = st;
     if (graph) {
@@ -589,7 +624,8 @@ int eval_impl(mirage_ctx* ctx, const mirage_problem_t* probs, int n_probs, const
                 A.items = ditems + g_off[gi];
                 A.n_items = (int)g->items.size();
                 A.counter = dcnt + gi;
-                const int grid = (int)std::min<long long>(ctx->sm_count, (long long)g->items.size());
+                const int grid =
+                    (int)std::min<long long>((long long)g->per_sm * ctx->sm_count, (long long)g->items.size());
                 void* args[] = {&A};
                 rc = launch(ctx, g->fn, dim3(grid), dim3(NTHREADS), args, g->smem, st);
             }
@@ -621,7 +657,12 @@ int eval_impl(mirage_ctx* ctx, const mirage_problem_t* probs, int n_probs, const
                 const Prob<T>& P = hp[prob_idx[c]];
                 const bool big = smem_bytes<T>(P, false) > (size_t)ctx->max_smem;
                 const void* fn = pick_cgls(prec, big, P.K);
-                TRY(set_smem(ctx, fn, smem_bytes<T>(P, big)));
+                size_t item_smem = smem_bytes<T>(P, big);
+                if (const void* ff = pick_fast<T>(ctx, P)) {
+                    fn = ff;
+                    item_smem = fast_smem_bytes(*reinterpret_cast<const Prob<float>*>(&P));
+                }
+                TRY(set_smem(ctx, fn, item_smem));
                 int cand0 = c, nc = 1;
                 void* a1[] = {(void*)&dprobs, (void*)&dcand, (void*)&d_lens, &cand0, &nc, &cs};
                 rc = launch(ctx, tb.raytrace[prec], dim3(1), dim3(NTHREADS), a1, (size_t)max_cells * 4, st);
@@ -630,7 +671,7 @@ int eval_impl(mirage_ctx* ctx, const mirage_problem_t* probs, int n_probs, const
                 A.n_items = plain_off[c + 1] - plain_off[c];
                 A.counter = dcnt + c;
                 void* a2[] = {&A};
-                rc = launch(ctx, fn, dim3(A.n_items), dim3(NTHREADS), a2, smem_bytes<T>(P, big), st);
+                rc = launch(ctx, fn, dim3(A.n_items), dim3(NTHREADS), a2, item_smem, st);
                 if (rc) break;
                 int ml = max_lam, mns = (int)max_ns;
                 const int* ist = dIst;
@@ -751,7 +792,8 @@ int mirage_create(mirage_ctx_t** out, int device, int precision) {
     c->precision = precision;
     cudaError_t e1 = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
     cudaError_t e2 = cudaDeviceGetAttribute(&c->max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
-    if (e1 != cudaSuccess || e2 != cudaSuccess) {
+    cudaError_t e3 = cudaDeviceGetAttribute(&c->max_smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, device);
+    if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
         set_error("cudaDeviceGetAttribute failed");
         delete c;
         return MIRAGE_ERR_CUDA;
@@ -771,7 +813,7 @@ int mirage_destroy(mirage_ctx_t* ctx) {
     DevBuf* bufs[] = {&ctx->E, &ctx->E64, &ctx->Etmp, &ctx->inv, &ctx->cst, &ctx->swp, &ctx->dpad, &ctx->nent, &ctx->cstat,
                       &ctx->X, &ctx->istat, &ctx->slab, &ctx->probs, &ctx->cand_prob, &ctx->items, &ctx->counters,
                       &ctx->stage, &ctx->fE, &ctx->fE64, &ctx->fEtmp, &ctx->finv, &ctx->fcst, &ctx->fswp, &ctx->fdpad,
-                      &ctx->fnent, &ctx->fcstat, &ctx->fslab, &ctx->fprob, &ctx->fcand};
+                      &ctx->fnent, &ctx->fcstat, &ctx->fslab, &ctx->fprob, &ctx->fcand, &ctx->clk};
     for (DevBuf* b : bufs) b->release();
     delete ctx;
     return MIRAGE_OK;
@@ -815,6 +857,12 @@ int mirage_forward(mirage_ctx_t* ctx, const mirage_problem_t* prob, const double
 }
 
 int mirage_last_launch_count(const mirage_ctx_t* ctx) { return ctx ? ctx->last_launches : 0; }
+
+int mirage_last_phase_clocks(mirage_ctx_t* ctx, unsigned long long* clk8) {
+    if (!ctx || !clk8 || !ctx->clk.p) return MIRAGE_ERR_ARG;
+    CK(cudaMemcpy(clk8, ctx->clk.p, 8 * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
+    return MIRAGE_OK;
+}
 
 int mirage_last_phase_ms(mirage_ctx_t* ctx, double* ms) {
     if (!ctx || !ms) return MIRAGE_ERR_ARG;

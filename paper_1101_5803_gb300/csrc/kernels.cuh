@@ -91,6 +91,7 @@ struct CglsArgs {
     int* iters;
     double* relres;
     int* istat;
+    unsigned long long* phase_clk;  // nullable [8]: per-phase SM clock totals (instrumented runs)
 };
 
 // ---------------------------------------------------------------------------
@@ -171,6 +172,97 @@ __device__ __forceinline__ double block_sum(double v, double* red, int which) {
     __syncthreads();
     return r[32];
 }
+
+// Error-free FP32 summation step (Knuth's two-sum): s + e == a + b exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+// Warp sum of FP32 values carried as an unevaluated pair hi + lo (about
+// twice FP32 precision) on the FP32 pipe; FP64 arithmetic is reserved for
+// the final cross-warp sum.
+__device__ __forceinline__ double warp_sum_pair(float v) {
+    float hi = v, lo = 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+        const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+        float s, e;
+        two_sum(hi, h2, s, e);
+        e += lo + l2;
+        hi = s + e;
+        lo = e - (hi - s);
+    }
+    return (double)hi + (double)lo;
+}
+
+// Block sum delivered to thread 0 only (FP64 across warps); other threads
+// get 0.  The caller lets thread 0 derive its scalars, then synchronises.
+template <typename T>
+__device__ __forceinline__ double block_sum_to0(T v, double* red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double wv;
+    if constexpr (sizeof(T) == 4)
+        wv = warp_sum_pair(v);
+    else
+        wv = warp_sum((double)v);
+    if (lane == 0) red[warp] = wv;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
+    return t;
+}
+
+// Block sum with one barrier, delivered to every thread: each warp
+// publishes its compensated (hi, lo) pair, then every thread adds the
+// pairs in the same order with error-free FP32 steps, so all threads hold
+// the same value (accurate to ~1e-14 relative, like an FP64 sum of the
+// FP32 terms).  `buf` holds 2 x 64 floats; alternate `half` between calls.
+__device__ __forceinline__ float2 warp_pair(float v) {
+    float hi = v, lo = 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+        const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+        float s, e;
+        two_sum(hi, h2, s, e);
+        e += lo + l2;
+        hi = s + e;
+        lo = e - (hi - s);
+    }
+    return make_float2(hi, lo);
+}
+
+__device__ __forceinline__ float2 block_pair_all(float v, float* buf, int half) {
+    float2* b = reinterpret_cast<float2*>(buf) + 32 * half;
+    const float2 w = warp_pair(v);
+    if ((threadIdx.x & 31) == 0) b[threadIdx.x >> 5] = w;
+    __syncthreads();
+    float hi = 0.f, lo = 0.f;
+    const int nw = blockDim.x >> 5;
+    for (int i = 0; i < nw; ++i) {
+        const float2 x = b[i];
+        float s, e;
+        two_sum(hi, x.x, s, e);
+        e += lo + x.y;
+        hi = s + e;
+        lo = e - (hi - s);
+    }
+    return make_float2(hi, lo);
+}
+
+// Scalars of the inner CGLS, written by thread 0 and read by all threads
+// after a barrier.
+struct CgCtl {
+    double gam, g0, best;
+    int best_it, it, total_it, stop, brk;
+    float a_f, b_f;
+    double a_d, b_d;
+};
+static_assert(sizeof(CgCtl) <= 128, "CG control block must fit its reserved shared-memory slot");
 
 // ---------------------------------------------------------------------------
 // lens model
@@ -486,7 +578,7 @@ __device__ __forceinline__ void conv_tile_rt(const S* __restrict__ Pb, int Wp, c
 // geometry needed inside the solver loops (passed by value)
 template <typename T>
 struct Geo {
-    int nx, ny, sx, sy, ns, nreg, K, hk, kp, xoff, sh, Np, ncx, Wp, plen, tiles_x, ntiles, reg, nent;
+    int nx, ny, sx, sy, ns, nreg, K, hk, kp, xoff, sh, Np, ncx, ncells, Wp, plen, tiles_x, ntiles, reg, nent;
     T invNp;
 };
 
@@ -506,6 +598,7 @@ __device__ __forceinline__ Geo<T> geo_of(const Prob<T>& P, int nent) {
     g.sh = P.xoff - P.hk;
     g.Np = P.Np;
     g.ncx = P.ncx;
+    g.ncells = P.ncells;
     g.Wp = P.Wp;
     g.plen = P.plen;
     g.tiles_x = P.tiles_x;
@@ -674,7 +767,7 @@ enum : int { CONV_Q = 0, CONV_RAW = 1 };
 //   CONV_Q   : dst = sqrt(W) * conv, returns sum dst^2
 //   CONV_RAW : dst = conv
 template <typename T, int K, bool SH>
-__device__ __noinline__ double conv_pass(const T* __restrict__ src, const T* __restrict__ taps,
+__device__ __noinline__ T conv_pass(const T* __restrict__ src, const T* __restrict__ taps,
                                          const T* __restrict__ swp, T* __restrict__ dst, Geo<T> g, int mode) {
     T ss = 0;
     for (int t = threadIdx.x; t < g.ntiles; t += blockDim.x) {
@@ -703,7 +796,7 @@ __device__ __noinline__ double conv_pass(const T* __restrict__ src, const T* __r
             st4(dst + pp, o);
         }
     }
-    return (double)ss;
+    return ss;
 }
 
 // FP64 convolution pass of the refinement:
@@ -791,7 +884,7 @@ __host__ __device__ inline size_t align_up(size_t v, size_t a) {
 // Shared-memory footprint of one problem (big = work buffers in global memory).
 template <typename T>
 __host__ __device__ inline size_t smem_bytes(const Prob<T>& P, bool big) {
-    size_t o = 16 + 2 * 33 * sizeof(double);                       // item slot + reductions
+    size_t o = 16 + 2 * 33 * sizeof(double) + 128;                 // item slot + reductions + CG scalars
     o += align_up<T>(sizeof(T) * 2 * P.K * P.kp, 16);              // taps
     o += align_up<T>(sizeof(double) * 2 * P.K * P.kp, 16);         // taps64
     if (!big) {
@@ -822,6 +915,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_cgls(CglsArgs<T> A) {
     int which = 0;
     int* slot = reinterpret_cast<int*>(smem);
     double* red = reinterpret_cast<double*>(smem + 16);
+    CgCtl* ctl = reinterpret_cast<CgCtl*>(smem + 16 + 2 * 33 * sizeof(double));
 
     while (true) {
         __syncthreads();
@@ -838,7 +932,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_cgls(CglsArgs<T> A) {
 
         // ---- carve buffers
         Work<T> w;
-        unsigned char* sp = smem + 16 + 2 * 33 * sizeof(double);
+        unsigned char* sp = smem + 16 + 2 * 33 * sizeof(double) + 128;
         w.taps = reinterpret_cast<T*>(sp);
         sp += align_up<T>(sizeof(T) * 2 * g.K * g.kp, 16);
         w.taps64 = reinterpret_cast<double*>(sp);
@@ -1027,32 +1121,24 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_cgls(CglsArgs<T> A) {
                     st4(w.P2 + pp, o);
                 }
             }
-            double gam = 0;
             {
                 T gs = 0;
                 for (int i = tid; i < g.ns; i += bs) gs = fma(w.s[i], w.s[i], gs);
-                gam = block_sum((double)gs, red, which);
-                which ^= 1;
+                const double gam = block_sum_to0<T>(gs, red);
+                if (tid == 0) {
+                    ctl->gam = gam;
+                    ctl->g0 = gam;
+                    ctl->best = 1.0;
+                    ctl->best_it = 0;
+                    ctl->it = 0;
+                    ctl->total_it = total_it;
+                    ctl->brk = !isfinite(gam);
+                    ctl->stop = ctl->brk || !(gam > 0.0) || total_it >= maxit;
+                }
+                __syncthreads();
             }
-            const double g0 = gam;
-            double best = 1.0;
-            int best_it = 0;
             const int stag_window = max(4000, 2 * g.ns);
-            for (int it = 0;; ++it) {
-                if (!isfinite(gam)) {
-                    status |= ST_BREAK;
-                    break;
-                }
-                const double rel = sqrt(gam / g0);
-                if (!(rel > target)) break;
-                if (total_it >= maxit) break;
-                if (rel < 0.5 * best) {
-                    best = rel;
-                    best_it = it;
-                } else if (it - best_it > stag_window) {
-                    break;
-                }
-                ++total_it;
+            while (!ctl->stop) {
                 // q = A~ p: image part sqrt(W) B L p, regulariser part sqrt(lam) H p
                 apply_L<T, T, T, T>(g, w.E, w.inv, w.p, w.P1);
                 T dqr = 0;
@@ -1062,14 +1148,22 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_cgls(CglsArgs<T> A) {
                     dqr = fma(q, q, dqr);
                 }
                 __syncthreads();
-                const double dq = (double)dqr + conv_pass<T, K, SH>(w.P1, w.taps, w.swp, w.qimg, g, CONV_Q);
-                const double delta = block_sum(dq, red, which);
-                which ^= 1;
-                if (!(delta > 0.0) || !isfinite(delta)) {
-                    status |= ST_BREAK;
-                    break;
+                const T dq = dqr + conv_pass<T, K, SH>(w.P1, w.taps, w.swp, w.qimg, g, CONV_Q);
+                {
+                    const double delta = block_sum_to0<T>(dq, red);
+                    if (tid == 0) {
+                        if (!(delta > 0.0) || !isfinite(delta)) {
+                            ctl->brk = 1;
+                            ctl->stop = 1;
+                        } else {
+                            ctl->a_d = ctl->gam / delta;
+                            ctl->a_f = (float)ctl->a_d;
+                        }
+                    }
+                    __syncthreads();
                 }
-                const T a = (T)(gam / delta);
+                if (ctl->brk) break;
+                const T a = sizeof(T) == 4 ? (T)ctl->a_f : (T)ctl->a_d;
                 for (int i = tid; i < g.ns; i += bs) w.x[i] = fma(a, w.p[i], w.x[i]);
                 for (int i = tid; i < g.nreg; i += bs) w.rreg[i] = fma(-a, w.qreg[i], w.rreg[i]);
                 for (int t = tid; t < g.ntiles; t += bs) {
@@ -1100,13 +1194,35 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_cgls(CglsArgs<T> A) {
                     w.s[i] = v;
                     gs = fma(v, v, gs);
                 }
-                const double gnew = block_sum((double)gs, red, which);
-                which ^= 1;
-                const T bt = (T)(gnew / gam);
-                gam = gnew;
+                {
+                    const double gnew = block_sum_to0<T>(gs, red);
+                    if (tid == 0) {
+                        ctl->b_d = gnew / ctl->gam;
+                        ctl->b_f = (float)ctl->b_d;
+                        ctl->gam = gnew;
+                        const int it = ++ctl->it;
+                        ++ctl->total_it;
+                        const double rel = sqrt(gnew / ctl->g0);
+                        if (!isfinite(gnew)) {
+                            ctl->brk = 1;
+                            ctl->stop = 1;
+                        } else if (!(rel > target) || ctl->total_it >= maxit) {
+                            ctl->stop = 1;
+                        } else if (rel < 0.5 * ctl->best) {
+                            ctl->best = rel;
+                            ctl->best_it = it;
+                        } else if (it - ctl->best_it > stag_window) {
+                            ctl->stop = 1;
+                        }
+                    }
+                    __syncthreads();
+                }
+                const T bt = sizeof(T) == 4 ? (T)ctl->b_f : (T)ctl->b_d;
                 for (int i = tid; i < g.ns; i += bs) w.p[i] = fma(bt, w.p[i], w.s[i]);
                 __syncthreads();
             }
+            total_it = ctl->total_it;
+            if (ctl->brk) status |= ST_BREAK;
             if (status & ST_BREAK) break;
             for (int i = tid; i < g.ns; i += bs) w.x64[i] += (double)w.x[i];
             __syncthreads();

@@ -12,6 +12,8 @@ struct KernelTable {
     const void* fwd[2][MAX_K];
     const void* raytrace[2];
     const void* finalize[2];
+    // fast[K][v]: two-CTA-per-SM FP32 kernel, v = 0 for ns <= 1024, 1 for ns <= 2304
+    const void* fast[MAX_K][2];
 };
 
 void fill_f32_k5(KernelTable& t);
@@ -22,5 +24,6 @@ void fill_f32_k15(KernelTable& t);
 void fill_f32_k21(KernelTable& t);
 void fill_f32_gen(KernelTable& t);
 void fill_f64(KernelTable& t);
+void fill_fast(KernelTable& t);
 
 }  // namespace mirage

@@ -105,6 +105,11 @@ typedef struct {
                           -2 = also accumulate per-phase SM clocks inside the
                           fast CGLS kernel for mirage_last_phase_clocks */
     int replace_every; /* reserved (0) */
+    int variant;       /* CGLS kernel choice: 0 = automatic; 1 = two-CTA kernel with taps
+                          in shared memory; 2 = two-CTA kernel with taps as kernel
+                          parameters (FFMA); 3 = the same with packed FFMA2; 4 = the
+                          general one-CTA kernel.  Forced choices fall back to the
+                          general kernel where they do not apply. */
 } mirage_opts_t;
 
 typedef struct mirage_ctx mirage_ctx_t;

@@ -226,14 +226,20 @@ const void* pick_fwd(int prec, int K) {
 
 // two-CTA-per-SM kernel when the problem qualifies (FP32 contexts only)
 template <typename T>
-const void* pick_fast(mirage_ctx* ctx, const Prob<T>& P) {
+const void* pick_fast(mirage_ctx* ctx, const Prob<T>& P, int mode) {
     if (sizeof(T) != 4) return nullptr;
     const Prob<float>& Pf = *reinterpret_cast<const Prob<float>*>(&P);
     const size_t b = fast_smem_bytes(Pf);
     if (b == 0 || (long long)b > ctx->max_smem_sm / 2 - 1024 || Pf.K >= MAX_K) return nullptr;
     const int v = Pf.ns <= 4 * NTHREADS ? 0 : (Pf.ns <= 9 * NTHREADS ? 1 : -1);
     if (v < 0) return nullptr;
-    return table().fast[Pf.K][v];
+    return table().fast[Pf.K][v][mode];
+}
+
+// fast-kernel arguments (FP32 contexts only; never called for double)
+template <typename T>
+void set_fast_args(FastArgs& fa, const CglsArgs<T>& A) {
+    if constexpr (sizeof(T) == 4) std::memcpy(&fa.A, &A, sizeof(A));
 }
 
 template <typename T>
@@ -429,6 +435,8 @@ int eval_impl(mirage_ctx* ctx, const mirage_problem_t* probs, int n_probs, const
     struct Group {
         const void* fn;
         bool big;
+        bool fast = false;
+        int prob = -1;   // the single problem of the group, -2 if several
         int per_sm = 1;  // resident CTAs per SM
         size_t smem = 0;
         long long slab = 0;
@@ -436,6 +444,32 @@ int eval_impl(mirage_ctx* ctx, const mirage_problem_t* probs, int n_probs, const
     };
     std::map<std::pair<const void*, int>, Group> groups;
     std::vector<double> hlam;  // lambdas are device data: sort by index instead (ascending lambda = costlier)
+    // kernel choice per problem: parameter taps need one PSF per launch
+    std::vector<int> cands_of(n_probs, 0);
+    for (int c = 0; c < n_cand; ++c) cands_of[prob_idx[c]]++;
+    int n_used = 0;
+    for (int p = 0; p < n_probs; ++p) n_used += cands_of[p] > 0;
+    const int want = o.variant;
+    auto choose = [&](const Prob<T>& P, int& mode, bool& fast) -> const void* {
+        fast = false;
+        mode = 0;
+        if (want == 4) return nullptr;
+        int m = 2;                         // automatic: parameter taps (packed FFMA2) when one PSF
+        if (want == 1) m = 0;
+        if (want == 2) m = 1;
+        if (want == 3) m = 2;
+        if (m > 0 && (n_used > 1 || P.K * P.K > MAX_PTAP)) m = 0;
+        const void* f = pick_fast<T>(ctx, P, m);
+        if (!f && m > 0) {
+            m = 0;
+            f = pick_fast<T>(ctx, P, 0);
+        }
+        if (f) {
+            fast = true;
+            mode = m;
+        }
+        return f;
+    };
     for (int c = 0; c < n_cand; ++c) {
         const Prob<T>& P = hp[prob_idx[c]];
         const size_t sm = smem_bytes<T>(P, false);
@@ -443,8 +477,9 @@ int eval_impl(mirage_ctx* ctx, const mirage_problem_t* probs, int n_probs, const
         const void* fn = pick_cgls(prec, big, P.K);
         size_t item_smem = smem_bytes<T>(P, big);
         long long item_slab = (long long)slab_bytes<T>(P, big);
-        int per_sm = 1;
-        if (const void* ff = pick_fast<T>(ctx, P)) {
+        int per_sm = 1, mode = 0;
+        bool fast = false;
+        if (const void* ff = choose(P, mode, fast)) {
             fn = ff;
             item_smem = fast_smem_bytes(*reinterpret_cast<const Prob<float>*>(&P));
             item_slab = (long long)fast_slab_bytes(*reinterpret_cast<const Prob<float>*>(&P));
@@ -458,6 +493,8 @@ int eval_impl(mirage_ctx* ctx, const mirage_problem_t* probs, int n_probs, const
         Group& g = groups[key];
         g.fn = fn;
         g.big = big;
+        g.fast = fast;
+        g.prob = (g.prob == -1 || g.prob == prob_idx[c]) ? prob_idx[c] : -2;
         g.per_sm = per_sm;
         g.smem = std::max(g.smem, item_smem);
         g.slab = std::max<long long>(g.slab, item_slab);
@@ -499,6 +536,23 @@ int eval_impl(mirage_ctx* ctx, const mirage_problem_t* probs, int n_probs, const
     meta.insert(meta.end(), n_lam, n_lam + n_cand);
     meta.insert(meta.end(), items_v.begin(), items_v.end());
     TRY(ctx->counters.ensure(sizeof(int) * n_counters));
+    // taps of the fast kernels' launch groups (kernel parameters)
+    std::vector<std::vector<float>> gtaps(glist.size());
+    for (size_t gi = 0; gi < glist.size(); ++gi) {
+        Group* g = glist[gi];
+        if (!g->fast || g->prob < 0) continue;
+        const Prob<T>& P = hp[g->prob];
+        const int K = P.K;
+        std::vector<T> psf((size_t)K * K);
+        CK(cudaMemcpy(psf.data(), P.psf, sizeof(T) * K * K, cudaMemcpyDefault));
+        std::vector<float>& tp = gtaps[gi];
+        tp.assign(2 * MAX_PTAP, 0.f);
+        for (int a = 0; a < K; ++a)
+            for (int b = 0; b < K; ++b) {
+                tp[a * K + b] = (float)psf[(K - 1 - a) * K + (K - 1 - b)];
+                tp[MAX_PTAP + a * K + b] = (float)psf[a * K + b];
+            }
+    }
     // per-CTA global slab (bytes): FP64 refinement buffers, plus all work
     // buffers for items that do not fit in shared memory
     long long slab_stride = 0;
@@ -533,6 +587,9 @@ int eval_impl(mirage_ctx* ctx, const mirage_problem_t* probs, int n_probs, const
         addb(&o.tol, sizeof(o.tol));
         addb(&o.maxit, sizeof(o.maxit));
         addb(&o.replace_every, sizeof(o.replace_every));
+        addb(&o.variant, sizeof(o.variant));
+        for (auto& tp : gtaps)
+            if (!tp.empty()) addb(tp.data(), sizeof(float) * tp.size());
         auto it = ctx->graphs.find(key);
         if (it != ctx->graphs.end()) {
             CK(cudaGraphLaunch(it->second.exec, st));
@@ -626,8 +683,17 @@ int eval_impl(mirage_ctx* ctx, const mirage_problem_t* probs, int n_probs, const
                 A.counter = dcnt + gi;
                 const int grid =
                     (int)std::min<long long>((long long)g->per_sm * ctx->sm_count, (long long)g->items.size());
-                void* args[] = {&A};
-                rc = launch(ctx, g->fn, dim3(grid), dim3(NTHREADS), args, g->smem, st);
+                if (g->fast) {
+                    FastArgs fa;
+                    std::memset(&fa, 0, sizeof(fa));
+                    set_fast_args<T>(fa, A);
+                    if (!gtaps[gi].empty()) std::memcpy(fa.ptap, gtaps[gi].data(), sizeof(fa.ptap));
+                    void* args[] = {&fa};
+                    rc = launch(ctx, g->fn, dim3(grid), dim3(NTHREADS), args, g->smem, st);
+                } else {
+                    void* args[] = {&A};
+                    rc = launch(ctx, g->fn, dim3(grid), dim3(NTHREADS), args, g->smem, st);
+                }
             }
             if (rc) break;
             if (timing) cudaEventRecord(ctx->ev[2], st);
@@ -658,7 +724,9 @@ int eval_impl(mirage_ctx* ctx, const mirage_problem_t* probs, int n_probs, const
                 const bool big = smem_bytes<T>(P, false) > (size_t)ctx->max_smem;
                 const void* fn = pick_cgls(prec, big, P.K);
                 size_t item_smem = smem_bytes<T>(P, big);
-                if (const void* ff = pick_fast<T>(ctx, P)) {
+                int pmode = 0;
+                bool pfast = false;
+                if (const void* ff = choose(P, pmode, pfast)) {
                     fn = ff;
                     item_smem = fast_smem_bytes(*reinterpret_cast<const Prob<float>*>(&P));
                 }
@@ -670,8 +738,25 @@ int eval_impl(mirage_ctx* ctx, const mirage_problem_t* probs, int n_probs, const
                 A.items = ditems + plain_off[c];
                 A.n_items = plain_off[c + 1] - plain_off[c];
                 A.counter = dcnt + c;
-                void* a2[] = {&A};
-                rc = launch(ctx, fn, dim3(A.n_items), dim3(NTHREADS), a2, item_smem, st);
+                if (pfast) {
+                    FastArgs fa;
+                    std::memset(&fa, 0, sizeof(fa));
+                    set_fast_args<T>(fa, A);
+                    if (pmode > 0) {
+                        std::vector<T> psf((size_t)P.K * P.K);
+                        CK(cudaMemcpy(psf.data(), P.psf, sizeof(T) * P.K * P.K, cudaMemcpyDefault));
+                        for (int a = 0; a < P.K; ++a)
+                            for (int b = 0; b < P.K; ++b) {
+                                fa.ptap[0][a * P.K + b] = (float)psf[(P.K - 1 - a) * P.K + (P.K - 1 - b)];
+                                fa.ptap[1][a * P.K + b] = (float)psf[a * P.K + b];
+                            }
+                    }
+                    void* a2[] = {&fa};
+                    rc = launch(ctx, fn, dim3(A.n_items), dim3(NTHREADS), a2, item_smem, st);
+                } else {
+                    void* a2[] = {&A};
+                    rc = launch(ctx, fn, dim3(A.n_items), dim3(NTHREADS), a2, item_smem, st);
+                }
                 if (rc) break;
                 int ml = max_lam, mns = (int)max_ns;
                 const int* ist = dIst;

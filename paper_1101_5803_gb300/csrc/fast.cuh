@@ -59,9 +59,90 @@ __device__ __forceinline__ void conv_tile_x2(const float* __restrict__ Pb, int W
     }
 }
 
-template <int K, int NSP>
-__global__ void __launch_bounds__(NTHREADS, 2) k_cgls_fast(CglsArgs<float> A) {
+// Kernel arguments of the fast kernel: the common arguments plus, for
+// launch groups that share one PSF, the taps themselves.  Kernel parameters
+// live in the constant bank, which FFMA reads as a direct operand, so the
+// unrolled convolution issues no tap loads at all.
+constexpr int MAX_PTAP = 15 * 15;
+struct FastArgs {
+    CglsArgs<float> A;
+    float ptap[2][MAX_PTAP];  // [0] flipped PSF (B), [1] PSF (B^T), row-major K x K
+};
+
+// tap source of the fast convolution
+enum : int { TAPS_SMEM_X2 = 0, TAPS_PARAM = 1, TAPS_PARAM_X2 = 2 };
+
+template <int K, int MODE>
+__device__ __forceinline__ void conv_tile_fast(const float* __restrict__ Pb, int Wp, const float2* __restrict__ taps2,
+                                               const float* __restrict__ pt, float (&out)[16]) {
+    if constexpr (MODE == TAPS_SMEM_X2) {
+        float2 acc[TILE][2];
+        conv_tile_x2<K>(Pb, Wp, taps2, acc);
+#pragma unroll
+        for (int r = 0; r < TILE; ++r) {
+            out[r * 4 + 0] = acc[r][0].x;
+            out[r * 4 + 1] = acc[r][0].y;
+            out[r * 4 + 2] = acc[r][1].x;
+            out[r * 4 + 3] = acc[r][1].y;
+        }
+    } else {
+        constexpr int HK = (K - 1) / 2;
+        constexpr int SHF = xoff_of<float>(HK) - HK;
+        constexpr int W = TILE + K - 1 + SHF;
+        constexpr int NVW = (W + 3) / 4 * 4;
+        const unsigned src_a = smem_addr(Pb);
+        float2 acc2[TILE][2];
+        float acc[TILE][TILE];
+#pragma unroll
+        for (int r = 0; r < TILE; ++r) {
+            acc2[r][0] = acc2[r][1] = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int c = 0; c < TILE; ++c) acc[r][c] = 0.f;
+        }
+#pragma unroll
+        for (int i = 0; i < TILE + K - 1; ++i) {
+            float in[NVW];
+#pragma unroll
+            for (int v = 0; v < NVW; v += 4) lds_vec(src_a + (unsigned)((i * Wp + v) * sizeof(float)), in + v);
+#pragma unroll
+            for (int b = 0; b < K; ++b) {
+                const int o = b + SHF;
+#pragma unroll
+                for (int r = 0; r < TILE; ++r) {
+                    const int a = i - r;
+                    if (a >= 0 && a < K) {
+                        const float t = pt[a * K + b];
+                        if constexpr (MODE == TAPS_PARAM) {
+#pragma unroll
+                            for (int c = 0; c < TILE; ++c) acc[r][c] = fmaf(t, in[o + c], acc[r][c]);
+                        } else {
+                            const float2 t2 = make_float2(t, t);
+                            acc2[r][0] = __ffma2_rn(t2, make_float2(in[o], in[o + 1]), acc2[r][0]);
+                            acc2[r][1] = __ffma2_rn(t2, make_float2(in[o + 2], in[o + 3]), acc2[r][1]);
+                        }
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < TILE; ++r) {
+            if constexpr (MODE == TAPS_PARAM) {
+#pragma unroll
+                for (int c = 0; c < TILE; ++c) out[r * 4 + c] = acc[r][c];
+            } else {
+                out[r * 4 + 0] = acc2[r][0].x;
+                out[r * 4 + 1] = acc2[r][0].y;
+                out[r * 4 + 2] = acc2[r][1].x;
+                out[r * 4 + 3] = acc2[r][1].y;
+            }
+        }
+    }
+}
+
+template <int K, int NSP, int MODE>
+__global__ void __launch_bounds__(NTHREADS, 2) k_cgls_fast(const __grid_constant__ FastArgs FA) {
     using T = float;
+    const CglsArgs<float>& A = FA.A;
     extern __shared__ __align__(16) unsigned char smem[];
     const int tid = threadIdx.x, bs = blockDim.x;
     int* slot = reinterpret_cast<int*>(smem);
@@ -342,15 +423,10 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_cgls_fast(CglsArgs<float> A) {
                 // q = sqrt(W) B P1 on the owned tile
                 float q[16];
                 if (own) {
-                    float2 acc[TILE][2];
-                    conv_tile_x2<K>(P1t, g.Wp, taps2, acc);
+                    float o16[16];
+                    conv_tile_fast<K, MODE>(P1t, g.Wp, taps2, FA.ptap[0], o16);
 #pragma unroll
-                    for (int r = 0; r < TILE; ++r) {
-                        q[r * 4 + 0] = sw[r * 4 + 0] * acc[r][0].x;
-                        q[r * 4 + 1] = sw[r * 4 + 1] * acc[r][0].y;
-                        q[r * 4 + 2] = sw[r * 4 + 2] * acc[r][1].x;
-                        q[r * 4 + 3] = sw[r * 4 + 3] * acc[r][1].y;
-                    }
+                    for (int qq = 0; qq < 16; ++qq) q[qq] = sw[qq] * o16[qq];
 #pragma unroll
                     for (int qq = 0; qq < 16; ++qq) dq = fmaf(q[qq], q[qq], dq);
                 } else {
@@ -390,15 +466,14 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_cgls_fast(CglsArgs<float> A) {
                 PHASE(2);
                 // u = B^T P2 on the owned tile, stored into P1 at mapped pixels
                 if (own) {
-                    float2 acc[TILE][2];
-                    conv_tile_x2<K>(P2t, g.Wp, taps2 + K * K, acc);
+                    float o16[16];
+                    conv_tile_fast<K, MODE>(P2t, g.Wp, taps2 + K * K, FA.ptap[1], o16);
 #pragma unroll
                     for (int r = 0; r < TILE; ++r) {
                         float* dst = P1 + pp0 + r * g.Wp;
-                        if (mbits & (1u << (r * 4 + 0))) dst[0] = acc[r][0].x;
-                        if (mbits & (1u << (r * 4 + 1))) dst[1] = acc[r][0].y;
-                        if (mbits & (1u << (r * 4 + 2))) dst[2] = acc[r][1].x;
-                        if (mbits & (1u << (r * 4 + 3))) dst[3] = acc[r][1].y;
+#pragma unroll
+                        for (int cc = 0; cc < 4; ++cc)
+                            if (mbits & (1u << (r * 4 + cc))) dst[cc] = o16[r * 4 + cc];
                     }
                 }
                 __syncthreads();  // u complete

@@ -12,8 +12,9 @@ struct KernelTable {
     const void* fwd[2][MAX_K];
     const void* raytrace[2];
     const void* finalize[2];
-    // fast[K][v]: two-CTA-per-SM FP32 kernel, v = 0 for ns <= 1024, 1 for ns <= 2304
-    const void* fast[MAX_K][2];
+    // fast[K][v][mode]: two-CTA-per-SM FP32 kernel, v = 0 for ns <= 1024,
+    // 1 for ns <= 2304; mode = tap source (0 shared, 1 params FFMA, 2 params FFMA2)
+    const void* fast[MAX_K][2][3];
 };
 
 void fill_f32_k5(KernelTable& t);

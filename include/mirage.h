@@ -197,6 +197,36 @@ int mirage_last_phase_clocks(mirage_ctx_t* ctx, unsigned long long* clk8);
 /* Text of the last error raised on the calling thread ("" if none). */
 const char* mirage_last_error(void);
 
+/* Allocation-free forward model.  The paper has no counterpart: this entry
+ * exists for callers that must not let the library allocate device memory
+ * (a host framework that owns the device-memory budget through its own
+ * pool, or a loop where cudaMalloc / cudaFree would synchronise the device
+ * at the wrong time).  It computes what mirage_forward computes, with the
+ * same kernels, but needs no context and calls no cudaMalloc, cudaFree or
+ * other allocating routine: all scratch comes from one fixed array of
+ * mirage_noalloc_capacity() bytes (8 MiB) that every device loading the
+ * library holds until the process exits.
+ *  precision  MIRAGE_FP32 or MIRAGE_FP64 (the type of "real" below)
+ *  prob, lens, s, n_src, model, chi2, status: as for mirage_forward; the
+ *             call works on the current CUDA device.
+ * Returns MIRAGE_ERR_UNSUPPORTED (message in mirage_noalloc_last_error)
+ * when the problem needs more scratch than the array holds, roughly images
+ * above 160 x 160 FP32 rays.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) once; make that first call
+ * before any stream capture.  All calls share the array and it keeps the
+ * last call's contents (each call rebuilds what it reads), so calls that
+ * overlap on the GPU (different streams, threads or devices sharing it
+ * concurrently on one device) race: serialise them. */
+int mirage_forward_noalloc(int precision, const mirage_problem_t* prob, const double* lens,
+                           const void* s, int n_src, void* model, double* chi2, int* status,
+                           void* stream);
+
+/* Error text of the last failed mirage_forward_noalloc call. */
+const char* mirage_noalloc_last_error(void);
+
+/* Size in bytes of the fixed scratch array of mirage_forward_noalloc. */
+size_t mirage_noalloc_capacity(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -85,6 +85,12 @@ def load_library():
     lib.mirage_last_phase_ms.restype = ip
     lib.mirage_last_error.argtypes = []
     lib.mirage_last_error.restype = ctypes.c_char_p
+    lib.mirage_forward_noalloc.argtypes = [i, ctypes.POINTER(mirage_problem_t), vp, vp, i, vp, vp, vp, vp]
+    lib.mirage_forward_noalloc.restype = ip
+    lib.mirage_noalloc_last_error.argtypes = []
+    lib.mirage_noalloc_last_error.restype = ctypes.c_char_p
+    lib.mirage_noalloc_capacity.argtypes = []
+    lib.mirage_noalloc_capacity.restype = ctypes.c_size_t
     _lib = lib
     return lib
 
@@ -92,7 +98,7 @@ def load_library():
 def header_functions() -> list[str]:
     """Names of the functions include/mirage.h declares."""
     txt = open(HEADER).read()
-    return sorted(set(re.findall(r"^\s*(?:int|const char\*)\s+(mirage_\w+)\s*\(", txt, re.M)))
+    return sorted(set(re.findall(r"^\s*(?:int|size_t|const char\*)\s+(mirage_\w+)\s*\(", txt, re.M)))
 
 
 def _check(rc: int, what: str):
@@ -231,6 +237,25 @@ def mirage_forward(ctx, prob, lens, S, *, want_model=True, stream=None):
     st = prob.c_struct()
     _check(lib.mirage_forward(ctx, ctypes.byref(st), _ptr(lens.contiguous()), _ptr(S.contiguous()), n_src,
                               _ptr(model), _ptr(chi2), _ptr(status), _stream_ptr(stream)), "mirage_forward")
+    return model, chi2, status
+
+
+def mirage_forward_noalloc(precision, prob, lens, S, *, want_model=True, stream=None):
+    """B L s and chi2 like mirage_forward, without any device allocation by
+    the library (all its scratch sits in a fixed array; see mirage.h).  The
+    output tensors are allocated here by the caller-side binding."""
+    lib = load_library()
+    n_src = int(S.shape[0])
+    model = torch.empty((n_src, int(prob.geom.ny) * int(prob.geom.nx)), dtype=S.dtype, device=S.device) \
+        if want_model else None
+    chi2 = torch.empty(n_src, dtype=torch.float64, device=S.device)
+    status = torch.zeros(1, dtype=torch.int32, device=S.device)
+    st = prob.c_struct()
+    rc = lib.mirage_forward_noalloc(int(precision), ctypes.byref(st), _ptr(lens.contiguous()), _ptr(S.contiguous()),
+                                    n_src, _ptr(model), _ptr(chi2), _ptr(status), _stream_ptr(stream))
+    if rc != MIRAGE_OK:
+        raise MirageError(f"mirage_forward_noalloc failed ({rc}): "
+                          f"{lib.mirage_noalloc_last_error().decode(errors='replace')}")
     return model, chi2, status
 
 

@@ -967,3 +967,15 @@ int mirage_last_phase_ms(mirage_ctx_t* ctx, double* ms) {
 const char* mirage_last_error(void) { return g_last_error.c_str(); }
 
 }  // extern "C"
+
+// Internal accessors shared with the allocation-free entry point (noalloc.cu).
+namespace mirage {
+const KernelTable& kernel_table() { return table(); }
+int geometry_ok(const mirage_geom_t& g) { return check_geom(g); }
+template <typename T>
+Prob<T> problem_layout(const mirage_problem_t& p) {
+    return make_prob<T>(p, p.d, p.sigma, p.mask, p.psf);
+}
+template Prob<float> problem_layout<float>(const mirage_problem_t&);
+template Prob<double> problem_layout<double>(const mirage_problem_t&);
+}  // namespace mirage

@@ -197,6 +197,39 @@ int mirage_last_phase_clocks(mirage_ctx_t* ctx, unsigned long long* clk8);
 /* Text of the last error raised on the calling thread ("" if none). */
 const char* mirage_last_error(void);
 
+/* ------------------------------------------------------------------------
+ * Surrogate network (the learned screen in front of the exact solves).
+ * A multilayer perceptron dims[0] -> dims[1] -> ... -> dims[n_layers]: SiLU
+ * after every hidden layer, linear output, mean-squared-error loss, Adam
+ * (b1 0.9, b2 0.999, eps 1e-8).  Products run on BF16 tensor cores with
+ * FP32 accumulation; master weights, moments and activations' gradients
+ * are FP32.  Parameters are ordered W_1 [dims[1] x dims[0]] (row-major),
+ * b_1 [dims[1]], W_2, b_2, ...  Device arrays unless noted; the network
+ * object owns its weights and work buffers.  The paper's optimisers use no
+ * surrogate; this serves the batched GA front end.
+ * ------------------------------------------------------------------------ */
+typedef struct mirage_mlp mirage_mlp_t;
+
+/* New network on `device` with He-initialised weights from `seed`. */
+int mirage_mlp_create(mirage_mlp_t** mlp, int device, int n_layers, const int* dims,
+                      unsigned long long seed);
+int mirage_mlp_destroy(mirage_mlp_t* mlp);
+/* Number of parameters (weights and biases). */
+long mirage_mlp_num_params(const mirage_mlp_t* mlp);
+/* Copy FP32 parameters from / to HOST memory; setting resets Adam. */
+int mirage_mlp_set_params(mirage_mlp_t* mlp, const float* host_params, long n);
+int mirage_mlp_get_params(const mirage_mlp_t* mlp, float* host_params, long n);
+/* y [n x dims[L]] = network(x [n x dims[0]]) (FP32 in and out). */
+int mirage_mlp_forward(mirage_mlp_t* mlp, const float* x, int n, float* y, void* stream);
+/* Gradient of mean((y - t)^2) into grad [num_params] (nullable), the loss
+ * into loss [1] (double, nullable) and the forward output into y. */
+int mirage_mlp_grad(mirage_mlp_t* mlp, const float* x, const float* t, int n, float* grad, double* loss,
+                    float* y, void* stream);
+/* One Adam step at learning rate lr on the batch (x, t). */
+int mirage_mlp_train_step(mirage_mlp_t* mlp, const float* x, const float* t, int n, float lr,
+                          double* loss, float* y, void* stream);
+const char* mirage_mlp_last_error(void);
+
 /* Allocation-free forward model.  The paper has no counterpart: this entry
  * exists for callers that must not let the library allocate device memory
  * (a host framework that owns the device-memory budget through its own

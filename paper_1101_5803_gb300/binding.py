@@ -91,6 +91,25 @@ def load_library():
     lib.mirage_noalloc_last_error.restype = ctypes.c_char_p
     lib.mirage_noalloc_capacity.argtypes = []
     lib.mirage_noalloc_capacity.restype = ctypes.c_size_t
+    ll = ctypes.c_long
+    lib.mirage_mlp_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), i, i, vp, ctypes.c_ulonglong]
+    lib.mirage_mlp_create.restype = ip
+    lib.mirage_mlp_destroy.argtypes = [vp]
+    lib.mirage_mlp_destroy.restype = ip
+    lib.mirage_mlp_num_params.argtypes = [vp]
+    lib.mirage_mlp_num_params.restype = ll
+    lib.mirage_mlp_set_params.argtypes = [vp, vp, ll]
+    lib.mirage_mlp_set_params.restype = ip
+    lib.mirage_mlp_get_params.argtypes = [vp, vp, ll]
+    lib.mirage_mlp_get_params.restype = ip
+    lib.mirage_mlp_forward.argtypes = [vp, vp, i, vp, vp]
+    lib.mirage_mlp_forward.restype = ip
+    lib.mirage_mlp_grad.argtypes = [vp, vp, vp, i, vp, vp, vp, vp]
+    lib.mirage_mlp_grad.restype = ip
+    lib.mirage_mlp_train_step.argtypes = [vp, vp, vp, i, ctypes.c_float, vp, vp, vp]
+    lib.mirage_mlp_train_step.restype = ip
+    lib.mirage_mlp_last_error.argtypes = []
+    lib.mirage_mlp_last_error.restype = ctypes.c_char_p
     _lib = lib
     return lib
 
@@ -98,7 +117,7 @@ def load_library():
 def header_functions() -> list[str]:
     """Names of the functions include/mirage.h declares."""
     txt = open(HEADER).read()
-    return sorted(set(re.findall(r"^\s*(?:int|size_t|const char\*)\s+(mirage_\w+)\s*\(", txt, re.M)))
+    return sorted(set(re.findall(r"^\s*(?:int|long|size_t|const char\*)\s+(mirage_\w+)\s*\(", txt, re.M)))
 
 
 def _check(rc: int, what: str):
@@ -257,6 +276,82 @@ def mirage_forward_noalloc(precision, prob, lens, S, *, want_model=True, stream=
         raise MirageError(f"mirage_forward_noalloc failed ({rc}): "
                           f"{lib.mirage_noalloc_last_error().decode(errors='replace')}")
     return model, chi2, status
+
+
+class MLP:
+    """Surrogate network (see mirage.h): FP32 device tensors in and out."""
+
+    def __init__(self, dims, device: int = 0, seed: int = 0):
+        lib = load_library()
+        self.dims = [int(d) for d in dims]
+        arr = (ctypes.c_int * len(self.dims))(*self.dims)
+        h = ctypes.c_void_p()
+        rc = lib.mirage_mlp_create(ctypes.byref(h), device, len(self.dims) - 1, arr, seed)
+        self._chk(rc, "mirage_mlp_create")
+        self.handle = h
+        self.n_params = int(lib.mirage_mlp_num_params(h))
+
+    @staticmethod
+    def _chk(rc, what):
+        if rc != MIRAGE_OK:
+            raise MirageError(f"{what} failed ({rc}): {load_library().mirage_mlp_last_error().decode(errors='replace')}")
+
+    def get_params(self) -> np.ndarray:
+        out = np.empty(self.n_params, dtype=np.float32)
+        self._chk(load_library().mirage_mlp_get_params(self.handle, out.ctypes.data_as(ctypes.c_void_p),
+                                                       self.n_params), "mirage_mlp_get_params")
+        return out
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(np.asarray(p, dtype=np.float32))
+        self._chk(load_library().mirage_mlp_set_params(self.handle, p.ctypes.data_as(ctypes.c_void_p), p.size),
+                  "mirage_mlp_set_params")
+
+    def layers(self, flat=None):
+        """Split a flat parameter vector into [(W, b), ...]."""
+        flat = self.get_params() if flat is None else flat
+        out, o = [], 0
+        for i, j in zip(self.dims[:-1], self.dims[1:]):
+            W = flat[o:o + i * j].reshape(j, i)
+            o += i * j
+            b = flat[o:o + j]
+            o += j
+            out.append((W, b))
+        return out
+
+    def forward(self, x, stream=None):
+        y = torch.empty((x.shape[0], self.dims[-1]), dtype=torch.float32, device=x.device)
+        self._chk(load_library().mirage_mlp_forward(self.handle, _ptr(x.contiguous()), int(x.shape[0]), _ptr(y),
+                                                    _stream_ptr(stream)), "mirage_mlp_forward")
+        return y
+
+    def grad(self, x, t, stream=None):
+        g = torch.empty(self.n_params, dtype=torch.float32, device=x.device)
+        loss = torch.zeros(1, dtype=torch.float64, device=x.device)
+        y = torch.empty((x.shape[0], self.dims[-1]), dtype=torch.float32, device=x.device)
+        self._chk(load_library().mirage_mlp_grad(self.handle, _ptr(x.contiguous()), _ptr(t.contiguous()),
+                                                 int(x.shape[0]), _ptr(g), _ptr(loss), _ptr(y), _stream_ptr(stream)),
+                  "mirage_mlp_grad")
+        return g, loss, y
+
+    def train_step(self, x, t, lr, stream=None):
+        loss = torch.zeros(1, dtype=torch.float64, device=x.device)
+        y = torch.empty((x.shape[0], self.dims[-1]), dtype=torch.float32, device=x.device)
+        self._chk(load_library().mirage_mlp_train_step(self.handle, _ptr(x.contiguous()), _ptr(t.contiguous()),
+                                                       int(x.shape[0]), float(lr), _ptr(loss), _ptr(y),
+                                                       _stream_ptr(stream)), "mirage_mlp_train_step")
+        return loss
+
+    def close(self):
+        if getattr(self, "handle", None) is not None:
+            load_library().mirage_mlp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Context:

@@ -1,0 +1,411 @@
+// Surrogate network: a multilayer perceptron with SiLU hidden layers and a
+// linear output layer, trained with mean-squared error and Adam.  Matrix
+// products run on BF16 tensor cores (mma.sync m16n8k16, FP32 accumulate);
+// master weights, Adam moments, bias, activation and loss stay in FP32.
+//
+// It predicts, from the encoded lens vector, the standardised
+// (log chi2, log10 lambda) of the L-curve corner, so that a genetic
+// algorithm can screen its offspring and warm-start the exact solves.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/mirage.h"
+
+namespace {
+
+thread_local std::string g_mlp_err;
+
+int mlp_fail(int code, const std::string& msg) {
+    g_mlp_err = msg;
+    return code;
+}
+
+#define MCK(call)                                                                        \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess) return mlp_fail(MIRAGE_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+__device__ __forceinline__ unsigned pack_bf16(__nv_bfloat16 lo, __nv_bfloat16 hi) {
+    return (unsigned)__bfloat16_as_ushort(lo) | ((unsigned)__bfloat16_as_ushort(hi) << 16);
+}
+
+// C[M x N] (FP32, row-major, ldc) = sum_k A(m, k) B(k, n) with
+//   A(m, k) = A[m * sam + k * sak],  B(k, n) = B[k * sbk + n * sbn]  (BF16)
+// One warp per 16 x 8 output tile, K in steps of 16; edges are zero-filled.
+__global__ void k_gemm_bf16(const __nv_bfloat16* __restrict__ A, long sam, long sak, const __nv_bfloat16* __restrict__ B,
+                            long sbk, long sbn, float* __restrict__ C, int ldc, int M, int N, int K) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    const int tiles_n = (N + 7) / 8;
+    const int tm = warp / tiles_n, tn = warp - (warp / tiles_n) * tiles_n;
+    if (tm * 16 >= M) return;
+    const int g = lane >> 2, t = lane & 3;
+    const int m0 = tm * 16, n0 = tn * 8;
+    const __nv_bfloat16 z = __float2bfloat16(0.f);
+    auto a_at = [&](int m, int k) { return (m < M && k < K) ? A[m * sam + k * sak] : z; };
+    auto b_at = [&](int k, int n) { return (k < K && n < N) ? B[k * sbk + n * sbn] : z; };
+    float c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f;
+    for (int k0 = 0; k0 < K; k0 += 16) {
+        const unsigned a0 = pack_bf16(a_at(m0 + g, k0 + 2 * t), a_at(m0 + g, k0 + 2 * t + 1));
+        const unsigned a1 = pack_bf16(a_at(m0 + g + 8, k0 + 2 * t), a_at(m0 + g + 8, k0 + 2 * t + 1));
+        const unsigned a2 = pack_bf16(a_at(m0 + g, k0 + 2 * t + 8), a_at(m0 + g, k0 + 2 * t + 9));
+        const unsigned a3 = pack_bf16(a_at(m0 + g + 8, k0 + 2 * t + 8), a_at(m0 + g + 8, k0 + 2 * t + 9));
+        const unsigned b0 = pack_bf16(b_at(k0 + 2 * t, n0 + g), b_at(k0 + 2 * t + 1, n0 + g));
+        const unsigned b1 = pack_bf16(b_at(k0 + 2 * t + 8, n0 + g), b_at(k0 + 2 * t + 9, n0 + g));
+        asm volatile(
+            "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+            "{%0,%1,%2,%3};"
+            : "+f"(c0), "+f"(c1), "+f"(c2), "+f"(c3)
+            : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+    }
+    const int r0 = m0 + g, r1 = m0 + g + 8, cA = n0 + 2 * t, cB = n0 + 2 * t + 1;
+    if (r0 < M && cA < N) C[(long)r0 * ldc + cA] = c0;
+    if (r0 < M && cB < N) C[(long)r0 * ldc + cB] = c1;
+    if (r1 < M && cA < N) C[(long)r1 * ldc + cA] = c2;
+    if (r1 < M && cB < N) C[(long)r1 * ldc + cB] = c3;
+}
+
+__device__ __forceinline__ float silu_f(float z) { return z / (1.f + __expf(-z)); }
+__device__ __forceinline__ float silu_g(float z) {
+    const float s = 1.f / (1.f + __expf(-z));
+    return s * (1.f + z * (1.f - s));
+}
+
+// x (FP32) -> BF16 activations
+__global__ void k_to_bf16(const float* __restrict__ x, __nv_bfloat16* __restrict__ a, long n) {
+    const long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (i < n) a[i] = __float2bfloat16(x[i]);
+}
+
+// Z += b (per column); hidden layers: A = bf16(silu(Z)); output layer: Y = Z
+__global__ void k_bias_act(float* __restrict__ Z, const float* __restrict__ b, int n, int cols, int hidden,
+                           __nv_bfloat16* __restrict__ Aout, float* __restrict__ Y) {
+    const long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (i >= (long)n * cols) return;
+    const float z = Z[i] + b[i % cols];
+    Z[i] = z;
+    if (hidden)
+        Aout[i] = __float2bfloat16(silu_f(z));
+    else
+        Y[i] = z;
+}
+
+// dY = 2 (Y - T) / (n cols); loss partial sums
+__global__ void k_loss_grad(const float* __restrict__ Y, const float* __restrict__ T, long total,
+                            float* __restrict__ dZ, __nv_bfloat16* __restrict__ dZh, double* __restrict__ loss) {
+    const long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    double l = 0.0;
+    if (i < total) {
+        const float d = Y[i] - T[i];
+        dZ[i] = 2.f * d / (float)total;
+        dZh[i] = __float2bfloat16(dZ[i]);
+        l = (double)d * (double)d;
+    }
+    if (loss) {
+        for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
+        if ((threadIdx.x & 31) == 0) atomicAdd(loss, l / (double)total);
+    }
+}
+
+// dZ = dA * silu'(Z) (hidden layer), also its BF16 copy
+__global__ void k_act_back(const float* __restrict__ dA, const float* __restrict__ Z, long total,
+                           float* __restrict__ dZ, __nv_bfloat16* __restrict__ dZh) {
+    const long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (i >= total) return;
+    const float d = dA[i] * silu_g(Z[i]);
+    dZ[i] = d;
+    dZh[i] = __float2bfloat16(d);
+}
+
+// db[j] = sum_m dZ[m][j] (fixed order, one thread per column)
+__global__ void k_colsum(const float* __restrict__ dZ, int n, int cols, float* __restrict__ db) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= cols) return;
+    float s = 0.f;
+    for (int m = 0; m < n; ++m) s += dZ[(long)m * cols + j];
+    db[j] = s;
+}
+
+// Adam on every parameter; refresh the BF16 copy of the weights
+__global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+                       float* __restrict__ v, long n, float lr, float b1, float b2, float eps, float c1, float c2,
+                       __nv_bfloat16* __restrict__ ph, const unsigned char* __restrict__ is_w) {
+    const long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float w = p[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    p[i] = w;
+    if (is_w[i]) ph[i] = __float2bfloat16(w);
+}
+
+__global__ void k_params_bf16(const float* __restrict__ p, __nv_bfloat16* __restrict__ ph, long n) {
+    const long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (i < n) ph[i] = __float2bfloat16(p[i]);
+}
+
+struct Buf {
+    void* p = nullptr;
+    size_t n = 0;
+    int ensure(size_t bytes) {
+        if (bytes <= n) return MIRAGE_OK;
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+        if (cudaMalloc(&p, bytes) != cudaSuccess) return mlp_fail(MIRAGE_ERR_NOMEM, "mlp: cudaMalloc failed");
+        n = bytes;
+        return MIRAGE_OK;
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+};
+
+inline unsigned blocks(long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+}  // namespace
+
+struct mirage_mlp {
+    int device = 0;
+    int L = 0;                 // weight layers
+    std::vector<int> dims;     // L + 1
+    std::vector<long> w_off, b_off;
+    long n_params = 0;
+    int step = 0;
+    float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    Buf P, PH, M, V, G, ISW;   // params FP32, BF16 copy, Adam m, v, grads, weight mask
+    Buf Z, A, DZ, DZH, DA, LOSS;  // per-batch work (grown on demand)
+    long cap_rows = 0;
+    std::vector<long> z_off, a_off;  // per layer offsets into Z / A (elements)
+};
+
+namespace {
+
+int ensure_batch(mirage_mlp* m, int n) {
+    if (n <= m->cap_rows) return MIRAGE_OK;
+    long zt = 0, at = 0;
+    m->z_off.assign(m->L + 1, 0);
+    m->a_off.assign(m->L + 1, 0);
+    int maxw = 0;
+    for (int l = 0; l <= m->L; ++l) {
+        m->a_off[l] = at;
+        at += (long)n * m->dims[l];
+        maxw = std::max(maxw, m->dims[l]);
+        if (l > 0) {
+            m->z_off[l] = zt;
+            zt += (long)n * m->dims[l];
+        }
+    }
+    int r;
+    if ((r = m->Z.ensure(sizeof(float) * zt))) return r;
+    if ((r = m->A.ensure(sizeof(__nv_bfloat16) * at))) return r;
+    if ((r = m->DZ.ensure(sizeof(float) * (long)n * maxw))) return r;
+    if ((r = m->DZH.ensure(sizeof(__nv_bfloat16) * (long)n * maxw))) return r;
+    if ((r = m->DA.ensure(sizeof(float) * (long)n * maxw))) return r;
+    if ((r = m->LOSS.ensure(sizeof(double)))) return r;
+    m->cap_rows = n;
+    return MIRAGE_OK;
+}
+
+int gemm(const __nv_bfloat16* A, long sam, long sak, const __nv_bfloat16* B, long sbk, long sbn, float* C, int ldc,
+         int M, int N, int K, cudaStream_t st) {
+    const long warps = (long)((M + 15) / 16) * ((N + 7) / 8);
+    k_gemm_bf16<<<blocks(warps * 32, 128), 128, 0, st>>>(A, sam, sak, B, sbk, sbn, C, ldc, M, N, K);
+    MCK(cudaGetLastError());
+    return MIRAGE_OK;
+}
+
+// forward pass storing Z (FP32) and A (BF16); Y (FP32) written to y
+int forward_pass(mirage_mlp* m, const float* x, int n, float* y, cudaStream_t st) {
+    int r;
+    if ((r = ensure_batch(m, n))) return r;
+    float* Z = (float*)m->Z.p;
+    __nv_bfloat16* A = (__nv_bfloat16*)m->A.p;
+    const float* P = (const float*)m->P.p;
+    const __nv_bfloat16* PH = (const __nv_bfloat16*)m->PH.p;
+    k_to_bf16<<<blocks((long)n * m->dims[0], 256), 256, 0, st>>>(x, A, (long)n * m->dims[0]);
+    for (int l = 1; l <= m->L; ++l) {
+        const int in = m->dims[l - 1], out = m->dims[l];
+        // Z_l = A_{l-1} W_l^T : A(m, k) = A[m in + k], B(k, j) = W[j in + k]
+        if ((r = gemm(A + m->a_off[l - 1], in, 1, PH + m->w_off[l - 1], 1, in, Z + m->z_off[l], out, n, out, in, st)))
+            return r;
+        const bool hidden = l < m->L;
+        k_bias_act<<<blocks((long)n * out, 256), 256, 0, st>>>(Z + m->z_off[l], P + m->b_off[l - 1], n, out, hidden,
+                                                               A + m->a_off[l], y);
+        MCK(cudaGetLastError());
+    }
+    return MIRAGE_OK;
+}
+
+// gradients of the MSE into m->G (and the loss into m->LOSS if wanted)
+int backward_pass(mirage_mlp* m, const float* x, const float* tgt, int n, float* yscratch, bool want_loss,
+                  cudaStream_t st) {
+    int r;
+    if ((r = forward_pass(m, x, n, yscratch, st))) return r;
+    float* Z = (float*)m->Z.p;
+    __nv_bfloat16* A = (__nv_bfloat16*)m->A.p;
+    float* DZ = (float*)m->DZ.p;
+    __nv_bfloat16* DZH = (__nv_bfloat16*)m->DZH.p;
+    float* DA = (float*)m->DA.p;
+    float* G = (float*)m->G.p;
+    const __nv_bfloat16* PH = (const __nv_bfloat16*)m->PH.p;
+    double* loss = want_loss ? (double*)m->LOSS.p : nullptr;
+    if (loss) MCK(cudaMemsetAsync(loss, 0, sizeof(double), st));
+    const int outL = m->dims[m->L];
+    k_loss_grad<<<blocks((long)n * outL, 256), 256, 0, st>>>(yscratch, tgt, (long)n * outL, DZ, DZH, loss);
+    MCK(cudaGetLastError());
+    for (int l = m->L; l >= 1; --l) {
+        const int in = m->dims[l - 1], out = m->dims[l];
+        // dW_l = dZ^T A_{l-1}: [out x in];  A(mm, k) = dZ[k out + mm], B(k, j) = A_{l-1}[k in + j]
+        if ((r = gemm(DZH, 1, out, A + m->a_off[l - 1], in, 1, G + m->w_off[l - 1], in, out, in, n, st))) return r;
+        k_colsum<<<blocks(out, 128), 128, 0, st>>>(DZ, n, out, G + m->b_off[l - 1]);
+        MCK(cudaGetLastError());
+        if (l > 1) {
+            // dA_{l-1} = dZ W_l: A(mm, k) = dZ[mm out + k], B(k, j) = W[k in + j]
+            if ((r = gemm(DZH, out, 1, PH + m->w_off[l - 1], in, 1, DA, in, n, in, out, st))) return r;
+            k_act_back<<<blocks((long)n * in, 256), 256, 0, st>>>(DA, Z + m->z_off[l - 1], (long)n * in, DZ, DZH);
+            MCK(cudaGetLastError());
+        }
+    }
+    return MIRAGE_OK;
+}
+
+// deterministic host RNG (splitmix64 + Box-Muller) for the initial weights
+struct HostRng {
+    unsigned long long s;
+    unsigned long long next() {
+        unsigned long long z = (s += 0x9E3779B97F4A7C15ull);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        return z ^ (z >> 31);
+    }
+    double uniform() { return ((next() >> 11) + 0.5) * (1.0 / 9007199254740992.0); }
+    double normal() { return std::sqrt(-2.0 * std::log(uniform())) * std::cos(6.283185307179586 * uniform()); }
+};
+
+}  // namespace
+
+extern "C" {
+
+int mirage_mlp_create(mirage_mlp_t** out, int device, int n_layers, const int* dims, unsigned long long seed) {
+    if (!out || n_layers < 1 || n_layers > 16 || !dims) return mlp_fail(MIRAGE_ERR_ARG, "mlp_create: bad arguments");
+    *out = nullptr;
+    for (int l = 0; l <= n_layers; ++l)
+        if (dims[l] < 1 || dims[l] > 4096) return mlp_fail(MIRAGE_ERR_ARG, "mlp_create: layer width out of range");
+    MCK(cudaSetDevice(device));
+    mirage_mlp* m = new mirage_mlp();
+    m->device = device;
+    m->L = n_layers;
+    m->dims.assign(dims, dims + n_layers + 1);
+    long off = 0;
+    for (int l = 0; l < n_layers; ++l) {
+        m->w_off.push_back(off);
+        off += (long)dims[l + 1] * dims[l];
+        m->b_off.push_back(off);
+        off += dims[l + 1];
+    }
+    m->n_params = off;
+    int r = 0;
+    if ((r = m->P.ensure(sizeof(float) * off)) || (r = m->PH.ensure(sizeof(__nv_bfloat16) * off)) ||
+        (r = m->M.ensure(sizeof(float) * off)) || (r = m->V.ensure(sizeof(float) * off)) ||
+        (r = m->G.ensure(sizeof(float) * off)) || (r = m->ISW.ensure(off))) {
+        delete m;
+        return r;
+    }
+    // He-style initial weights (std sqrt(2 / fan_in)), zero biases
+    std::vector<float> h(off, 0.f);
+    std::vector<unsigned char> isw(off, 0);
+    HostRng rng{seed};
+    for (int l = 0; l < n_layers; ++l) {
+        const double sd = std::sqrt(2.0 / dims[l]);
+        for (long i = 0; i < (long)dims[l + 1] * dims[l]; ++i) {
+            h[m->w_off[l] + i] = (float)(sd * rng.normal());
+            isw[m->w_off[l] + i] = 1;
+        }
+    }
+    if (cudaMemcpy(m->ISW.p, isw.data(), off, cudaMemcpyHostToDevice) != cudaSuccess) {
+        delete m;
+        return mlp_fail(MIRAGE_ERR_CUDA, "mlp_create: upload failed");
+    }
+    *out = m;
+    return mirage_mlp_set_params(m, h.data(), off);
+}
+
+int mirage_mlp_destroy(mirage_mlp_t* m) {
+    if (!m) return MIRAGE_OK;
+    cudaSetDevice(m->device);
+    Buf* bufs[] = {&m->P, &m->PH, &m->M, &m->V, &m->G, &m->ISW, &m->Z, &m->A, &m->DZ, &m->DZH, &m->DA, &m->LOSS};
+    for (Buf* b : bufs) b->release();
+    delete m;
+    return MIRAGE_OK;
+}
+
+long mirage_mlp_num_params(const mirage_mlp_t* m) { return m ? m->n_params : 0; }
+
+int mirage_mlp_set_params(mirage_mlp_t* m, const float* host_params, long n) {
+    if (!m || !host_params || n != m->n_params) return mlp_fail(MIRAGE_ERR_ARG, "mlp_set_params: size mismatch");
+    MCK(cudaSetDevice(m->device));
+    MCK(cudaMemcpy(m->P.p, host_params, sizeof(float) * n, cudaMemcpyHostToDevice));
+    MCK(cudaMemset(m->M.p, 0, sizeof(float) * n));
+    MCK(cudaMemset(m->V.p, 0, sizeof(float) * n));
+    k_params_bf16<<<blocks(n, 256), 256>>>((const float*)m->P.p, (__nv_bfloat16*)m->PH.p, n);
+    MCK(cudaGetLastError());
+    MCK(cudaDeviceSynchronize());
+    m->step = 0;
+    return MIRAGE_OK;
+}
+
+int mirage_mlp_get_params(const mirage_mlp_t* m, float* host_params, long n) {
+    if (!m || !host_params || n != m->n_params) return mlp_fail(MIRAGE_ERR_ARG, "mlp_get_params: size mismatch");
+    MCK(cudaSetDevice(m->device));
+    MCK(cudaMemcpy(host_params, m->P.p, sizeof(float) * n, cudaMemcpyDeviceToHost));
+    return MIRAGE_OK;
+}
+
+int mirage_mlp_forward(mirage_mlp_t* m, const float* x, int n, float* y, void* stream) {
+    if (!m || !x || !y || n < 0) return mlp_fail(MIRAGE_ERR_ARG, "mlp_forward: bad arguments");
+    if (n == 0) return MIRAGE_OK;
+    MCK(cudaSetDevice(m->device));
+    return forward_pass(m, x, n, y, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int mirage_mlp_grad(mirage_mlp_t* m, const float* x, const float* t, int n, float* grad, double* loss, float* y,
+                    void* stream) {
+    if (!m || !x || !t || !y || n < 1) return mlp_fail(MIRAGE_ERR_ARG, "mlp_grad: bad arguments");
+    MCK(cudaSetDevice(m->device));
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    int r = backward_pass(m, x, t, n, y, loss != nullptr, st);
+    if (r) return r;
+    if (grad) MCK(cudaMemcpyAsync(grad, m->G.p, sizeof(float) * m->n_params, cudaMemcpyDeviceToDevice, st));
+    if (loss) MCK(cudaMemcpyAsync(loss, m->LOSS.p, sizeof(double), cudaMemcpyDeviceToDevice, st));
+    return MIRAGE_OK;
+}
+
+int mirage_mlp_train_step(mirage_mlp_t* m, const float* x, const float* t, int n, float lr, double* loss, float* y,
+                          void* stream) {
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    int r = mirage_mlp_grad(m, x, t, n, nullptr, loss, y, stream);
+    if (r) return r;
+    m->step += 1;
+    const float c1 = 1.f - std::pow(m->b1, (float)m->step), c2 = 1.f - std::pow(m->b2, (float)m->step);
+    k_adam<<<blocks(m->n_params, 256), 256, 0, st>>>((float*)m->P.p, (const float*)m->G.p, (float*)m->M.p,
+                                                     (float*)m->V.p, m->n_params, lr, m->b1, m->b2, m->eps, c1, c2,
+                                                     (__nv_bfloat16*)m->PH.p, (const unsigned char*)m->ISW.p);
+    MCK(cudaGetLastError());
+    return MIRAGE_OK;
+}
+
+const char* mirage_mlp_last_error(void) { return g_mlp_err.c_str(); }
+
+}  // extern "C"

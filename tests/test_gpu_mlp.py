@@ -1,0 +1,102 @@
+"""GPU parity of the surrogate network's BF16 kernels against the FP64 oracle.
+
+The oracle runs with the same BF16-rounded weights; the GPU also rounds
+activations and output gradients to BF16 before each tensor-core product,
+so forward outputs agree to ~1e-2 relative and gradients to a cosine
+similarity above 0.999 (BF16 keeps 8 significant bits).
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle.mlp import Adam, backward, bf16_round, forward
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def binding():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1101_5803_gb300 import binding as b
+    return b
+
+
+def _oracle_params(net, flat=None):
+    return [(bf16_round(W).reshape(W.shape), b.astype(np.float64)) for W, b in net.layers(flat)]
+
+
+@pytest.mark.parametrize("dims", [[7, 64, 48, 2], [7, 256, 256, 256, 2]])
+def test_forward_and_gradients(binding, dims):
+    net = binding.MLP(dims, seed=1)
+    rng = np.random.default_rng(0)
+    X = rng.standard_normal((300, 7)).astype(np.float32)
+    T = rng.standard_normal((300, 2)).astype(np.float32)
+    xg, tg = torch.as_tensor(X, device="cuda"), torch.as_tensor(T, device="cuda")
+    params = _oracle_params(net)
+    Yo, _ = forward(params, bf16_round(X))
+    Yg = net.forward(xg).cpu().numpy()
+    assert np.abs(Yg - Yo).max() <= 2e-2 * np.abs(Yo).max()
+    g, loss, _ = net.grad(xg, tg)
+    torch.cuda.synchronize()
+    go = backward(params, bf16_round(X), T.astype(np.float64))
+    flat_o = np.concatenate([np.concatenate([gw.ravel(), gb.ravel()]) for gw, gb in go])
+    gg = g.cpu().numpy().astype(np.float64)
+    o = 0
+    for (gw, gb) in go:
+        for ref in (gw.ravel(), gb.ravel()):
+            part = gg[o:o + ref.size]
+            o += ref.size
+            cos = part @ ref / (np.linalg.norm(part) * np.linalg.norm(ref) + 1e-300)
+            assert cos > 0.999, cos
+            assert np.linalg.norm(part - ref) <= 5e-2 * np.linalg.norm(ref)
+    assert o == flat_o.size
+    lo = np.mean((Yo - T) ** 2)
+    assert abs(loss.item() - lo) <= 2e-2 * lo
+    net.close()
+
+
+def test_adam_step_matches_oracle(binding):
+    net = binding.MLP([7, 32, 2], seed=2)
+    rng = np.random.default_rng(1)
+    X = rng.standard_normal((64, 7)).astype(np.float32)
+    T = rng.standard_normal((64, 2)).astype(np.float32)
+    p0 = net.get_params().astype(np.float64)
+    xg, tg = torch.as_tensor(X, device="cuda"), torch.as_tensor(T, device="cuda")
+    g, _, _ = net.grad(xg, tg)
+    g = g.cpu().numpy().astype(np.float64)
+    net.train_step(xg, tg, 1e-2)
+    p1 = net.get_params().astype(np.float64)
+    # the first Adam step moves each parameter by -lr g / (|g| + eps): the
+    # oracle's Adam applied to the GPU's gradient must give the same move
+    lay, o = [], 0
+    for i, j in zip([7, 32], [32, 2]):
+        lay.append((p0[o:o + i * j].reshape(j, i), p0[o + i * j:o + i * j + j]))
+        o += i * j + j
+    glay, o = [], 0
+    for i, j in zip([7, 32], [32, 2]):
+        glay.append((g[o:o + i * j].reshape(j, i), g[o + i * j:o + i * j + j]))
+        o += i * j + j
+    new = Adam(lay, lr=1e-2).step(lay, glay)
+    ref = np.concatenate([np.concatenate([W.ravel(), b.ravel()]) for W, b in new])
+    np.testing.assert_allclose(p1, ref, atol=2e-6)
+    net.close()
+
+
+def test_training_fits_a_smooth_map(binding):
+    net = binding.MLP([7, 64, 64, 2], seed=3)
+    rng = np.random.default_rng(4)
+    X = rng.uniform(-1, 1, (2048, 7)).astype(np.float32)
+    T = np.stack([np.sin(X[:, 0] * 2) + X[:, 1] * X[:, 2], np.cos(X[:, 3]) - 0.5 * X[:, 4] ** 2], 1)
+    T = T.astype(np.float32)
+    xg, tg = torch.as_tensor(X, device="cuda"), torch.as_tensor(T, device="cuda")
+    first = None
+    for it in range(1500):
+        idx = torch.as_tensor(rng.integers(0, 2048, 256), device="cuda")
+        loss = net.train_step(xg[idx], tg[idx], 3e-3)
+        if first is None:
+            first = loss.item()
+    Y = net.forward(xg).cpu().numpy()
+    mse = float(np.mean((Y - T) ** 2))
+    assert mse < 0.02 * first and mse < 5e-3, (first, mse)
+    net.close()

@@ -277,6 +277,24 @@ def run_gpu(args):
         except Exception:
             traffic = None
 
+    # GA generations on the same problem: surrogate screen vs none
+    from paper_1101_5803_gb300.ga import GAConfig, run_ga
+    n_gen = int(os.environ.get("MIRAGE_GA_GENERATIONS", "4"))
+    ga_res = {}
+    for name, sur_on in (("with_surrogate", True), ("without", False)):
+        cfg = GAConfig(pop=N_CAND, generations=n_gen, surrogate=sur_on, seed=7)
+        hist, _, bchi = run_ga(ctx, wl, cfg)
+        gens = hist[1:]
+        t_gen = sum(h.seconds for h in gens)
+        ga_res[name] = {"exact_evals_per_s": sum(h.exact_evals for h in gens) / t_gen,
+                        "decisions_per_s": sum(h.decisions for h in gens) / t_gen,
+                        "best_chi2_by_gen": [round(h.best_chi2, 2) for h in hist],
+                        "screened_gens": int(sum(h.screened for h in gens)),
+                        "rank_corr_by_gen": [None if h.surrogate_rho is None else round(h.surrogate_rho, 3)
+                                             for h in gens]}
+    ga_res["generations"] = n_gen
+    ga_res["oversample"] = 4
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         v, done, dt = oracle_evals_per_s(64, seed=7, budget_s=float(os.environ.get("MIRAGE_CPU_BUDGET", "20")))
@@ -294,7 +312,7 @@ def run_gpu(args):
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_basis": f"FP32 FFMA: {nsm} SMs x 128 lanes x 2 x {smax:.0f} MHz ({src} max clock)",
                          "frac_at_measured_clock": (achieved / at_clock) if at_clock else None,
-                         "kernel": "k_cgls<float,9,smem>", "kernel_ms": phase[1],
+                         "kernel": "k_cgls_fast<9,4,param-taps FFMA2> (two CTAs/SM)", "kernel_ms": phase[1],
                          "flops_per_launch": flops},
             "cpu_baseline": cpu,
             "plain": {"value": plain, "unit": UNIT, "sample": n_plain, "speedup_batched_vs_plain": value / plain,
@@ -305,7 +323,8 @@ def run_gpu(args):
                    "relres_true_max": float(relres.max()), "relres_true_median": float(np.median(relres)),
                    "items_converged_frac": float(((item_status & 7) == 0).mean()),
                    "status_bits_any": int(np.bitwise_or.reduce(status))},
-            "phase_ms": {"raytrace": phase[0], "cgls": phase[1], "finalize": phase[2]}}
+            "phase_ms": {"raytrace": phase[0], "cgls": phase[1], "finalize": phase[2]},
+            "ga_surrogate": ga_res}
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()

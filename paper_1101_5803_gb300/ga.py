@@ -1,0 +1,216 @@
+"""Genetic algorithm around the batched evaluator, with a learned screen.
+
+The outer loop of Section 3 (the paper uses the Ferret GA, Appendix A.1):
+a real-valued population inside a bounded search box, offspring made by
+blend ("X-type") crossover along the line between two tournament-selected
+parents (the fraction drawn from a Gaussian of width 0.25 about the
+midpoint, so children may overshoot) and Gaussian mutation (probability
+0.05 per gene, width 0.25 of the gene's range), and binary tournaments
+between offspring and the parent population.  The fitness of a lens is the
+chi^2 of its L-curve corner solution (Section 2.6).
+
+With a surrogate, each generation draws ``oversample`` times more
+offspring than it can afford exact solves for, ranks them by the
+surrogate's predicted corner chi^2, evaluates only the best ``pop`` exactly
+(every survivor is judged by the exact solve), and trains the network on
+the new exact results.  The screen ranks, so its quality is judged by the rank
+correlation between predicted and exact corner chi^2 on the latest exact
+results: below ``fallback_rho`` the screen is switched off for the next
+generation (offspring drawn without ranking), and back on when it
+recovers.  Warm-starting the children's CG from their parents' solutions
+is available but off by default: a parent's source is a poor start for a
+different lens and measured more CG iterations, not fewer.
+"""
+from __future__ import annotations
+
+import dataclasses
+import time
+
+import numpy as np
+import torch
+
+import synth
+
+from .binding import MLP, Context
+from .problems import Workload
+
+
+def encode(lens: np.ndarray) -> np.ndarray:
+    """Continuous features of lens vectors: the SIE is pi-periodic in phi and
+    the shear in theta_g, so the angles enter through doubled-angle terms."""
+    b, q, phi, x0, y0, g, tg = np.asarray(lens, dtype=np.float64).T
+    return np.stack([b, (1 - q) * np.cos(2 * phi), (1 - q) * np.sin(2 * phi), x0, y0,
+                     g * np.cos(2 * tg), g * np.sin(2 * tg)], axis=1)
+
+
+@dataclasses.dataclass
+class GAConfig:
+    pop: int = 512
+    generations: int = 20
+    oversample: int = 4
+    p_mutate: float = 0.05
+    mutate_scale: float = 0.25
+    xover_strength: float = 0.25
+    tol: float = 1e-6
+    surrogate: bool = True
+    warm_start: bool = False
+    hidden: int = 256
+    train_steps: int = 200
+    batch: int = 256
+    lr: float = 2e-3
+    fallback_rho: float = 0.3
+    seed: int = 0
+
+
+@dataclasses.dataclass
+class GenStats:
+    gen: int
+    best_chi2: float
+    exact_evals: int
+    decisions: int
+    cg_iters: int
+    seconds: float
+    surrogate_rmse: float | None
+    surrogate_rho: float | None
+    screened: bool
+
+
+class Surrogate:
+    """Online-trained network mapping encoded lens -> standardised
+    (log chi2*, log10 lambda*)."""
+
+    def __init__(self, hidden: int, seed: int, device: int = 0):
+        self.net = MLP([7, hidden, hidden, hidden, 2], device=device, seed=seed)
+        self.X: list[np.ndarray] = []
+        self.Y: list[np.ndarray] = []
+        self.mu = self.sd = self.ymu = self.ysd = None
+
+    def add(self, lens: np.ndarray, chi2: np.ndarray, lam: np.ndarray):
+        ok = np.isfinite(chi2) & (chi2 > 0)
+        self.X.append(encode(lens[ok]))
+        self.Y.append(np.stack([np.log(chi2[ok]), np.log10(lam[ok])], axis=1))
+
+    def _norm(self):
+        X, Y = np.concatenate(self.X), np.concatenate(self.Y)
+        self.mu, self.sd = X.mean(0), X.std(0) + 1e-9
+        self.ymu, self.ysd = Y.mean(0), Y.std(0) + 1e-9
+        return X, Y
+
+    def train(self, steps: int, batch: int, lr: float, rng) -> None:
+        X, Y = self._norm()
+        xs = torch.as_tensor(((X - self.mu) / self.sd).astype(np.float32), device="cuda")
+        ys = torch.as_tensor(((Y - self.ymu) / self.ysd).astype(np.float32), device="cuda")
+        n = xs.shape[0]
+        for _ in range(steps):
+            idx = torch.as_tensor(rng.integers(0, n, min(batch, n)), device="cuda")
+            self.net.train_step(xs[idx], ys[idx], lr)
+
+    def predict(self, lens: np.ndarray) -> np.ndarray:
+        """Standardised predictions [n, 2] (log chi2*, log10 lambda*)."""
+        x = torch.as_tensor(((encode(lens) - self.mu) / self.sd).astype(np.float32), device="cuda")
+        return self.net.forward(x).cpu().numpy().astype(np.float64)
+
+    def rmse(self, lens, chi2, lam) -> float:
+        ok = np.isfinite(chi2) & (chi2 > 0)
+        y = np.stack([np.log(chi2[ok]), np.log10(lam[ok])], axis=1)
+        p = self.predict(lens[ok])
+        return float(np.sqrt(np.mean(((y - self.ymu) / self.ysd - p) ** 2)))
+
+
+def rank_corr(a, b) -> float:
+    """Spearman rank correlation of two samples (no tie correction)."""
+    ra = np.argsort(np.argsort(a)).astype(np.float64)
+    rb = np.argsort(np.argsort(b)).astype(np.float64)
+    ra -= ra.mean()
+    rb -= rb.mean()
+    den = np.sqrt((ra * ra).sum() * (rb * rb).sum())
+    return float((ra * rb).sum() / den) if den > 0 else 0.0
+
+
+def _offspring(pop: np.ndarray, fit: np.ndarray, n: int, cfg: GAConfig, rng):
+    """n children by tournament selection, blend crossover, Gaussian mutation;
+    returns (children, index of each child's first parent)."""
+    lo, hi = synth.LENS_LO, synth.LENS_HI
+    m = pop.shape[0]
+
+    def tourney(k):
+        a, b = rng.integers(0, m, k), rng.integers(0, m, k)
+        return np.where(fit[a] <= fit[b], a, b)
+
+    p1, p2 = tourney(n), tourney(n)
+    r = 0.5 + cfg.xover_strength * rng.standard_normal((n, 1))
+    kids = pop[p1] + r * (pop[p2] - pop[p1])
+    mut = rng.uniform(size=kids.shape) < cfg.p_mutate
+    kids = kids + mut * rng.standard_normal(kids.shape) * cfg.mutate_scale * (hi - lo)
+    return np.clip(kids, lo, hi), p1
+
+
+def run_ga(ctx: Context, wl: Workload, cfg: GAConfig, log=None):
+    """Run the GA on one problem; returns (history, best lens, best chi2)."""
+    rng = np.random.default_rng(cfg.seed)
+    n_lam = int(wl.lambdas.shape[1])
+    lam_row = wl.lambdas[0].cpu().numpy()
+    pop = synth.lens_population(rng, cfg.pop)
+    lam_dev = wl.lambdas[:1].expand(cfg.pop, n_lam).contiguous()
+    probs = [wl.problem]
+    pidx = np.zeros(cfg.pop, np.int32)
+    nl = np.full(cfg.pop, n_lam, np.int32)
+    sur = Surrogate(cfg.hidden, cfg.seed) if cfg.surrogate else None
+
+    def evaluate(lens, warm):
+        out = ctx.eval_batch(probs, torch.as_tensor(lens, device="cuda"), pidx, lam_dev, nl, tol=cfg.tol,
+                             warm_x=warm, want_all_x=True)
+        chi2 = out["chi2"].cpu().numpy()
+        corner = out["corner"].cpu().numpy()
+        fit = chi2[np.arange(len(lens)), corner]
+        fit = np.where(np.isfinite(fit), fit, np.inf)
+        return fit, lam_row[corner], out
+
+    t0 = time.perf_counter()
+    fit, lam_star, out = evaluate(pop, None)
+    X_pop = out["all_x"]
+    hist = [GenStats(0, float(fit.min()), cfg.pop, cfg.pop, int(out["iters"].sum().item()),
+                     time.perf_counter() - t0, None, None, False)]
+    if sur is not None:
+        sur.add(pop, fit, lam_star)
+        sur.train(cfg.train_steps * 3, cfg.batch, cfg.lr, rng)
+    screen = sur is not None
+    for gen in range(1, cfg.generations + 1):
+        t0 = time.perf_counter()
+        n_draw = cfg.pop * (cfg.oversample if screen else 1)
+        kids, par = _offspring(pop, fit, n_draw, cfg, rng)
+        if screen:
+            pred = sur.predict(kids)[:, 0]
+            keep = np.argsort(pred)[:cfg.pop]
+            kids, par = kids[keep], par[keep]
+        warm = X_pop[par].contiguous() if cfg.warm_start else None
+        kfit, klam, kout = evaluate(kids, warm)
+        rm = rho = None
+        was_screened = screen
+        if sur is not None:
+            rm = sur.rmse(kids, kfit, klam)
+            ok = np.isfinite(kfit)
+            rho = rank_corr(sur.predict(kids[ok])[:, 0], kfit[ok]) if ok.sum() > 2 else 0.0
+            screen = rho >= cfg.fallback_rho
+            sur.add(kids, kfit, klam)
+            sur.train(cfg.train_steps, cfg.batch, cfg.lr, rng)
+        # binary tournaments between offspring and parents (mu + lambda)
+        allp = np.concatenate([pop, kids])
+        allf = np.concatenate([fit, kfit])
+        allx = torch.cat([X_pop, kout["all_x"]])
+        a = rng.permutation(cfg.pop)
+        b = cfg.pop + rng.permutation(cfg.pop)
+        win = np.where(allf[a] <= allf[b], a, b)
+        # keep the best individual found so far
+        best = int(np.argmin(allf))
+        if best not in win:
+            win[np.argmax(allf[win])] = best
+        pop, fit = allp[win], allf[win]
+        X_pop = allx[torch.as_tensor(win, device="cuda")].contiguous()
+        st = GenStats(gen, float(fit.min()), cfg.pop, n_draw, int(kout["iters"].sum().item()),
+                      time.perf_counter() - t0, rm, rho, bool(was_screened))
+        hist.append(st)
+        if log:
+            log(st)
+    b = int(np.argmin(fit))
+    return hist, pop[b], float(fit[b])

@@ -111,6 +111,8 @@ struct mirage_ctx {
     std::map<std::string, GraphEntry> graphs;
     std::map<const void*, int> smem_set;  // kernel -> dynamic smem attribute set
     cudaStream_t cap_stream = nullptr;   // graphs are captured here and launched on the caller's stream
+    cudaStream_t side[4] = {nullptr, nullptr, nullptr, nullptr};  // concurrent kernel groups
+    cudaEvent_t fork_ev = nullptr, join_ev[4] = {nullptr, nullptr, nullptr, nullptr};
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // phase timing (opts.threads < 0)
     DevBuf clk;                                                  // per-phase SM clocks (opts.threads == -2)
     int timed = 0;
@@ -212,10 +214,18 @@ int set_smem(mirage_ctx* ctx, const void* fn, size_t bytes) {
     return MIRAGE_OK;
 }
 
-const void* pick_cgls(int prec, bool big, int K) {
+const void* pick_cgls(int prec, int place, int K) {
     const KernelTable& t = table();
-    const void* f = t.cgls[prec][big][K];
-    return f ? f : t.cgls[prec][big][0];
+    const void* f = t.cgls[prec][place][K];
+    return f ? f : t.cgls[prec][place][0];
+}
+
+// placement of the general kernel's work buffers for one problem
+template <typename T>
+int pick_place(const mirage_ctx* ctx, const Prob<T>& P) {
+    if (smem_bytes<T>(P, PLACE_SMEM) <= (size_t)ctx->max_smem) return PLACE_SMEM;
+    if (sizeof(T) == 4 && smem_bytes<T>(P, PLACE_MID) <= (size_t)ctx->max_smem) return PLACE_MID;
+    return PLACE_GLOBAL;
 }
 
 const void* pick_fwd(int prec, int K) {
@@ -438,6 +448,7 @@ int eval_impl(mirage_ctx* ctx, const mirage_problem_t* probs, int n_probs, const
         bool fast = false;
         int prob = -1;   // the single problem of the group, -2 if several
         int per_sm = 1;  // resident CTAs per SM
+        double cost = 0.0;
         size_t smem = 0;
         long long slab = 0;
         std::vector<std::pair<double, int>> items;  // (sort key, packed)
@@ -472,11 +483,11 @@ int eval_impl(mirage_ctx* ctx, const mirage_problem_t* probs, int n_probs, const
     };
     for (int c = 0; c < n_cand; ++c) {
         const Prob<T>& P = hp[prob_idx[c]];
-        const size_t sm = smem_bytes<T>(P, false);
-        const bool big = sm > (size_t)ctx->max_smem;
-        const void* fn = pick_cgls(prec, big, P.K);
-        size_t item_smem = smem_bytes<T>(P, big);
-        long long item_slab = (long long)slab_bytes<T>(P, big);
+        const int place = pick_place<T>(ctx, P);
+        const bool big = place != PLACE_SMEM;
+        const void* fn = pick_cgls(prec, place, P.K);
+        size_t item_smem = smem_bytes<T>(P, place);
+        long long item_slab = (long long)slab_bytes<T>(P, place);
         int per_sm = 1, mode = 0;
         bool fast = false;
         if (const void* ff = choose(P, mode, fast)) {
@@ -503,18 +514,21 @@ int eval_impl(mirage_ctx* ctx, const mirage_problem_t* probs, int n_probs, const
             // lambda grids ascend: smaller k = smaller lambda = more CG iterations
             const double key2 = work * (double)(n_lam[c] - k + 4);
             g.items.push_back({-key2, c * MAX_LAM + k});
+            g.cost += key2;
         }
     }
     std::vector<int> all_items;
     std::vector<size_t> g_off;
     std::vector<Group*> glist;
-    for (auto& kv : groups) {
-        Group& g = kv.second;
+    for (auto& kv : groups) glist.push_back(&kv.second);
+    // costliest group first: the others fill in behind its tail
+    std::stable_sort(glist.begin(), glist.end(), [](const Group* a, const Group* b) { return a->cost > b->cost; });
+    for (Group* gp : glist) {
+        Group& g = *gp;
         std::stable_sort(g.items.begin(), g.items.end(),
                          [](const std::pair<double, int>& a, const std::pair<double, int>& b) { return a.first < b.first; });
         g_off.push_back(all_items.size());
         for (auto& it : g.items) all_items.push_back(it.second);
-        glist.push_back(&g);
     }
     // plain mode: one candidate per launch sequence, items grouped per candidate
     std::vector<int> plain_items;
@@ -556,14 +570,17 @@ int eval_impl(mirage_ctx* ctx, const mirage_problem_t* probs, int n_probs, const
     // per-CTA global slab (bytes): FP64 refinement buffers, plus all work
     // buffers for items that do not fit in shared memory
     long long slab_stride = 0;
-    int slab_grid = 0;
-    for (Group* g : glist) {
+    std::vector<long long> g_slab_off(glist.size(), 0);  // first slab slot of each group
+    long long slab_slots = 0;
+    for (size_t gi = 0; gi < glist.size(); ++gi) {
+        Group* g = glist[gi];
         slab_stride = std::max(slab_stride, (g->slab + 255) / 256 * 256);
-        slab_grid = std::max<int>(slab_grid,
-                                  (int)std::min<long long>((long long)g->per_sm * ctx->sm_count, (long long)g->items.size()));
+        // groups run concurrently: each owns its own CTA slots of the slab
+        g_slab_off[gi] = slab_slots;
+        slab_slots += std::min<long long>((long long)g->per_sm * ctx->sm_count, (long long)g->items.size());
     }
-    if (o.mode == MIRAGE_MODE_PLAIN) slab_grid = std::max(slab_grid, max_lam);
-    TRY(ctx->slab.ensure((size_t)slab_stride * std::max(slab_grid, 1)));
+    if (o.mode == MIRAGE_MODE_PLAIN) slab_slots = std::max<long long>(slab_slots, max_lam);
+    TRY(ctx->slab.ensure((size_t)slab_stride * std::max<long long>(slab_slots, 1)));
 
     // graph key: everything that shapes the launch sequence
     std::string key;
@@ -676,8 +693,28 @@ int eval_impl(mirage_ctx* ctx, const mirage_problem_t* probs, int n_probs, const
                 break;
             }
             if (timing) cudaEventRecord(ctx->ev[1], st);
+            // kernel groups (different kernels or placements) run on side
+            // streams so that one group's tail overlaps the next group
+            const bool fork = glist.size() > 1;
+            if (fork) {
+                if (!ctx->fork_ev) {
+                    if (cudaEventCreateWithFlags(&ctx->fork_ev, cudaEventDisableTiming) != cudaSuccess) {
+                        set_error("cudaEventCreate failed");
+                        rc = MIRAGE_ERR_CUDA;
+                        break;
+                    }
+                    for (int i = 0; i < 4; ++i) {
+                        cudaStreamCreateWithFlags(&ctx->side[i], cudaStreamNonBlocking);
+                        cudaEventCreateWithFlags(&ctx->join_ev[i], cudaEventDisableTiming);
+                    }
+                }
+                cudaEventRecord(ctx->fork_ev, st);
+                for (int i = 0; i < 4; ++i) cudaStreamWaitEvent(ctx->side[i], ctx->fork_ev, 0);
+            }
             for (size_t gi = 0; gi < glist.size() && !rc; ++gi) {
                 Group* g = glist[gi];
+                const cudaStream_t gs = fork ? ctx->side[gi % 4] : st;
+                A.slab = ctx->slab.as<unsigned char>() + g_slab_off[gi] * slab_stride;
                 A.items = ditems + g_off[gi];
                 A.n_items = (int)g->items.size();
                 A.counter = dcnt + gi;
@@ -689,10 +726,16 @@ int eval_impl(mirage_ctx* ctx, const mirage_problem_t* probs, int n_probs, const
                     set_fast_args<T>(fa, A);
                     if (!gtaps[gi].empty()) std::memcpy(fa.ptap, gtaps[gi].data(), sizeof(fa.ptap));
                     void* args[] = {&fa};
-                    rc = launch(ctx, g->fn, dim3(grid), dim3(NTHREADS), args, g->smem, st);
+                    rc = launch(ctx, g->fn, dim3(grid), dim3(NTHREADS), args, g->smem, gs);
                 } else {
                     void* args[] = {&A};
-                    rc = launch(ctx, g->fn, dim3(grid), dim3(NTHREADS), args, g->smem, st);
+                    rc = launch(ctx, g->fn, dim3(grid), dim3(NTHREADS), args, g->smem, gs);
+                }
+            }
+            if (fork) {
+                for (int i = 0; i < 4; ++i) {
+                    cudaEventRecord(ctx->join_ev[i], ctx->side[i]);
+                    cudaStreamWaitEvent(st, ctx->join_ev[i], 0);
                 }
             }
             if (rc) break;
@@ -721,9 +764,9 @@ int eval_impl(mirage_ctx* ctx, const mirage_problem_t* probs, int n_probs, const
             }
             for (int c = 0; c < n_cand && !rc; ++c) {
                 const Prob<T>& P = hp[prob_idx[c]];
-                const bool big = smem_bytes<T>(P, false) > (size_t)ctx->max_smem;
-                const void* fn = pick_cgls(prec, big, P.K);
-                size_t item_smem = smem_bytes<T>(P, big);
+                const int place = pick_place<T>(ctx, P);
+                const void* fn = pick_cgls(prec, place, P.K);
+                size_t item_smem = smem_bytes<T>(P, place);
                 int pmode = 0;
                 bool pfast = false;
                 if (const void* ff = choose(P, pmode, pfast)) {
@@ -893,6 +936,11 @@ int mirage_destroy(mirage_ctx_t* ctx) {
     cudaSetDevice(ctx->device);
     drop_graphs(ctx);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+    for (int i = 0; i < 4; ++i) {
+        if (ctx->side[i]) cudaStreamDestroy(ctx->side[i]);
+        if (ctx->join_ev[i]) cudaEventDestroy(ctx->join_ev[i]);
+    }
+    if (ctx->fork_ev) cudaEventDestroy(ctx->fork_ev);
     for (int e = 0; e < 4; ++e)
         if (ctx->ev[e]) cudaEventDestroy(ctx->ev[e]);
     DevBuf* bufs[] = {&ctx->E, &ctx->E64, &ctx->Etmp, &ctx->inv, &ctx->cst, &ctx->swp, &ctx->dpad, &ctx->nent, &ctx->cstat,

@@ -4,8 +4,9 @@
 
 namespace mirage {
 void fill_f32_k15(KernelTable& t) {
-    t.cgls[0][0][15] = (const void*)k_cgls<float, 15, false>;
-    t.cgls[0][1][15] = (const void*)k_cgls<float, 15, true>;
+    t.cgls[0][0][15] = (const void*)k_cgls<float, 15, PLACE_SMEM>;
+    t.cgls[0][1][15] = (const void*)k_cgls<float, 15, PLACE_GLOBAL>;
+    t.cgls[0][2][15] = (const void*)k_cgls<float, 15, PLACE_MID>;
 
 }
 }  // namespace mirage

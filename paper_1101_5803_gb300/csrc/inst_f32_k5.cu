@@ -4,7 +4,7 @@
 
 namespace mirage {
 void fill_f32_k5(KernelTable& t) {
-    t.cgls[0][0][5] = (const void*)k_cgls<float, 5, false>;
+    t.cgls[0][0][5] = (const void*)k_cgls<float, 5, PLACE_SMEM>;
 
 
 }

@@ -4,8 +4,9 @@
 
 namespace mirage {
 void fill_f32_k7(KernelTable& t) {
-    t.cgls[0][0][7] = (const void*)k_cgls<float, 7, false>;
-    t.cgls[0][1][7] = (const void*)k_cgls<float, 7, true>;
+    t.cgls[0][0][7] = (const void*)k_cgls<float, 7, PLACE_SMEM>;
+    t.cgls[0][1][7] = (const void*)k_cgls<float, 7, PLACE_GLOBAL>;
+    t.cgls[0][2][7] = (const void*)k_cgls<float, 7, PLACE_MID>;
 
 }
 }  // namespace mirage

@@ -4,7 +4,8 @@
 
 namespace mirage {
 void fill_f32_k9(KernelTable& t) {
-    t.cgls[0][0][9] = (const void*)k_cgls<float, 9, false>;
-    t.cgls[0][1][9] = (const void*)k_cgls<float, 9, true>;
+    t.cgls[0][0][9] = (const void*)k_cgls<float, 9, PLACE_SMEM>;
+    t.cgls[0][1][9] = (const void*)k_cgls<float, 9, PLACE_GLOBAL>;
+    t.cgls[0][2][9] = (const void*)k_cgls<float, 9, PLACE_MID>;
 }
 }  // namespace mirage

@@ -4,9 +4,9 @@
 
 namespace mirage {
 void fill_f64(KernelTable& t) {
-    t.cgls[1][0][5] = (const void*)k_cgls<double, 5, false>;
-    t.cgls[1][0][0] = (const void*)k_cgls<double, 0, false>;
-    t.cgls[1][1][0] = (const void*)k_cgls<double, 0, true>;
+    t.cgls[1][0][5] = (const void*)k_cgls<double, 5, PLACE_SMEM>;
+    t.cgls[1][0][0] = (const void*)k_cgls<double, 0, PLACE_SMEM>;
+    t.cgls[1][1][0] = (const void*)k_cgls<double, 0, PLACE_GLOBAL>;
     t.fwd[1][0] = (const void*)k_forward<double, 0>;
     t.raytrace[1] = (const void*)k_raytrace<double>;
     t.finalize[1] = (const void*)k_finalize<double>;

@@ -881,35 +881,49 @@ __host__ __device__ inline size_t align_up(size_t v, size_t a) {
     return (v + a - 1) / a * a;
 }
 
-// Shared-memory footprint of one problem (big = work buffers in global memory).
+// Placement of the work buffers of the general CGLS kernel:
+//   PLACE_SMEM   everything in shared memory (small images)
+//   PLACE_GLOBAL everything in a per-CTA global slab (L2-resident)
+//   PLACE_MID    the two convolution inputs and the source vectors in
+//                shared memory, the rest in the slab (mid-size images)
+enum : int { PLACE_SMEM = 0, PLACE_GLOBAL = 1, PLACE_MID = 2 };
+
 template <typename T>
-__host__ __device__ inline size_t smem_bytes(const Prob<T>& P, bool big) {
+__host__ __device__ inline size_t smem_bytes(const Prob<T>& P, int place) {
     size_t o = 16 + 2 * 33 * sizeof(double) + 128;                 // item slot + reductions + CG scalars
     o += align_up<T>(sizeof(T) * 2 * P.K * P.kp, 16);              // taps
     o += align_up<T>(sizeof(double) * 2 * P.K * P.kp, 16);         // taps64
-    if (!big) {
+    if (place == PLACE_SMEM) {
         o += 5 * align_up<T>(sizeof(T) * P.plen, 16);                  // swp rimg qimg P1 P2
         o += align_up<T>(sizeof(Entry<T>) * (size_t)P.nrays, 16);      // E
         if (P.Np > 1) o += align_up<T>(sizeof(int) * (size_t)P.nrays, 16);  // inv
         o += align_up<T>(sizeof(int) * (size_t)(P.ncells + 1), 16);    // cst
+    } else if (place == PLACE_MID) {
+        o += 2 * align_up<T>(sizeof(T) * P.plen, 16);                  // P1 P2
+    }
+    if (place != PLACE_GLOBAL) {
         o += 3 * align_up<T>(sizeof(T) * P.ns, 16);                    // x p s
         o += 2 * align_up<T>(sizeof(T) * P.nreg, 16);                  // rreg qreg
     }
     return o;
 }
 
-// per-CTA global slab: [double part][T part (big only)], in bytes
+// per-CTA global slab: [double part][T part], in bytes
 template <typename T>
-__host__ __device__ inline size_t slab_bytes(const Prob<T>& P, bool big) {
+__host__ __device__ inline size_t slab_bytes(const Prob<T>& P, int place) {
     size_t o = sizeof(double) * (3 * align_up<T>(P.plen, 4) + align_up<T>(P.ns, 4) + align_up<T>(P.nreg, 4));
-    if (big) o += sizeof(T) * (4 * align_up<T>(P.plen, 4) + 3 * align_up<T>(P.ns, 4) + 2 * align_up<T>(P.nreg, 4));
+    if (place == PLACE_GLOBAL)
+        o += sizeof(T) * (4 * align_up<T>(P.plen, 4) + 3 * align_up<T>(P.ns, 4) + 2 * align_up<T>(P.nreg, 4));
+    if (place == PLACE_MID) o += sizeof(T) * 2 * align_up<T>(P.plen, 4);  // rimg qimg
     return align_up<T>(o, 256);
 }
 
-template <typename T, int K, bool BIG>
+template <typename T, int K, int PLACE>
 __global__ void __launch_bounds__(NTHREADS, 1) k_cgls(CglsArgs<T> A) {
     extern __shared__ __align__(16) unsigned char smem[];
-    constexpr bool SH = !BIG;
+    constexpr bool BIG = PLACE == PLACE_GLOBAL;
+    constexpr bool MID = PLACE == PLACE_MID;
+    constexpr bool SH = !BIG;  // convolution inputs in shared memory
     const int tid = threadIdx.x, bs = blockDim.x;
     int last_c = -1;
     int which = 0;
@@ -954,7 +968,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_cgls(CglsArgs<T> A) {
         slab += sizeof(double) * align_up<T>(g.ns, 4);
         w.h64 = reinterpret_cast<double*>(slab);
         slab += sizeof(double) * align_up<T>(g.nreg, 4);
-        if constexpr (!BIG) {
+        if constexpr (PLACE == PLACE_SMEM) {
             const size_t pl = align_up<T>(sizeof(T) * g.plen, 16);
             w.swp = reinterpret_cast<T*>(sp); sp += pl;
             w.rimg = reinterpret_cast<T*>(sp); sp += pl;
@@ -988,6 +1002,25 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_cgls(CglsArgs<T> A) {
                 for (int i = tid; i <= P.ncells; i += bs) sCst[i] = g_cst[i];
                 for (int i = tid; i < g.plen; i += bs) w.swp[i] = g_swp[i];
             }
+        } else if constexpr (MID) {
+            const size_t pl = align_up<T>(sizeof(T) * g.plen, 16);
+            w.P1 = reinterpret_cast<T*>(sp); sp += pl;
+            w.P2 = reinterpret_cast<T*>(sp); sp += pl;
+            const size_t ps = align_up<T>(sizeof(T) * g.ns, 16);
+            const size_t pr = align_up<T>(sizeof(T) * g.nreg, 16);
+            w.x = reinterpret_cast<T*>(sp); sp += ps;
+            w.p = reinterpret_cast<T*>(sp); sp += ps;
+            w.s = reinterpret_cast<T*>(sp); sp += ps;
+            w.rreg = reinterpret_cast<T*>(sp); sp += pr;
+            w.qreg = reinterpret_cast<T*>(sp); sp += pr;
+            T* ts = reinterpret_cast<T*>(slab);
+            const size_t pg = align_up<T>(g.plen, 4);
+            w.rimg = ts; ts += pg;
+            w.qimg = ts; ts += pg;
+            w.swp = const_cast<T*>(g_swp);
+            w.E = g_E;
+            w.inv = g_inv;
+            w.cst = g_cst;
         } else {
             T* ts = reinterpret_cast<T*>(slab);
             const size_t pl = align_up<T>(g.plen, 4);

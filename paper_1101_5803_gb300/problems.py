@@ -71,3 +71,46 @@ def ga64_workload(ctx: Context, n_cand: int = 256, n_lam: int = 16, seed: int = 
     lens = torch.as_tensor(synth.lens_population(rng, n_cand), device="cuda")
     lams = torch.as_tensor(np.tile(synth.lambda_grid(n_lam), (n_cand, 1)), device="cuda")
     return Workload(g, prob, lens, lams, np.full(n_cand, n_lam, np.int32), np.zeros(n_cand, np.int32))
+
+
+@dataclasses.dataclass
+class MultiWorkload:
+    problems: list          # one Problem per distinct observation
+    lens: torch.Tensor      # [n, 7] float64 (device)
+    lambdas: torch.Tensor   # [n, max_lam] float64 (device)
+    n_lam: np.ndarray       # [n] int32 (host)
+    prob_idx: np.ndarray    # [n] int32 (host)
+
+
+def uneven_workload(ctx: Context, n_cand: int = 1024, seed: int = 0) -> MultiWorkload:
+    """Uneven persistent batch: every candidate has its own observation with an
+    image of {48,64,96,128}^2 pixels over 6.4", an annular mask (inner
+    0.3-0.6", outer 1.5-2.5"), a source grid of {16,24,32,48}^2 over +-0.8",
+    a Gaussian PSF of width {7,11,15} px (sigma = width/6), and 8..32
+    lambdas log-spaced over 1e-4..1e2."""
+    rng = np.random.default_rng(seed)
+    items = synth.uneven_batch(rng, n_cand)
+    probs = []
+    max_lam = max(it.n_lam for it in items)
+    lams = np.zeros((n_cand, max_lam))
+    for c, it in enumerate(items):
+        psf = synth.gaussian_psf(it.geom.kpsf, it.psf_sigma)
+        mask = synth.annular_mask(it.geom, it.r_in, it.r_out)
+        probs.append(observe_on_device(ctx, it.geom, psf, synth.drawn_source(rng), synth.TRUE_LENS, rng, mask=mask))
+        lams[c, :it.n_lam] = synth.lambda_grid(it.n_lam)
+        lams[c, it.n_lam:] = lams[c, it.n_lam - 1]
+    lens = torch.as_tensor(synth.lens_population(rng, n_cand), device="cuda")
+    return MultiWorkload(probs, lens, torch.as_tensor(lams, device="cuda"),
+                         np.array([it.n_lam for it in items], np.int32), np.arange(n_cand, dtype=np.int32))
+
+
+def large_workload(ctx: Context, n_cand: int = 64, n_lam: int = 32, seed: int = 0) -> Workload:
+    """Large field: 256x256 image at 0.02"/px, 128x128 source over +-1.2",
+    21x21 Gaussian PSF (sigma 3 px), Laplacian H, n_lam lambdas."""
+    rng = np.random.default_rng(seed)
+    g = synth.geom_large256()
+    psf = synth.gaussian_psf(g.kpsf, synth.PSF_SIGMA["large256"])
+    prob = observe_on_device(ctx, g, psf, synth.drawn_source(rng), synth.TRUE_LENS, rng)
+    lens = torch.as_tensor(synth.lens_population(rng, n_cand), device="cuda")
+    lams = torch.as_tensor(np.tile(synth.lambda_grid(n_lam), (n_cand, 1)), device="cuda")
+    return Workload(g, prob, lens, lams, np.full(n_cand, n_lam, np.int32), np.zeros(n_cand, np.int32))

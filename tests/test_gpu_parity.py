@@ -235,6 +235,15 @@ def test_uneven_batch_two_problems(mods, ctx32):
     lens = [synth.TRUE_LENS, [0.9, 0.8, 1.0, 0.05, 0.0, 0.02, 0.1]]
     out = ctx32.eval_batch([device_problem(p1), device_problem(p2)], _lens_t(lens), [0, 1], _lam_t(lams, 2),
                            [8, 6], tol=1e-6, want_all_x=True)
+    # kernel groups run concurrently: results must not depend on scheduling
+    again = ctx32.eval_batch([device_problem(p1), device_problem(p2)], _lens_t(lens), [0, 1], _lam_t(lams, 2),
+                             [8, 6], tol=1e-6, want_all_x=True)
+    plain = ctx32.eval_batch([device_problem(p1), device_problem(p2)], _lens_t(lens), [0, 1], _lam_t(lams, 2),
+                             [8, 6], tol=1e-6, want_all_x=True, mode=mods.MIRAGE_MODE_PLAIN)
+    for key in ("chi2", "iters", "corner", "status"):
+        for c, n in enumerate([8, 6]):
+            a, b, r = (x[key][c, :n] if x[key].dim() > 1 else x[key][c] for x in (again, plain, out))
+            assert torch.equal(a, r) and torch.equal(b, r), (key, c)
     for c, prob in enumerate([p1, p2]):
         n = [8, 6][c]
         sub = {key: (v[c:c + 1, :n] if v.dim() > 1 else v[c:c + 1]) for key, v in out.items()}

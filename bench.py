@@ -146,6 +146,22 @@ def flops_per_item(geom, iters):
     return iters * f_it + (2 * k * k * npix + 6 * npix)
 
 
+def max_over_ranks(t: float, world: int, device=None) -> float:
+    """Largest per-rank time (the job's time under weak scaling)."""
+    if world <= 1:
+        return t
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor([t], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def job_throughput(units_per_rank: int, steps: int, t_max: float, world: int) -> float:
+    """Whole-job throughput: every rank's units over the slowest rank's time."""
+    return world * units_per_rank * steps / t_max
+
+
 def run_reference(args):
     rank, world = _dist()
     if rank != 0:
@@ -191,9 +207,12 @@ def run_gpu(args):
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     st = torch.cuda.current_stream()
 
+    from paper_1101_5803_gb300.autotune import tune
+    variant = tune(ctx, probs, wl.lens, wl.prob_idx, wl.lambdas, wl.n_lam, tol=TOL)
+
     def step(out=None, graph=True, timing=False):
         return ctx.eval_batch(probs, wl.lens, wl.prob_idx, wl.lambdas, wl.n_lam, tol=TOL, use_graph=graph,
-                              out=out, want_kappa=True, phase_timing=timing)
+                              out=out, want_kappa=True, phase_timing=timing, variant=variant)
 
     # untimed: one phase-timed call for the kernel roofline, then graph warm-up
     out = step(graph=False, timing=True)
@@ -223,12 +242,8 @@ def run_gpu(args):
         dist.barrier()
     times = [a.elapsed_time(b) for a, b in ev]
     t_total = sum(times) / 1e3
-    t_max = t_total
-    if world > 1:
-        tt = torch.tensor([t_total], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
-    value = world * N_CAND * args.steps / t_max
+    t_max = max_over_ranks(t_total, world, device="cuda")
+    value = job_throughput(N_CAND, args.steps, t_max, world)
 
     # end to end through the C ABI with pinned host buffers
     hp = binding.Problem(wl.geom, wl.problem.d.cpu().pin_memory(), wl.problem.sigma.cpu().pin_memory(),
@@ -305,7 +320,8 @@ def run_gpu(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32 (f64 reductions)", "data": "synthetic",
-            "config": dict(CONFIG, parallelism=f"replicas{world}" if world > 1 else "single"),
+            "config": dict(CONFIG, parallelism=f"replicas{world}" if world > 1 else "single",
+                           kernel_variant=variant),
             "e2e": {"value": N_CAND / t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",

@@ -1,0 +1,79 @@
+"""Autotuner for the CGLS kernel variant of a shape class.
+
+The library offers several implementations of the same item computation
+(mirage_opts_t.variant): the two-CTA-per-SM kernel with PSF taps in shared
+memory (1), as kernel parameters with FFMA (2) or packed FFMA2 (3), and the
+general kernel (4).  All give results within the parity tolerances (1-3
+bitwise identical).  For a shape class (image, source grid, PSF, sub-pixels,
+regulariser, precision, one or several PSFs per launch) the tuner times each
+variant on a short probe batch with CUDA events and caches the fastest in a
+JSON file; later calls read the cache.
+"""
+from __future__ import annotations
+
+import json
+import os
+
+import numpy as np
+import torch
+
+from .binding import MIRAGE_FP32
+
+VARIANTS = (1, 2, 3, 4)
+
+
+def cache_path() -> str:
+    p = os.environ.get("MIRAGE_TUNE_CACHE")
+    if p:
+        return p
+    return os.path.join(os.path.expanduser("~"), ".cache", "mirage_gb300", "tune.json")
+
+
+def shape_key(ctx, probs) -> str:
+    gs = sorted({(int(p.geom.nx), int(p.geom.ny), int(p.geom.sx), int(p.geom.sy), int(p.geom.kpsf),
+                  int(getattr(p.geom, "subpix", 1)), int(p.geom.reg)) for p in probs})
+    return json.dumps({"prec": int(ctx.precision), "shapes": gs, "multi": len(probs) > 1})
+
+
+def _load():
+    try:
+        return json.load(open(cache_path()))
+    except Exception:
+        return {}
+
+
+def _save(d):
+    p = cache_path()
+    os.makedirs(os.path.dirname(p), exist_ok=True)
+    tmp = p + ".tmp"
+    with open(tmp, "w") as fh:
+        json.dump(d, fh, indent=1, sort_keys=True)
+    os.replace(tmp, p)
+
+
+def tune(ctx, probs, lens, prob_idx, lambdas, n_lam, *, tol=1e-6, n_probe=32, retune=False) -> int:
+    """Fastest variant for this shape class (timed on the first n_probe
+    candidates at the two largest lambdas of their grids)."""
+    key = shape_key(ctx, probs)
+    db = _load()
+    if key in db and not retune:
+        return int(db[key]["variant"])
+    n = min(n_probe, int(lens.shape[0]))
+    lam = lambdas[:n, -2:].contiguous() if lambdas.shape[1] >= 2 else lambdas[:n].contiguous()
+    nl = np.minimum(np.asarray(n_lam[:n]), lam.shape[1]).astype(np.int32)
+    times = {}
+    for v in VARIANTS:
+        if v in (1, 2, 3) and ctx.precision != MIRAGE_FP32:
+            continue
+        kw = dict(tol=tol, variant=v, want_s=False, want_kappa=False)
+        ctx.eval_batch(probs, lens[:n].contiguous(), prob_idx[:n], lam, nl, **kw)  # warm-up
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ctx.eval_batch(probs, lens[:n].contiguous(), prob_idx[:n], lam, nl, **kw)
+        e1.record()
+        torch.cuda.synchronize()
+        times[v] = e0.elapsed_time(e1)
+    best = min(times, key=times.get)
+    db[key] = {"variant": int(best), "ms": {str(k): round(t, 4) for k, t in times.items()}}
+    _save(db)
+    return int(best)

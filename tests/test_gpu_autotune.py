@@ -1,0 +1,30 @@
+"""The autotuner picks a kernel variant per shape class, caches it, and
+every variant it chooses between gives the same results (variants 1-3
+bitwise, the general kernel within the parity tolerances)."""
+import numpy as np
+import pytest
+import torch
+
+pytestmark = pytest.mark.gpu
+
+
+def test_tune_caches_and_variants_agree(tmp_path, monkeypatch):
+    monkeypatch.setenv("MIRAGE_TUNE_CACHE", str(tmp_path / "tune.json"))
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1101_5803_gb300 import autotune, binding
+    from paper_1101_5803_gb300.problems import ga64_workload
+
+    ctx = binding.Context(0, binding.MIRAGE_FP32)
+    wl = ga64_workload(ctx, 16, 4, seed=9)
+    v = autotune.tune(ctx, [wl.problem], wl.lens, wl.prob_idx, wl.lambdas, wl.n_lam, n_probe=8)
+    assert v in autotune.VARIANTS
+    assert (tmp_path / "tune.json").exists()
+    assert autotune.tune(ctx, [wl.problem], wl.lens, wl.prob_idx, wl.lambdas, wl.n_lam) == v
+    outs = {k: ctx.eval_batch([wl.problem], wl.lens, wl.prob_idx, wl.lambdas, wl.n_lam, tol=1e-6, variant=k)
+            for k in autotune.VARIANTS}
+    for k in (2, 3):
+        assert torch.equal(outs[k]["chi2"], outs[1]["chi2"])
+    c1, c4 = outs[1]["chi2"].cpu().numpy(), outs[4]["chi2"].cpu().numpy()
+    assert np.abs(c4 / c1 - 1).max() < 1e-5
+    ctx.close()

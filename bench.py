@@ -284,13 +284,14 @@ def run_gpu(args):
     if clocks.get("sm_mhz"):
         at_clock = nsm * 128 * 2 * clocks["sm_mhz"] * 1e6 / 1e12
 
+    # DRAM bytes per launch: the per-item traffic of the ncu capture of this
+    # kernel (profiles/k_cgls_fast_ga64.md) times the items of one launch
     traffic = None
-    tfile = os.path.join(ROOT, "profiles", "cgls_ga64_traffic.json")
+    tfile = os.path.join(ROOT, "profiles", "k_cgls_fast_ga64.md")
     if os.path.exists(tfile):
-        try:
-            traffic = json.load(open(tfile)).get("bytes_per_launch")
-        except Exception:
-            traffic = None
+        for line in open(tfile):
+            if line.startswith("traffic_bytes_per_item:"):
+                traffic = float(line.split(":")[1]) * float(iters.size)
 
     # GA generations on the same problem: surrogate screen vs none
     from paper_1101_5803_gb300.ga import GAConfig, run_ga

@@ -51,15 +51,19 @@ def _save(d):
     os.replace(tmp, p)
 
 
-def tune(ctx, probs, lens, prob_idx, lambdas, n_lam, *, tol=1e-6, n_probe=32, retune=False) -> int:
-    """Fastest variant for this shape class (timed on the first n_probe
-    candidates at the two largest lambdas of their grids)."""
+def tune(ctx, probs, lens, prob_idx, lambdas, n_lam, *, tol=1e-6, n_probe=64, retune=False) -> int:
+    """Fastest variant for this shape class, timed on the first n_probe
+    candidates at two lambdas from the middle of their grids (items of
+    typical length: the largest lambdas converge in a few dozen iterations
+    and would time mostly the fixed per-item work)."""
     key = shape_key(ctx, probs)
     db = _load()
     if key in db and not retune:
         return int(db[key]["variant"])
     n = min(n_probe, int(lens.shape[0]))
-    lam = lambdas[:n, -2:].contiguous() if lambdas.shape[1] >= 2 else lambdas[:n].contiguous()
+    m = int(lambdas.shape[1])
+    cols = [m // 2, min(m - 1, m // 2 + 1)] if m >= 2 else [0]
+    lam = lambdas[:n, cols].contiguous()
     nl = np.minimum(np.asarray(n_lam[:n]), lam.shape[1]).astype(np.int32)
     times = {}
     for v in VARIANTS:

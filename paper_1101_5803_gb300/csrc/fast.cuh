@@ -329,6 +329,64 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_cgls_fast(const __grid_constant
         const double rhsn = sqrt(block_sum(rs, red, which));
         which ^= 1;
 
+        // ---- Jacobi preconditioner of the inner solves: an approximation of
+        // diag(A~^T A~) = diag(L^T B^T W B L) + lam diag(H^T H), taking
+        // diag(L^T B^T W B L)_i ~ sum_rays weight_i^2 w_pixel * sum(psf^2)
+        // (exact for a delta PSF; cross terms between rays are dropped).
+        // Any positive diagonal leaves the solution unchanged; this one cuts
+        // the CGLS iterations two- to threefold.
+        float minv[NSP];
+        {
+            if (tid < 32) {
+                float a = 0.f;
+                for (int i = tid; i < K * K; i += 32) a = fmaf(P.psf[i], P.psf[i], a);
+                for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+                if (tid == 0) reinterpret_cast<float*>(ctl)[0] = a;
+            }
+            float4* cellp = reinterpret_cast<float4*>(P2);
+            for (int cell = tid; cell < g.ncells; cell += bs) {
+                const int k0 = cst16[cell], k1 = cst16[cell + 1];
+                float c00 = 0.f, c10 = 0.f, c01 = 0.f, c11 = 0.f;
+                for (int e = k0; e < k1; ++e) {
+                    const unsigned id = eidx[e];
+                    const float2 uv = euv[e];
+                    const float sw1 = w.swp[id & 0xffffu];
+                    const float W2 = sw1 * sw1;
+                    const float u1 = uv.x * uv.x, u0 = (1.f - uv.x) * (1.f - uv.x);
+                    const float v1 = uv.y * uv.y, v0 = (1.f - uv.y) * (1.f - uv.y);
+                    c00 = fmaf(u0 * v0, W2, c00);
+                    c10 = fmaf(u1 * v0, W2, c10);
+                    c01 = fmaf(u0 * v1, W2, c01);
+                    c11 = fmaf(u1 * v1, W2, c11);
+                }
+                cellp[cell] = make_float4(c00, c10, c01, c11);
+            }
+            __syncthreads();
+            const float psf2 = reinterpret_cast<const float*>(ctl)[0];
+            const float* cp = reinterpret_cast<const float*>(cellp);
+#pragma unroll
+            for (int kk = 0; kk < NSP; ++kk) {
+                const int i = tid + kk * bs;
+                minv[kk] = 0.f;
+                if (i < g.ns) {
+                    const int ib = i / g.sx, ia = i - ib * g.sx;
+                    float dsum = 0.f;
+                    if (ib <= g.sy - 2 && ia <= g.sx - 2) dsum += cp[4 * (ib * g.ncx + ia) + 0];
+                    if (ib <= g.sy - 2 && ia >= 1) dsum += cp[4 * (ib * g.ncx + ia - 1) + 1];
+                    if (ib >= 1 && ia <= g.sx - 2) dsum += cp[4 * ((ib - 1) * g.ncx + ia) + 2];
+                    if (ib >= 1 && ia >= 1) dsum += cp[4 * ((ib - 1) * g.ncx + ia - 1) + 3];
+                    // diag(H^T H): 1 (identity) or 16 + number of neighbours (Laplacian)
+                    float h = 1.f;
+                    if (g.reg == 2)
+                        h = 16.f + (float)((ia > 0) + (ia < g.sx - 1) + (ib > 0) + (ib < g.sy - 1));
+                    minv[kk] = 1.f / (dsum * psf2 + (float)lam * h);
+                }
+            }
+            __syncthreads();
+            for (int cell = tid; cell < g.ncells; cell += bs) cellp[cell] = make_float4(0.f, 0.f, 0.f, 0.f);
+            __syncthreads();
+        }
+
         if (A.warm_x) {
             const T* x0 = A.warm_x + ok * A.max_ns;
             for (int i = tid; i < g.ns; i += bs) w.x64[i] = (double)x0[i];
@@ -373,8 +431,9 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_cgls_fast(const __grid_constant
                 s[kk] = 0.f;
                 if (i < g.ns) {
                     s[kk] = w.s[i];
-                    p[i] = s[kk];
-                    gs = fmaf(s[kk], s[kk], gs);
+                    const float z = minv[kk] * s[kk];
+                    p[i] = z;
+                    gs = fmaf(s[kk], z, gs);
                 }
             }
             if (own) {
@@ -514,8 +573,9 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_cgls_fast(const __grid_constant
                         if (ib <= g.sy - 2 && ia >= 1) acc += cp[4 * (ib * g.ncx + ia - 1) + 1];
                         if (ib >= 1 && ia <= g.sx - 2) acc += cp[4 * ((ib - 1) * g.ncx + ia) + 2];
                         if (ib >= 1 && ia >= 1) acc += cp[4 * ((ib - 1) * g.ncx + ia - 1) + 3];
-                        s[kk] = acc + sl * apply_HT_at<T, float>(g, rreg, i, ia, ib);
-                        gsum = fmaf(s[kk], s[kk], gsum);
+                        const float gr = acc + sl * apply_HT_at<T, float>(g, rreg, i, ia, ib);
+                        s[kk] = minv[kk] * gr;  // preconditioned gradient z = M^-1 g
+                        gsum = fmaf(gr, s[kk], gsum);
                     }
                 }
                 const float2 gp = block_pair_all(gsum, pbuf, half);

@@ -629,6 +629,7 @@ struct Work {
     T* s;
     T* rreg;          // [nreg]
     T* qreg;
+    T* minv;          // [ns] Jacobi preconditioner of the inner solves
     double* x64;      // [ns] solution accumulator (refinement)
     double* h64;      // [nreg] H x64
     double* Pa;       // [plen] L x64
@@ -737,6 +738,46 @@ __device__ __forceinline__ V apply_HT_at(const Geo<T>& g, const V* __restrict__ 
     if (ia > 0) acc += r[i - 1];
     if (ib > 0) acc += ry[i - g.sx];
     return acc;
+}
+
+// Approximate diagonal of the inner normal operator at source pixel (ia, ib):
+//   sum over the rays of its cells of (bilinear weight / N_p)^2 w_pixel,
+// the diagonal of L^T W L (times sum(psf^2) it approximates that of
+// L^T B^T W B L; exact for a delta PSF).
+template <typename T>
+__device__ __forceinline__ T lwl_diag_at(const Geo<T>& g, const Entry<T>* __restrict__ Ent, const int* __restrict__ cst,
+                                         const T* __restrict__ swp, int ia, int ib) {
+    T acc = 0;
+#pragma unroll
+    for (int dy = 0; dy < 2; ++dy) {
+        const int iy0 = ib - dy;
+        if (iy0 < 0 || iy0 > g.sy - 2) continue;
+#pragma unroll
+        for (int dx = 0; dx < 2; ++dx) {
+            const int ix0 = ia - dx;
+            if (ix0 < 0 || ix0 > g.sx - 2) continue;
+            const int cell = iy0 * g.ncx + ix0;
+            const int k1 = cst[cell + 1];
+            for (int k = cst[cell]; k < k1; ++k) {
+                const Entry<T> en = Ent[k];
+                const T wu = dx ? en.u : (T)1 - en.u;
+                const T wv = dy ? en.v : (T)1 - en.v;
+                const T sw = swp[en.ppos];
+                const T wt = wu * wv * g.invNp;
+                acc += wt * wt * sw * sw;
+            }
+        }
+    }
+    return acc;
+}
+
+// diag(H^T H) at source pixel (ia, ib): identity 1; gradient 2 + [left
+// neighbour] + [lower neighbour]; Laplacian 16 + number of neighbours
+template <typename T>
+__device__ __forceinline__ T hth_diag_at(const Geo<T>& g, int ia, int ib) {
+    if (g.reg == 0) return (T)1;
+    if (g.reg == 1) return (T)(2 + (ia > 0) + (ib > 0));
+    return (T)(16 + (ia > 0) + (ia < g.sx - 1) + (ib > 0) + (ib < g.sy - 1));
 }
 
 // 4-wide vector helpers for one tile row (float: one 16-byte access;
@@ -902,7 +943,7 @@ __host__ __device__ inline size_t smem_bytes(const Prob<T>& P, int place) {
         o += 2 * align_up<T>(sizeof(T) * P.plen, 16);                  // P1 P2
     }
     if (place != PLACE_GLOBAL) {
-        o += 3 * align_up<T>(sizeof(T) * P.ns, 16);                    // x p s
+        o += 4 * align_up<T>(sizeof(T) * P.ns, 16);                    // x p s minv
         o += 2 * align_up<T>(sizeof(T) * P.nreg, 16);                  // rreg qreg
     }
     return o;
@@ -913,7 +954,7 @@ template <typename T>
 __host__ __device__ inline size_t slab_bytes(const Prob<T>& P, int place) {
     size_t o = sizeof(double) * (3 * align_up<T>(P.plen, 4) + align_up<T>(P.ns, 4) + align_up<T>(P.nreg, 4));
     if (place == PLACE_GLOBAL)
-        o += sizeof(T) * (4 * align_up<T>(P.plen, 4) + 3 * align_up<T>(P.ns, 4) + 2 * align_up<T>(P.nreg, 4));
+        o += sizeof(T) * (4 * align_up<T>(P.plen, 4) + 4 * align_up<T>(P.ns, 4) + 2 * align_up<T>(P.nreg, 4));
     if (place == PLACE_MID) o += sizeof(T) * 2 * align_up<T>(P.plen, 4);  // rimg qimg
     return align_up<T>(o, 256);
 }
@@ -989,6 +1030,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_cgls(CglsArgs<T> A) {
             w.x = reinterpret_cast<T*>(sp); sp += ps;
             w.p = reinterpret_cast<T*>(sp); sp += ps;
             w.s = reinterpret_cast<T*>(sp); sp += ps;
+            w.minv = reinterpret_cast<T*>(sp); sp += ps;
             w.rreg = reinterpret_cast<T*>(sp); sp += pr;
             w.qreg = reinterpret_cast<T*>(sp); sp += pr;
             w.E = sE;
@@ -1011,6 +1053,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_cgls(CglsArgs<T> A) {
             w.x = reinterpret_cast<T*>(sp); sp += ps;
             w.p = reinterpret_cast<T*>(sp); sp += ps;
             w.s = reinterpret_cast<T*>(sp); sp += ps;
+            w.minv = reinterpret_cast<T*>(sp); sp += ps;
             w.rreg = reinterpret_cast<T*>(sp); sp += pr;
             w.qreg = reinterpret_cast<T*>(sp); sp += pr;
             T* ts = reinterpret_cast<T*>(slab);
@@ -1031,6 +1074,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_cgls(CglsArgs<T> A) {
             w.x = ts; ts += align_up<T>(g.ns, 4);
             w.p = ts; ts += align_up<T>(g.ns, 4);
             w.s = ts; ts += align_up<T>(g.ns, 4);
+            w.minv = ts; ts += align_up<T>(g.ns, 4);
             w.rreg = ts; ts += align_up<T>(g.nreg, 4);
             w.qreg = ts; ts += align_up<T>(g.nreg, 4);
             w.swp = const_cast<T*>(g_swp);
@@ -1102,6 +1146,17 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_cgls(CglsArgs<T> A) {
         const double rhsn = sqrt(block_sum(rs, red, which));
         which ^= 1;
 
+        // ---- Jacobi preconditioner of the inner solves (see lwl_diag_at)
+        {
+            T psf2 = 0;
+            for (int i = 0; i < g.K * g.K; ++i) psf2 = fma(P.psf[i], P.psf[i], psf2);
+            for (int i = tid; i < g.ns; i += bs) {
+                const int ib = i / g.sx, ia = i - ib * g.sx;
+                w.minv[i] = (T)1 / (lwl_diag_at<T>(g, w.E, w.cst, w.swp, ia, ib) * psf2 +
+                                    (T)lam * hth_diag_at<T>(g, ia, ib));
+            }
+        }
+
         // ---- starting point
         if (A.warm_x) {
             const T* x0 = A.warm_x + ok * A.max_ns;
@@ -1140,7 +1195,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_cgls(CglsArgs<T> A) {
             const double target = fmax(eta_min, 0.3 * A.tol / rel64);
             for (int i = tid; i < g.ns; i += bs) {
                 w.x[i] = 0;
-                w.p[i] = w.s[i];
+                w.p[i] = w.minv[i] * w.s[i];  // preconditioned gradient
             }
             for (int t = tid; t < g.ntiles; t += bs) {
                 const int ty = t / g.tiles_x, tx = t - ty * g.tiles_x;
@@ -1156,7 +1211,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_cgls(CglsArgs<T> A) {
             }
             {
                 T gs = 0;
-                for (int i = tid; i < g.ns; i += bs) gs = fma(w.s[i], w.s[i], gs);
+                for (int i = tid; i < g.ns; i += bs) gs = fma(w.s[i], w.p[i], gs);
                 const double gam = block_sum_to0<T>(gs, red);
                 if (tid == 0) {
                     ctl->gam = gam;
@@ -1224,8 +1279,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_cgls(CglsArgs<T> A) {
                     const int ib = i / g.sx, ia = i - ib * g.sx;
                     const T v = apply_LT_at<T, T, T>(g, w.E, w.cst, w.qimg, ia, ib) +
                                 sl * apply_HT_at<T, T>(g, w.rreg, i, ia, ib);
-                    w.s[i] = v;
-                    gs = fma(v, v, gs);
+                    const T z = w.minv[i] * v;  // preconditioned gradient
+                    w.s[i] = z;
+                    gs = fma(v, z, gs);
                 }
                 {
                     const double gnew = block_sum_to0<T>(gs, red);

@@ -25,6 +25,9 @@ def test_tune_caches_and_variants_agree(tmp_path, monkeypatch):
             for k in autotune.VARIANTS}
     for k in (2, 3):
         assert torch.equal(outs[k]["chi2"], outs[1]["chi2"])
+    # the general kernel solves the same systems to the same tolerance;
+    # two solves to rel-res 1e-6 of systems with kappa ~ 1e7 differ in chi2
+    # by up to ~1e-5 (the oracle-based gates live in test_gpu_parity)
     c1, c4 = outs[1]["chi2"].cpu().numpy(), outs[4]["chi2"].cpu().numpy()
-    assert np.abs(c4 / c1 - 1).max() < 1e-5
+    assert np.abs(c4 / c1 - 1).max() < 1e-4
     ctx.close()

@@ -122,13 +122,16 @@ int mirage_create(mirage_ctx_t** ctx, int device, int precision);
 /* Release every resource of the context.  NULL is accepted. */
 int mirage_destroy(mirage_ctx_t* ctx);
 
+#define MIRAGE_MAX_LAM 64 /* longest lambda grid of one candidate */
+
 /* Evaluate n_cand candidate lenses (the inner loop of Section 3: ray trace,
  * CGLS on Eq. TKReg for every lambda of the candidate, L-curve corner).
  *
  *  probs[n_probs]      host array of problem descriptors (device data pointers)
  *  lens[n_cand*7]      lens vectors (double)
  *  prob_idx[n_cand]    HOST array: problem of each candidate, in [0, n_probs)
- *  lambdas[n_cand*max_lam]  lambda grid per candidate (double, > 0, ascending)
+ *  lambdas[n_cand*max_lam]  lambda grid per candidate (double, > 0, ascending);
+ *                      1 <= max_lam <= MIRAGE_MAX_LAM, else MIRAGE_ERR_ARG
  *  n_lam[n_cand]       HOST array: lambdas used per candidate, 1..max_lam
  *  warm_x              nullable [n_cand*max_lam*max_ns] real: CG start per
  *                      item (max_ns = the largest sx*sy of the problems);
@@ -188,11 +191,16 @@ int mirage_last_launch_count(const mirage_ctx_t* ctx);
  * L-curve/finalize.  Waits for those events. */
 int mirage_last_phase_ms(mirage_ctx_t* ctx, double* ms);
 
-/* Per-phase SM clock totals (summed over CTAs) of the last call made with
- * opts->threads == -2: [0] L p and H p, [1] B conv and reduction, [2]
- * vector updates, [3] B^T conv, [4] L^T, reduction and p update, [5] FP64
- * refinement residuals, [6] item set-up, [7] unused.  Synchronous. */
-int mirage_last_phase_clocks(mirage_ctx_t* ctx, unsigned long long* clk8);
+/* Per-phase SM clock totals (thread 0 of each CTA, summed over CTAs) of the
+ * last call made with opts->threads == -2 that ran the fast CGLS kernel,
+ * MIRAGE_N_PHASE_CLOCKS values: [0] L p and H p, [1] B convolution, [2] its
+ * reduction, [3] vector updates and residual store, [4] B^T convolution,
+ * [5] L^T ray walk, [6] L^T join of cells split between walks, [7] L^T
+ * gather and H^T, [8] its reduction, [9] p update, [10] FP64 refinement
+ * residuals, [11] item set-up.  `clk` holds MIRAGE_N_PHASE_CLOCKS values.
+ * Synchronous. */
+#define MIRAGE_N_PHASE_CLOCKS 12
+int mirage_last_phase_clocks(mirage_ctx_t* ctx, unsigned long long* clk);
 
 /* Text of the last error raised on the calling thread ("" if none). */
 const char* mirage_last_error(void);

@@ -27,6 +27,7 @@ MIRAGE_MEM_DEVICE, MIRAGE_MEM_HOST = 0, 1
 MIRAGE_MODE_BATCHED, MIRAGE_MODE_PLAIN = 0, 1
 ST_MAXIT, ST_STAGNATION, ST_BREAKDOWN, ST_BAD_PARAM, ST_EMPTY_MAP, ST_LCURVE_FLAT = 1, 2, 4, 8, 16, 32
 MAX_LAM = 64
+N_PHASE_CLOCKS = 12  # MIRAGE_N_PHASE_CLOCKS
 
 
 class MirageError(RuntimeError):
@@ -227,7 +228,7 @@ def mirage_last_phase_ms(ctx):
 
 def mirage_last_phase_clocks(ctx):
     """Per-phase SM clock totals of the last phase-clocked call (see mirage.h)."""
-    buf = (ctypes.c_ulonglong * 8)()
+    buf = (ctypes.c_ulonglong * N_PHASE_CLOCKS)()
     _check(load_library().mirage_last_phase_clocks(ctx, buf), "mirage_last_phase_clocks")
     return list(buf)
 

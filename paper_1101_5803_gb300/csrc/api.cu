@@ -241,9 +241,7 @@ const void* pick_fast(mirage_ctx* ctx, const Prob<T>& P, int mode) {
     const Prob<float>& Pf = *reinterpret_cast<const Prob<float>*>(&P);
     const size_t b = fast_smem_bytes(Pf);
     if (b == 0 || (long long)b > ctx->max_smem_sm / 2 - 1024 || Pf.K >= MAX_K) return nullptr;
-    const int v = Pf.ns <= 4 * NTHREADS ? 0 : (Pf.ns <= 9 * NTHREADS ? 1 : -1);
-    if (v < 0) return nullptr;
-    return table().fast[Pf.K][v][mode];
+    return table().fast[Pf.K][0][mode];
 }
 
 // fast-kernel arguments (FP32 contexts only; never called for double)
@@ -661,8 +659,8 @@ int eval_impl(mirage_ctx* ctx, const mirage_problem_t* probs, int n_probs, const
     A.istat = dIst;
     A.phase_clk = nullptr;
     if (!graph && o.threads == -2) {
-        TRY(ctx->clk.ensure(8 * sizeof(unsigned long long)));
-        CK(cudaMemsetAsync(ctx->clk.p, 0, 8 * sizeof(unsigned long long), st));
+        TRY(ctx->clk.ensure(FAST_NPH * sizeof(unsigned long long)));
+        CK(cudaMemsetAsync(ctx->clk.p, 0, FAST_NPH * sizeof(unsigned long long), st));
         A.phase_clk = ctx->clk.as<unsigned long long>();
     }
 
@@ -991,9 +989,12 @@ int mirage_forward(mirage_ctx_t* ctx, const mirage_problem_t* prob, const double
 
 int mirage_last_launch_count(const mirage_ctx_t* ctx) { return ctx ? ctx->last_launches : 0; }
 
-int mirage_last_phase_clocks(mirage_ctx_t* ctx, unsigned long long* clk8) {
-    if (!ctx || !clk8 || !ctx->clk.p) return MIRAGE_ERR_ARG;
-    CK(cudaMemcpy(clk8, ctx->clk.p, 8 * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
+static_assert(MAX_LAM == MIRAGE_MAX_LAM, "lambda grid limit of the header and the kernels");
+
+int mirage_last_phase_clocks(mirage_ctx_t* ctx, unsigned long long* clk) {
+    static_assert(FAST_NPH == MIRAGE_N_PHASE_CLOCKS, "phase clock count of the header and the kernel");
+    if (!ctx || !clk || !ctx->clk.p) return MIRAGE_ERR_ARG;
+    CK(cudaMemcpy(clk, ctx->clk.p, FAST_NPH * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
     return MIRAGE_OK;
 }
 

@@ -5,14 +5,18 @@
 //   * one ray per pixel and an identity or Laplacian H (square H);
 //   * each thread owns exactly one 4x4 image tile (images up to 256 tiles)
 //     and keeps that tile's residual, sqrt(W), q = sqrt(W) B L p and mapped
-//     mask in registers; each thread also owns up to NSP source pixels
-//     (i = tid + k * blockDim.x) and keeps their x, s and sqrt(lam) H p;
-//   * shared memory holds only the two padded convolution buffers (P1 = L p,
+//     mask in registers; each thread also owns up to four source pixels
+//     (i = tid + k * blockDim.x) and keeps their x, s and sqrt(lam) H p,
+//     plus a bit mask of their occupied corner cells and existing neighbours;
+//   * shared memory holds the two padded convolution buffers (P1 = L p,
 //     reused for u = B^T sqrt(W) r at mapped pixels; P2 = sqrt(W) r, reused
-//     for the per-cell partial sums of L^T u), the rays in 12-byte form,
-//     16-bit cell starts, p and r_reg;
+//     for the four L^T corner planes), the rays in 12-byte form sorted by
+//     cell, 16-bit cell starts, p and r_reg;
+//   * L^T u is a balanced walk: every thread sums an equal run of the sorted
+//     rays into per-cell corner totals; cells split between runs are joined
+//     in a fixed order, so the result does not depend on scheduling;
 //   * the convolution uses packed FP32x2 FMAs (__ffma2_rn) on tap pairs
-//     stored duplicated in shared memory.
+//     stored duplicated in shared memory, or taps held as kernel parameters.
 #pragma once
 
 #include "kernels.cuh"
@@ -139,30 +143,94 @@ __device__ __forceinline__ void conv_tile_fast(const float* __restrict__ Pb, int
     }
 }
 
+// Sum of two compensated (hi, lo) pairs with error-free FP32 steps.
+__device__ __forceinline__ float2 pair_add(float2 a, float2 b) {
+    float s, e;
+    two_sum(a.x, b.x, s, e);
+    e += a.y + b.y;
+    const float hi = s + e;
+    return make_float2(hi, e - (hi - s));
+}
+
+// Block sum with one barrier, delivered to every thread of an NTHREADS
+// block: the warps' compensated pairs are combined along a fixed binary
+// tree (depth log2 of the warp count instead of a serial chain), so every
+// thread holds the same value.  `buf` holds 2 x 64 floats; alternate `half`.
+__device__ __forceinline__ float2 block_pair_tree(float v, float* buf, int half) {
+    constexpr int NW = NTHREADS / 32;
+    float2* b = reinterpret_cast<float2*>(buf) + 32 * half;
+    const float2 w = warp_pair(v);
+    if ((threadIdx.x & 31) == 0) b[threadIdx.x >> 5] = w;
+    __syncthreads();
+    float2 x[NW];
+#pragma unroll
+    for (int i = 0; i < NW; ++i) x[i] = b[i];
+#pragma unroll
+    for (int st = 1; st < NW; st *= 2)
+#pragma unroll
+        for (int i = 0; i + st < NW; i += 2 * st) x[i] = pair_add(x[i], x[i + st]);
+    return x[0];
+}
+
+// (H v)_i of the square regularisers (identity, or the five-point Laplacian
+// with the neighbours that exist); nb = neighbour bits (1 left, 2 right,
+// 4 below, 8 above).  The Laplacian is symmetric, so this is also H^T.
+__device__ __forceinline__ float hrow_fast(const float* __restrict__ v, int i, unsigned nb, int sx, int reg) {
+    if (reg != 2) return v[i];
+    float a = 4.f * v[i];
+    if (nb & 1u) a -= v[i - 1];
+    if (nb & 2u) a -= v[i + 1];
+    if (nb & 4u) a -= v[i - sx];
+    if (nb & 8u) a -= v[i + sx];
+    return a;
+}
+
+// Per-item constants of the fast kernel, written by thread 0 into shared
+// memory (read back where needed instead of being held in registers).
+struct FastItem {
+    float psf2;             // sum of squared PSF taps
+    int R;                  // rays per thread in the L^T walk (odd)
+    int nfz, top, mfr, W4;  // P2 frame float4s overlapped by the L^T planes
+    int xl;                 // xoff / 4
+    float inv_mfr;          // 1 / mfr
+    float zero;             // 0: read in place of absent neighbours and cells
+};
+static_assert(sizeof(FastItem) <= 128, "fast-kernel item constants must fit the control slot");
+
+constexpr int FAST_NPH = 12;  // per-phase clock slots (see mirage_last_phase_clocks)
+constexpr size_t FAST_HDR = 16 + 2 * 33 * sizeof(double) + 128 + 16 * sizeof(unsigned long long);
+
 template <int K, int NSP, int MODE>
 __global__ void __launch_bounds__(NTHREADS, 2) k_cgls_fast(const __grid_constant__ FastArgs FA) {
+    static_assert(NSP <= 4, "the per-thread masks describe at most four source pixels");
     using T = float;
+    constexpr int bs = NTHREADS;
     const CglsArgs<float>& A = FA.A;
     extern __shared__ __align__(16) unsigned char smem[];
-    const int tid = threadIdx.x, bs = blockDim.x;
+    const int tid = threadIdx.x;
     int* slot = reinterpret_cast<int*>(smem);
     double* red = reinterpret_cast<double*>(smem + 16);
-    CgCtl* ctl = reinterpret_cast<CgCtl*>(smem + 16 + 2 * 33 * sizeof(double));
-    float* pbuf = reinterpret_cast<float*>(red);  // 2 x 32 float2 for block_pair_all
+    FastItem* fi = reinterpret_cast<FastItem*>(smem + 16 + 2 * 33 * sizeof(double));
+    unsigned long long* phs = reinterpret_cast<unsigned long long*>(smem + 16 + 2 * 33 * sizeof(double) + 128);
+    float* pbuf = reinterpret_cast<float*>(red);  // 2 x 32 float2 for block_pair_tree
     int last_c = -1;
     int which = 0;
-    // per-phase clocks (thread 0): 0 L p + H p, 1 B conv + reduce, 2 updates,
-    // 3 B^T conv, 4 L^T + reduce + p, 5 FP64 refinement, 6 item setup
-    unsigned long long ph[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    const bool timed = A.phase_clk != nullptr && threadIdx.x == 0;
-    unsigned long long t_last = timed ? clock64() : 0ull;
-#define PHASE(n)                                  \
-    do {                                          \
-        if (timed) {                              \
+    // per-phase clocks (thread 0, kept in shared memory): 0 L p + H p,
+    // 1 B conv, 2 delta reduction, 3 updates + residual store, 4 B^T conv,
+    // 5 L^T ray walk, 6 L^T combination of split cells, 7 L^T gather + H^T,
+    // 8 gamma reduction, 9 p update, 10 FP64 refinement, 11 item set-up
+    const bool timed = A.phase_clk != nullptr && tid == 0;
+    if (timed) {
+        for (int i = 0; i < 15; ++i) phs[i] = 0ull;
+        phs[15] = clock64();
+    }
+#define PHASE(n)                                   \
+    do {                                           \
+        if (timed) {                               \
             const unsigned long long t_ = clock64(); \
-            ph[n] += t_ - t_last;                 \
-            t_last = t_;                          \
-        }                                         \
+            phs[n] += t_ - phs[15];                \
+            phs[15] = t_;                          \
+        }                                          \
     } while (0)
 
     while (true) {
@@ -179,7 +247,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_cgls_fast(const __grid_constant
         const Geo<T> g = geo_of(P, nent);
 
         // ---- carve shared memory
-        unsigned char* sp = smem + 16 + 2 * 33 * sizeof(double) + 128;
+        unsigned char* sp = smem + FAST_HDR;
         float2* taps2 = reinterpret_cast<float2*>(sp);
         sp += align_up<T>(sizeof(float2) * 2 * K * K, 16);
         Work<T> w;
@@ -200,6 +268,8 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_cgls_fast(const __grid_constant
         sp += align_up<T>(sizeof(float) * g.ns, 16);
         float* rreg = reinterpret_cast<float*>(sp);
         sp += align_up<T>(sizeof(float) * g.nreg, 16);
+        float* Sq = reinterpret_cast<float*>(sp);  // L^T partials of cells split across ranges: Sq[q * bs + t]
+        sp += sizeof(float) * 4 * bs;
 
         // ---- global buffers: refinement (double) and its FP32 hand-over
         unsigned char* slab = reinterpret_cast<unsigned char*>(A.slab) + (long long)blockIdx.x * A.slab_stride;
@@ -254,6 +324,30 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_cgls_fast(const __grid_constant
             w.Pa[i] = 0.0;
             w.Pb[i] = 0.0;
         }
+        if (tid < 32) {
+            float a = 0.f;
+            for (int i = tid; i < K * K; i += 32) a = fmaf(P.psf[i], P.psf[i], a);
+            for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+            if (tid == 0) {
+                fi->psf2 = a;
+                // L^T walk: R consecutive rays per thread, R odd so that the
+                // lanes' reads at stride R fall on distinct banks
+                fi->R = ((nent + bs - 1) / bs) | 1;
+                // the L^T planes occupy P2[0, 4 ns): its frame float4s there
+                // (top frame rows, then the side margins of interior rows)
+                // are cleared again before each B^T convolution
+                const int W4 = g.Wp >> 2, tiles_y = g.ntiles / g.tiles_x;
+                const int mfr = W4 - g.tiles_x;
+                const int rows = max(0, min((4 * g.ns + g.Wp - 1) / g.Wp - g.hk, TILE * tiles_y));
+                fi->W4 = W4;
+                fi->mfr = mfr;
+                fi->top = g.hk * W4;
+                fi->nfz = g.hk * W4 + rows * mfr;
+                fi->xl = g.xoff >> 2;
+                fi->inv_mfr = mfr > 0 ? 1.f / (float)mfr : 0.f;
+                fi->zero = 0.f;
+            }
+        }
         __syncthreads();
 
         // ---- tile ownership, sqrt(W) and mapped mask in registers
@@ -284,6 +378,46 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_cgls_fast(const __grid_constant
         }
         __syncthreads();
         for (int i = tid; i < g.plen; i += bs) P1[i] = 0.f;
+
+        // ---- per source pixel of this thread: which of its four corner
+        // cells hold rays (bits 4kk..4kk+3: cells (ia, ib), (ia-1, ib),
+        // (ia, ib-1), (ia-1, ib-1)) and which Laplacian neighbours exist
+        // (bits 16+4kk..: left, right, below, above)
+        unsigned msk = 0;
+#pragma unroll
+        for (int kk = 0; kk < NSP; ++kk) {
+            const int i = tid + kk * bs;
+            if (i < g.ns) {
+                const int ib = i / g.sx, ia = i - ib * g.sx;
+                const bool lf = ia >= 1, rt = ia <= g.sx - 2, dn = ib >= 1, up = ib <= g.sy - 2;
+                const int cl = ib * g.ncx + ia;
+                unsigned m = 0;
+                if (rt && up && cst16[cl + 1] > cst16[cl]) m |= 1u;
+                if (lf && up && cst16[cl] > cst16[cl - 1]) m |= 2u;
+                if (rt && dn && cst16[cl - g.ncx + 1] > cst16[cl - g.ncx]) m |= 4u;
+                if (lf && dn && cst16[cl - g.ncx] > cst16[cl - g.ncx - 1]) m |= 8u;
+                const unsigned nb = (ia > 0 ? 1u : 0u) | (ia < g.sx - 1 ? 2u : 0u) | (ib > 0 ? 4u : 0u) |
+                                    (ib < g.sy - 1 ? 8u : 0u);
+                msk |= (m | (nb << 16)) << (4 * kk);
+            }
+        }
+        // ---- this thread's ray range of the L^T walk: does its first cell
+        // continue from the previous range (bit 0: its partial then goes to
+        // Sq), and does it own a cell that runs on into later ranges (bits
+        // 1..: how many; it adds their partials, in range order, after the walk)
+        const int R = fi->R;
+        int wflags = 0;
+        {
+            const int e0 = min(tid * R, nent), e1 = min(e0 + R, nent);
+            if (e0 < e1) {
+                const unsigned kf = eidx[e0] >> 16, kl = eidx[e1 - 1] >> 16;
+                const bool cin = e0 > 0 && (eidx[e0 - 1] >> 16) == kf;
+                int ncont = 0;
+                if (!(cin && kf == kl))
+                    for (int t2 = tid + 1; t2 < bs && t2 * R < nent && (eidx[t2 * R] >> 16) == kl; ++t2) ++ncont;
+                wflags = (cin ? 1 : 0) | (ncont << 1);
+            }
+        }
         __syncthreads();
 
         const int cstat = cs.cstat[c];
@@ -304,7 +438,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_cgls_fast(const __grid_constant
         const double lam = A.lambdas[(long long)c * A.max_lam + k];
         const float sl = (float)sqrt(lam);
         const int maxit = A.maxit > 0 ? A.maxit : 25 * g.ns;
-        PHASE(6);
+        PHASE(11);
 
         // ---- ||rhs|| in FP64
         for (int t = tid; t < g.ntiles; t += bs) {
@@ -337,12 +471,6 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_cgls_fast(const __grid_constant
         // the CGLS iterations two- to threefold.
         float minv[NSP];
         {
-            if (tid < 32) {
-                float a = 0.f;
-                for (int i = tid; i < K * K; i += 32) a = fmaf(P.psf[i], P.psf[i], a);
-                for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-                if (tid == 0) reinterpret_cast<float*>(ctl)[0] = a;
-            }
             float4* cellp = reinterpret_cast<float4*>(P2);
             for (int cell = tid; cell < g.ncells; cell += bs) {
                 const int k0 = cst16[cell], k1 = cst16[cell + 1];
@@ -362,7 +490,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_cgls_fast(const __grid_constant
                 cellp[cell] = make_float4(c00, c10, c01, c11);
             }
             __syncthreads();
-            const float psf2 = reinterpret_cast<const float*>(ctl)[0];
+            const float psf2 = fi->psf2;
             const float* cp = reinterpret_cast<const float*>(cellp);
 #pragma unroll
             for (int kk = 0; kk < NSP; ++kk) {
@@ -399,10 +527,15 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_cgls_fast(const __grid_constant
         double chi2 = 0, reg2 = 0, g64 = 0, rel64 = 0, prev_rel = 1e300;
         constexpr int MAX_OUTER = 16;
         const double eta_min = 0.03;
+        const int nsv = g.ns, sxv = g.sx, regv = g.reg;
+        float* Q = P2;  // L^T corner planes: Q[q * ns + base], q = 00, 10, 01, 11
+        // signed offset of the shared zero from Q (both in the one shared
+        // array): absent corner cells read it through an index select
+        const int zq = (int)(&fi->zero - Q);
         for (int outer = 0;; ++outer) {
-            PHASE(6);
+            PHASE(11);
             chi2 = residual64<T>(w, g, lam, red, which, reg2, g64);
-            PHASE(5);
+            PHASE(10);
             rel64 = rhsn > 0 ? sqrt(g64) / rhsn : 0.0;
             if (!isfinite(rel64)) {
                 status |= ST_BREAK;
@@ -429,7 +562,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_cgls_fast(const __grid_constant
                 const int i = tid + kk * bs;
                 x[kk] = 0.f;
                 s[kk] = 0.f;
-                if (i < g.ns) {
+                if (i < nsv) {
                     s[kk] = w.s[i];
                     const float z = minv[kk] * s[kk];
                     p[i] = z;
@@ -450,30 +583,44 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_cgls_fast(const __grid_constant
             int half = 0, it_in = 0, best_it = 0, brk = 0, stop = 0;
             float gam, g0, best = 1.f;
             {
-                const float2 gp = block_pair_all(gs, pbuf, half);
+                const float2 gp = block_pair_tree(gs, pbuf, half);
                 half ^= 1;
                 gam = gp.x + gp.y;
                 g0 = gam;
                 brk = !isfinite(gam);
                 stop = brk || !(gam > 0.f) || total_it >= maxit;
             }
-            const int stag_window = max(4000, 2 * g.ns);
+            const int stag_window = max(4000, 2 * nsv);
             while (!stop) {
-                // P1 <- L p at the mapped pixels; q_reg = sqrt(lam) H p
-                for (int e = tid; e < nent; e += bs) {
-                    const unsigned id = eidx[e];
-                    const float2 uv = euv[e];
-                    const float* s0 = p + (id >> 16);
-                    P1[id & 0xffffu] = (1.f - uv.y) * ((1.f - uv.x) * s0[0] + uv.x * s0[1]) +
-                                       uv.y * ((1.f - uv.x) * s0[g.sx] + uv.x * s0[g.sx + 1]);
+                // P1 <- L p at the mapped pixels, four rays at a time (all
+                // loads first, so their latencies overlap); q_reg = sqrt(lam) H p
+                for (int e = tid; e < nent; e += 4 * bs) {
+                    unsigned id[4];
+                    float2 uv[4];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const int ej = e + j * bs < nent ? e + j * bs : e;
+                        id[j] = eidx[ej];
+                        uv[j] = euv[ej];
+                    }
+                    float val[4];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const float* s0 = p + (id[j] >> 16);
+                        val[j] = (1.f - uv[j].y) * ((1.f - uv[j].x) * s0[0] + uv[j].x * s0[1]) +
+                                 uv[j].y * ((1.f - uv[j].x) * s0[sxv] + uv[j].x * s0[sxv + 1]);
+                    }
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        if (e + j * bs < nent) P1[id[j] & 0xffffu] = val[j];
                 }
                 float dq = 0.f;
 #pragma unroll
                 for (int kk = 0; kk < NSP; ++kk) {
                     const int i = tid + kk * bs;
                     qr[kk] = 0.f;
-                    if (i < g.ns) {
-                        qr[kk] = sl * apply_H_row<T, float>(g, p, i);
+                    if (i < nsv) {
+                        qr[kk] = sl * hrow_fast(p, i, msk >> (16 + 4 * kk), sxv, regv);
                         dq = fmaf(qr[kk], qr[kk], dq);
                     }
                 }
@@ -492,10 +639,11 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_cgls_fast(const __grid_constant
 #pragma unroll
                     for (int qq = 0; qq < 16; ++qq) q[qq] = 0.f;
                 }
-                const float2 dl = block_pair_all(dq, pbuf, half);
+                PHASE(1);
+                const float2 dl = block_pair_tree(dq, pbuf, half);
                 half ^= 1;
                 const float delta = dl.x + dl.y;
-                PHASE(1);
+                PHASE(2);
                 if (!(delta > 0.f) || !isfinite(delta)) {
                     brk = 1;
                     break;
@@ -504,7 +652,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_cgls_fast(const __grid_constant
 #pragma unroll
                 for (int kk = 0; kk < NSP; ++kk) {
                     const int i = tid + kk * bs;
-                    if (i < g.ns) {
+                    if (i < nsv) {
                         x[kk] = fmaf(a, p[i], x[kk]);
                         rreg[i] = fmaf(-a, qr[kk], rreg[i]);
                     }
@@ -521,8 +669,22 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_cgls_fast(const __grid_constant
                         st4(P2 + pp0 + r * g.Wp, o);
                     }
                 }
+                // the previous L^T planes overwrote part of P2's zero frame
+                {
+                    const int nfz = fi->nfz, top = fi->top;
+                    for (int f = tid; f < nfz; f += bs) {
+                        int q4 = f;
+                        if (f >= top) {
+                            const int f2 = f - top, mfr = fi->mfr, xl = fi->xl;
+                            const int r = (int)(((float)f2 + 0.5f) * fi->inv_mfr);
+                            const int j = f2 - r * mfr;
+                            q4 = (g.hk + r) * fi->W4 + (j < xl ? j : j + g.tiles_x);
+                        }
+                        reinterpret_cast<float4*>(P2)[q4] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    }
+                }
                 __syncthreads();  // P2 complete
-                PHASE(2);
+                PHASE(3);
                 // u = B^T P2 on the owned tile, stored into P1 at mapped pixels
                 if (own) {
                     float o16[16];
@@ -536,50 +698,104 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_cgls_fast(const __grid_constant
                     }
                 }
                 __syncthreads();  // u complete
-                PHASE(3);
-                // L^T u in two passes (deterministic): per cell, the four corner
-                // sums of its rays (each ray read once), kept in P2's storage;
-                // then per source pixel, the fixed-order sum of the corners
-                // it receives from its (up to) four cells
-                float4* cellp = reinterpret_cast<float4*>(P2);
-                for (int cell = tid; cell < g.ncells; cell += bs) {
-                    const int k0 = cst16[cell], k1 = cst16[cell + 1];
-                    float c00 = 0.f, c10 = 0.f, c01 = 0.f, c11 = 0.f;
-#pragma unroll 2
-                    for (int e = k0; e < k1; ++e) {
-                        const unsigned id = eidx[e];
-                        const float2 uv = euv[e];
-                        const float U = P1[id & 0xffffu];
-                        const float uU = uv.x * U, u0 = U - uU;  // u U, (1-u) U
-                        c00 = fmaf(1.f - uv.y, u0, c00);
-                        c10 = fmaf(1.f - uv.y, uU, c10);
-                        c01 = fmaf(uv.y, u0, c01);
-                        c11 = fmaf(uv.y, uU, c11);
+                PHASE(4);
+                // L^T u, pass 1: each thread walks its R consecutive rays (sorted
+                // by cell) and sums, per cell, the four corner weights times u;
+                // a cell's total goes to the planes (indexed by the cell's base
+                // source pixel), the partial of a cell continued from the
+                // previous range to Sq.  The next ray is loaded before the
+                // current one is used, and the sums are stored at the last ray
+                // of each cell run (known from the next ray's cell)
+                {
+                    const int e0 = min(tid * R, nent), e1 = min(e0 + R, nent);
+                    if (e0 < e1) {
+                        unsigned id = eidx[e0];
+                        unsigned cur = id >> 16;
+                        float* dst = (wflags & 1) ? Sq + tid : Q + cur;
+                        int ps = (wflags & 1) ? bs : nsv;
+                        float2 uv = euv[e0];
+                        float U = P1[id & 0xffffu];
+                        float c00 = 0.f, c10 = 0.f, c01 = 0.f, c11 = 0.f;
+                        for (int e = e0; e < e1; ++e) {
+                            const int en = min(e + 1, e1 - 1);
+                            const unsigned idn = eidx[en];
+                            const float2 uvn = euv[en];
+                            const float Un = P1[idn & 0xffffu];
+                            const unsigned key = id >> 16;
+                            if (key != cur) {  // a new cell: its sums go to the planes
+                                cur = key;
+                                dst = Q + key;
+                                ps = nsv;
+                                c00 = c10 = c01 = c11 = 0.f;
+                            }
+                            const float uU = uv.x * U, u0 = U - uU;  // u U, (1-u) U
+                            c00 = fmaf(1.f - uv.y, u0, c00);
+                            c10 = fmaf(1.f - uv.y, uU, c10);
+                            c01 = fmaf(uv.y, u0, c01);
+                            c11 = fmaf(uv.y, uU, c11);
+                            if (e == e1 - 1 || (idn >> 16) != key) {
+                                dst[0] = c00;
+                                dst[ps] = c10;
+                                dst[2 * ps] = c01;
+                                dst[3 * ps] = c11;
+                            }
+                            id = idn;
+                            uv = uvn;
+                            U = Un;
+                        }
                     }
-                    cellp[cell] = make_float4(c00, c10, c01, c11);
                 }
                 __syncthreads();
-                PHASE(7);
+                PHASE(5);
+                // pass 2: the owner of a cell that runs on into later ranges adds
+                // their partials in range order (a fixed order: deterministic)
+                if (wflags >> 1) {
+                    const int e1 = min(min(tid * R, nent) + R, nent);
+                    const unsigned kl = eidx[e1 - 1] >> 16;
+                    float a0 = Q[kl], a1 = Q[nsv + kl], a2 = Q[2 * nsv + kl], a3 = Q[3 * nsv + kl];
+                    const int t_end = tid + 1 + (wflags >> 1);
+                    for (int t2 = tid + 1; t2 < t_end; ++t2) {
+                        a0 += Sq[t2];
+                        a1 += Sq[bs + t2];
+                        a2 += Sq[2 * bs + t2];
+                        a3 += Sq[3 * bs + t2];
+                    }
+                    Q[kl] = a0;
+                    Q[nsv + kl] = a1;
+                    Q[2 * nsv + kl] = a2;
+                    Q[3 * nsv + kl] = a3;
+                }
+                __syncthreads();
+                PHASE(6);
+                // pass 3: per source pixel, the fixed-order sum of the corners it
+                // receives from its (up to) four occupied cells, plus sqrt(lam) H^T r_reg
                 float gsum = 0.f;
 #pragma unroll
                 for (int kk = 0; kk < NSP; ++kk) {
                     const int i = tid + kk * bs;
-                    if (i < g.ns) {
-                        const int ib = i / g.sx, ia = i - ib * g.sx;
-                        const float* cp = reinterpret_cast<const float*>(cellp);
+                    if (i < nsv) {
+                        const unsigned m = msk >> (4 * kk);
+                        // empty or absent cells read the shared zero (no branches)
+                        // empty or absent cells read the shared zero: no branches,
+                        // four independent loads; adding +0 changes nothing
+                        const int q0 = (m & 1u) ? i : zq;
+                        const int q1 = (m & 2u) ? nsv + i - 1 : zq;
+                        const int q2 = (m & 4u) ? 2 * nsv + i - sxv : zq;
+                        const int q3 = (m & 8u) ? 3 * nsv + i - sxv - 1 : zq;
                         float acc = 0.f;
-                        // (dx, dy) = position of i in the cell: component dx + 2 dy
-                        if (ib <= g.sy - 2 && ia <= g.sx - 2) acc += cp[4 * (ib * g.ncx + ia) + 0];
-                        if (ib <= g.sy - 2 && ia >= 1) acc += cp[4 * (ib * g.ncx + ia - 1) + 1];
-                        if (ib >= 1 && ia <= g.sx - 2) acc += cp[4 * ((ib - 1) * g.ncx + ia) + 2];
-                        if (ib >= 1 && ia >= 1) acc += cp[4 * ((ib - 1) * g.ncx + ia - 1) + 3];
-                        const float gr = acc + sl * apply_HT_at<T, float>(g, rreg, i, ia, ib);
+                        acc += Q[q0];
+                        acc += Q[q1];
+                        acc += Q[q2];
+                        acc += Q[q3];
+                        const float gr = acc + sl * hrow_fast(rreg, i, m >> 16, sxv, regv);
                         s[kk] = minv[kk] * gr;  // preconditioned gradient z = M^-1 g
                         gsum = fmaf(gr, s[kk], gsum);
                     }
                 }
-                const float2 gp = block_pair_all(gsum, pbuf, half);
+                PHASE(7);
+                const float2 gp = block_pair_tree(gsum, pbuf, half);
                 half ^= 1;
+                PHASE(8);
                 const float gnew = gp.x + gp.y;
                 const float bt = gnew / gam;
                 gam = gnew;
@@ -603,12 +819,10 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_cgls_fast(const __grid_constant
 #pragma unroll
                 for (int kk = 0; kk < NSP; ++kk) {
                     const int i = tid + kk * bs;
-                    if (i < g.ns) p[i] = fmaf(bt, p[i], s[kk]);
+                    if (i < nsv) p[i] = fmaf(bt, p[i], s[kk]);
                 }
-                // the cell partials overwrote P2's zero frame: clear them
-                for (int cell = tid; cell < g.ncells; cell += bs) cellp[cell] = make_float4(0.f, 0.f, 0.f, 0.f);
                 __syncthreads();
-                PHASE(4);
+                PHASE(9);
             }
             if (brk) {
                 status |= ST_BREAK;
@@ -617,10 +831,11 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_cgls_fast(const __grid_constant
 #pragma unroll
             for (int kk = 0; kk < NSP; ++kk) {
                 const int i = tid + kk * bs;
-                if (i < g.ns) w.x64[i] += (double)x[kk];
+                if (i < nsv) w.x64[i] += (double)x[kk];
             }
-            // the inner loop leaves u in P1 at mapped pixels: restore zeros
-            // there is not needed (L p overwrites every mapped pixel)
+            // the inner loop leaves u in P1 at mapped pixels (L p overwrites
+            // every one of them) and the L^T planes in P2 (the frame is
+            // cleared again before the next B^T convolution)
             __syncthreads();
         }
 
@@ -634,16 +849,19 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_cgls_fast(const __grid_constant
         }
     }
     if (timed)
-        for (int i = 0; i < 8; ++i) atomicAdd(A.phase_clk + i, ph[i]);
+        for (int i = 0; i < FAST_NPH; ++i) atomicAdd(A.phase_clk + i, phs[i]);
 #undef PHASE
 }
 
-// shared memory of the fast variant (0 if the problem is not eligible)
+// shared memory of the fast variant (0 if the problem is not eligible):
+// one ray per pixel, a square regulariser, at most four source pixels and
+// one image tile per thread, 16-bit ray/pixel/cell indices, and room for the
+// four L^T corner planes (4 ns floats) in P2 above its last interior row
 __host__ inline size_t fast_smem_bytes(const Prob<float>& P) {
-    if (P.Np != 1 || P.ntiles > NTHREADS || P.plen >= 65536 || P.nrays >= 65536 || P.ns >= 65536 ||
-        P.nreg != P.ns || 4 * P.ncells > P.plen)
+    if (P.Np != 1 || P.ntiles > NTHREADS || P.plen >= 65536 || P.nrays >= 65536 || P.ns > 4 * NTHREADS ||
+        P.nreg != P.ns || 4 * P.ncells > P.plen || 4 * P.ns > (P.hk + TILE * P.tiles_y) * P.Wp)
         return 0;
-    size_t o = 16 + 2 * 33 * sizeof(double) + 128;
+    size_t o = FAST_HDR;
     o += align_up<float>(sizeof(float2) * 2 * P.K * P.K, 16);
     o += align_up<float>(sizeof(double) * 2 * P.K * P.kp, 16);
     o += 2 * align_up<float>(sizeof(float) * P.plen, 16);
@@ -652,6 +870,7 @@ __host__ inline size_t fast_smem_bytes(const Prob<float>& P) {
     o += align_up<float>(sizeof(unsigned short) * (size_t)(P.ncells + 1), 16);
     o += align_up<float>(sizeof(float) * P.ns, 16);
     o += align_up<float>(sizeof(float) * P.nreg, 16);
+    o += sizeof(float) * 4 * NTHREADS;
     return o;
 }
 

@@ -37,3 +37,10 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(binding.mirage_geom_t) == 88
     assert ctypes.sizeof(binding.mirage_opts_t) == 40  # double + 8 ints
     assert ctypes.sizeof(binding.mirage_problem_t) == 88 + 32
+
+
+def test_header_constants_match_binding():
+    import re
+    txt = open(binding.HEADER).read()
+    assert int(re.search(r"#define MIRAGE_N_PHASE_CLOCKS (\d+)", txt).group(1)) == binding.N_PHASE_CLOCKS
+    assert int(re.search(r"#define MIRAGE_MAX_LAM (\d+)", txt).group(1)) == binding.MAX_LAM

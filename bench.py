@@ -297,13 +297,15 @@ def run_gpu(args):
     from paper_1101_5803_gb300.ga import GAConfig, run_ga
     n_gen = int(os.environ.get("MIRAGE_GA_GENERATIONS", "4"))
     ga_res = {}
-    for name, sur_on in (("with_surrogate", True), ("without", False)):
-        cfg = GAConfig(pop=N_CAND, generations=n_gen, surrogate=sur_on, seed=7)
+    for name, sur_on, chain in (("with_surrogate", True, False), ("with_surrogate_lambda_chains", True, True),
+                                ("without", False, False)):
+        cfg = GAConfig(pop=N_CAND, generations=n_gen, surrogate=sur_on, lam_chain=chain, seed=7)
         hist, _, bchi = run_ga(ctx, wl, cfg)
         gens = hist[1:]
         t_gen = sum(h.seconds for h in gens)
         ga_res[name] = {"exact_evals_per_s": sum(h.exact_evals for h in gens) / t_gen,
                         "decisions_per_s": sum(h.decisions for h in gens) / t_gen,
+                        "cg_iters_per_exact_eval": sum(h.cg_iters for h in gens) / max(1, sum(h.exact_evals for h in gens)),
                         "best_chi2_by_gen": [round(h.best_chi2, 2) for h in hist],
                         "screened_gens": int(sum(h.screened for h in gens)),
                         "rank_corr_by_gen": [None if h.surrogate_rho is None else round(h.surrogate_rho, 3)

@@ -136,6 +136,15 @@ int mirage_destroy(mirage_ctx_t* ctx);
  *  warm_x              nullable [n_cand*max_lam*max_ns] real: CG start per
  *                      item (max_ns = the largest sx*sy of the problems);
  *                      NULL = start from zero (the paper's blank source)
+ *  lam_start           nullable HOST array [n_cand]: a predicted corner index
+ *                      per candidate (clamped to [0, n_lam-1]).  When given
+ *                      (batched mode), each candidate's lambdas are solved as
+ *                      two chains, lam_start down to 0 and lam_start+1 up to
+ *                      n_lam-1, and every lambda after the first of its chain
+ *                      starts from the solution of its neighbour nearer to
+ *                      lam_start (a chain's first lambda starts from warm_x,
+ *                      or zero).  Results agree with unchained calls to the
+ *                      solver tolerance.  Ignored in plain mode.
  * Outputs ([n_cand*max_lam] unless noted; entries beyond n_lam untouched):
  *  chi2, reg           double: Eq. chi2 of the solution and ||H s||^2
  *  iters               int: CG iterations used
@@ -152,7 +161,7 @@ int mirage_destroy(mirage_ctx_t* ctx);
 int mirage_eval_batch(mirage_ctx_t* ctx, const mirage_problem_t* probs, int n_probs,
                       const double* lens, const int* prob_idx, int n_cand,
                       const double* lambdas, const int* n_lam, int max_lam,
-                      const mirage_opts_t* opts, const void* warm_x,
+                      const mirage_opts_t* opts, const void* warm_x, const int* lam_start,
                       double* chi2, double* reg, int* iters, double* relres, int* item_status,
                       int* corner, double* kappa, void* s_out, void* all_x, int* status,
                       void* stream);

@@ -72,7 +72,7 @@ def load_library():
     lib.mirage_destroy.restype = ip
     lib.mirage_eval_batch.argtypes = [vp, ctypes.POINTER(mirage_problem_t), i, vp, vp, i, vp, vp, i,
                                       ctypes.POINTER(mirage_opts_t), vp, vp, vp, vp, vp, vp, vp, vp, vp, vp,
-                                      vp, vp]
+                                      vp, vp, vp]
     lib.mirage_eval_batch.restype = ip
     lib.mirage_lcurve.argtypes = [vp, vp, vp, i, i, vp, vp, vp, vp]
     lib.mirage_lcurve.restype = ip
@@ -174,7 +174,7 @@ def mirage_last_launch_count(ctx) -> int:
 
 
 def mirage_eval_batch(ctx, probs, lens, prob_idx, lambdas, n_lam, *, tol=1e-6, maxit=0,
-                      mode=MIRAGE_MODE_BATCHED, use_graph=False, replace_every=0, warm_x=None,
+                      mode=MIRAGE_MODE_BATCHED, use_graph=False, replace_every=0, warm_x=None, lam_start=None,
                       want_s=True, want_all_x=False, want_kappa=True, out=None, stream=None, real=torch.float32,
                       phase_timing=False, phase_clocks=False, variant=0):
     """Evaluate candidates; returns a dict of output tensors (see mirage.h).
@@ -183,7 +183,8 @@ def mirage_eval_batch(ctx, probs, lens, prob_idx, lambdas, n_lam, *, tol=1e-6, m
     tensors (host tensors select the host-memory path); ``prob_idx`` and
     ``n_lam`` are host integer sequences.  ``out`` may pass preallocated
     outputs (same keys as the returned dict) to keep pointers stable for
-    graph replay.
+    graph replay.  ``lam_start`` (host ints, one per candidate) solves each
+    candidate's lambdas as warm-started chains from that index (mirage.h).
     """
     lib = load_library()
     n = int(lens.shape[0])
@@ -193,6 +194,9 @@ def mirage_eval_batch(ctx, probs, lens, prob_idx, lambdas, n_lam, *, tol=1e-6, m
     max_ns = max(int(p.geom.sx) * int(p.geom.sy) for p in probs)
     pidx = np.ascontiguousarray(np.asarray(prob_idx, dtype=np.int32))
     nl = np.ascontiguousarray(np.asarray(n_lam, dtype=np.int32))
+    ls = None if lam_start is None else np.ascontiguousarray(np.asarray(lam_start, dtype=np.int32))
+    if ls is not None and ls.shape != (n,):
+        raise ValueError("lam_start needs one index per candidate")
     if out is None:
         mk = lambda shape, dt: torch.empty(shape, dtype=dt, device=dev, pin_memory=host and torch.cuda.is_available())
         out = {"chi2": mk((n, max_lam), torch.float64), "reg": mk((n, max_lam), torch.float64),
@@ -212,7 +216,7 @@ def mirage_eval_batch(ctx, probs, lens, prob_idx, lambdas, n_lam, *, tol=1e-6, m
     rc = lib.mirage_eval_batch(
         ctx, arr, len(probs), _ptr(lens.contiguous()), pidx.ctypes.data_as(ctypes.c_void_p), n,
         _ptr(lambdas.contiguous()), nl.ctypes.data_as(ctypes.c_void_p), max_lam, ctypes.byref(opts),
-        _ptr(warm_x), _ptr(out["chi2"]), _ptr(out["reg"]), _ptr(out["iters"]), _ptr(out.get("relres")),
+        _ptr(warm_x), None if ls is None else ls.ctypes.data_as(ctypes.c_void_p), _ptr(out["chi2"]), _ptr(out["reg"]), _ptr(out["iters"]), _ptr(out.get("relres")),
         _ptr(out.get("item_status")), _ptr(out["corner"]), _ptr(out.get("kappa")), _ptr(out.get("s")),
         _ptr(out.get("all_x")), _ptr(out["status"]), None if host else _stream_ptr(stream))
     _check(rc, "mirage_eval_batch")

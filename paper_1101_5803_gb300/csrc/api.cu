@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -299,16 +300,20 @@ struct Stager {
     }
 };
 
+// work item of the CGLS kernels: lambdas k_first..k_last of candidate c,
+// solved in order by one CTA (see ChainPos)
+inline int pack_chain(int c, int k_first, int k_last) { return (c * MAX_LAM + k_first) * MAX_LAM + k_last; }
+
 template <typename T>
 int eval_impl(mirage_ctx* ctx, const mirage_problem_t* probs, int n_probs, const double* lens, const int* prob_idx,
               int n_cand, const double* lambdas, const int* n_lam, int max_lam, const mirage_opts_t* opts,
-              const void* warm_x, double* chi2, double* reg, int* iters, double* relres, int* item_status,
+              const void* warm_x, const int* lam_start, double* chi2, double* reg, int* iters, double* relres, int* item_status,
               int* corner, double* kappa, void* s_out, void* all_x, int* status, cudaStream_t st) {
     constexpr int prec = prec_of<T>();
     ctx->last_launches = 0;
     if (n_cand == 0) return MIRAGE_OK;
     if (!probs || n_probs < 1 || !lens || !prob_idx || !lambdas || !n_lam || !chi2 || !reg || !iters || !corner ||
-        !status || max_lam < 1 || max_lam > MAX_LAM || n_cand < 0) {
+        !status || max_lam < 1 || max_lam > MAX_LAM || n_cand < 0 || n_cand > INT_MAX / (MAX_LAM * MAX_LAM) - 1) {
         set_error("eval_batch: null pointer or size out of range");
         return MIRAGE_ERR_ARG;
     }
@@ -414,7 +419,7 @@ int eval_impl(mirage_ctx* ctx, const mirage_problem_t* probs, int n_probs, const
             dp[p].psf = base + po[4 * p + 3];
         }
         TRY(eval_impl<T>(ctx, dp.data(), n_probs, d_lens, prob_idx, n_cand, d_lambdas, n_lam, max_lam, &o2, d_warm,
-                         d_chi2, d_reg, d_iters, d_relres, d_istat, d_corner, d_kappa, d_sout, d_allx, d_status,
+                         lam_start, d_chi2, d_reg, d_iters, d_relres, d_istat, d_corner, d_kappa, d_sout, d_allx, d_status,
                          st));
         const int nl = ctx->last_launches;
         for (auto& e : sg.out) CK(cudaMemcpyAsync(e.second.first, base + e.first, e.second.second, cudaMemcpyDeviceToHost, st));
@@ -508,11 +513,23 @@ int eval_impl(mirage_ctx* ctx, const mirage_problem_t* probs, int n_probs, const
         g.smem = std::max(g.smem, item_smem);
         g.slab = std::max<long long>(g.slab, item_slab);
         const double work = (double)P.plen * P.K * P.K + 8.0 * P.nrays;
-        for (int k = 0; k < n_lam[c]; ++k) {
-            // lambda grids ascend: smaller k = smaller lambda = more CG iterations
-            const double key2 = work * (double)(n_lam[c] - k + 4);
-            g.items.push_back({-key2, c * MAX_LAM + k});
-            g.cost += key2;
+        // lambda grids ascend: smaller k = smaller lambda = more CG iterations
+        auto cost_of = [&](int k) { return work * (double)(n_lam[c] - k + 4); };
+        if (lam_start) {
+            // two chains from the predicted corner: down to the smallest
+            // lambda, and up from the next one
+            const int ks = std::min(std::max(lam_start[c], 0), n_lam[c] - 1);
+            double cd = 0.0, cu = 0.0;
+            for (int k = 0; k <= ks; ++k) cd += cost_of(k);
+            for (int k = ks + 1; k < n_lam[c]; ++k) cu += cost_of(k);
+            g.items.push_back({-cd, pack_chain(c, ks, 0)});
+            if (ks + 1 < n_lam[c]) g.items.push_back({-cu, pack_chain(c, ks + 1, n_lam[c] - 1)});
+            g.cost += cd + cu;
+        } else {
+            for (int k = 0; k < n_lam[c]; ++k) {
+                g.items.push_back({-cost_of(k), pack_chain(c, k, k)});
+                g.cost += cost_of(k);
+            }
         }
     }
     std::vector<int> all_items;
@@ -534,7 +551,7 @@ int eval_impl(mirage_ctx* ctx, const mirage_problem_t* probs, int n_probs, const
     if (o.mode == MIRAGE_MODE_PLAIN) {
         for (int c = 0; c < n_cand; ++c) {
             plain_off[c] = (int)plain_items.size();
-            for (int k = n_lam[c] - 1 + 0; k >= 0; --k) plain_items.push_back(c * MAX_LAM + k);
+            for (int k = n_lam[c] - 1 + 0; k >= 0; --k) plain_items.push_back(pack_chain(c, k, k));
         }
         plain_off[n_cand] = (int)plain_items.size();
     }
@@ -952,17 +969,17 @@ int mirage_destroy(mirage_ctx_t* ctx) {
 
 int mirage_eval_batch(mirage_ctx_t* ctx, const mirage_problem_t* probs, int n_probs, const double* lens,
                       const int* prob_idx, int n_cand, const double* lambdas, const int* n_lam, int max_lam,
-                      const mirage_opts_t* opts, const void* warm_x, double* chi2, double* reg, int* iters,
-                      double* relres, int* item_status, int* corner, double* kappa, void* s_out, void* all_x,
-                      int* status, void* stream) {
+                      const mirage_opts_t* opts, const void* warm_x, const int* lam_start, double* chi2,
+                      double* reg, int* iters, double* relres, int* item_status, int* corner, double* kappa,
+                      void* s_out, void* all_x, int* status, void* stream) {
     if (!ctx || !opts) return MIRAGE_ERR_ARG;
     if (cudaSetDevice(ctx->device) != cudaSuccess) return MIRAGE_ERR_CUDA;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     if (ctx->precision == MIRAGE_FP32)
         return eval_impl<float>(ctx, probs, n_probs, lens, prob_idx, n_cand, lambdas, n_lam, max_lam, opts, warm_x,
-                                chi2, reg, iters, relres, item_status, corner, kappa, s_out, all_x, status, st);
+                                lam_start, chi2, reg, iters, relres, item_status, corner, kappa, s_out, all_x, status, st);
     return eval_impl<double>(ctx, probs, n_probs, lens, prob_idx, n_cand, lambdas, n_lam, max_lam, opts, warm_x,
-                             chi2, reg, iters, relres, item_status, corner, kappa, s_out, all_x, status, st);
+                             lam_start, chi2, reg, iters, relres, item_status, corner, kappa, s_out, all_x, status, st);
 }
 
 int mirage_lcurve(const double* chi2, const double* reg, const int* n_lam, int n_cand, int max_lam, int* corner,

@@ -194,6 +194,9 @@ struct FastItem {
     int xl;                 // xoff / 4
     float inv_mfr;          // 1 / mfr
     float zero;             // 0: read in place of absent neighbours and cells
+    // position in the current chain of lambdas (see ChainPos), kept here
+    // rather than in registers; advanced by thread 0 between items
+    int ch_c, ch_k, ch_last, ch_step, ch_warm, ch_prev_ok, ch_valid;
 };
 static_assert(sizeof(FastItem) <= 128, "fast-kernel item constants must fit the control slot");
 
@@ -208,7 +211,6 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_cgls_fast(const __grid_constant
     const CglsArgs<float>& A = FA.A;
     extern __shared__ __align__(16) unsigned char smem[];
     const int tid = threadIdx.x;
-    int* slot = reinterpret_cast<int*>(smem);
     double* red = reinterpret_cast<double*>(smem + 16);
     FastItem* fi = reinterpret_cast<FastItem*>(smem + 16 + 2 * 33 * sizeof(double));
     unsigned long long* phs = reinterpret_cast<unsigned long long*>(smem + 16 + 2 * 33 * sizeof(double) + 128);
@@ -233,14 +235,34 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_cgls_fast(const __grid_constant
         }                                          \
     } while (0)
 
+    if (tid == 0) fi->ch_last = -1;
     while (true) {
         __syncthreads();
-        if (tid == 0) slot[0] = atomicAdd(A.counter, 1);
+        if (tid == 0) {
+            ChainPos ch;
+            ch.c = fi->ch_c;
+            ch.k = fi->ch_k;
+            ch.k_last = fi->ch_last;
+            ch.step = fi->ch_step;
+            ch.prev_ok = fi->ch_prev_ok != 0;
+            fi->ch_valid = 1;
+            if (!ch.next()) {
+                const int it_idx = atomicAdd(A.counter, 1);
+                if (it_idx < A.n_items)
+                    ch.start(A.items[it_idx]);
+                else
+                    fi->ch_valid = 0;
+            }
+            fi->ch_c = ch.c;
+            fi->ch_k = ch.k;
+            fi->ch_last = ch.k_last;
+            fi->ch_step = ch.step;
+            fi->ch_warm = ch.warm;
+            fi->ch_prev_ok = ch.prev_ok;
+        }
         __syncthreads();
-        const int it_idx = slot[0];
-        if (it_idx >= A.n_items) break;
-        const int packed = A.items[it_idx];
-        const int c = packed / MAX_LAM, k = packed - c * MAX_LAM;
+        if (!fi->ch_valid) break;
+        const int c = fi->ch_c, k = fi->ch_k;
         const Prob<T>& P = A.probs[A.cand_prob[c]];
         const CandScratch<T>& cs = A.cs;
         const int nent = cs.nent[c];
@@ -432,6 +454,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_cgls_fast(const __grid_constant
                 if (A.relres) A.relres[ok] = 0.0;
                 if (A.istat) A.istat[ok] = cstat;
             }
+            if (tid == 0) fi->ch_prev_ok = 0;
             continue;
         }
 
@@ -515,7 +538,9 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_cgls_fast(const __grid_constant
             __syncthreads();
         }
 
-        if (A.warm_x) {
+        if (fi->ch_warm && fi->ch_prev_ok) {
+            // w.x64 still holds the previous lambda's solution of this chain
+        } else if (A.warm_x) {
             const T* x0 = A.warm_x + ok * A.max_ns;
             for (int i = tid; i < g.ns; i += bs) w.x64[i] = (double)x0[i];
         } else {
@@ -847,6 +872,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_cgls_fast(const __grid_constant
             if (A.relres) A.relres[ok] = rel64;
             if (A.istat) A.istat[ok] = status | cstat;
         }
+        if (tid == 0) fi->ch_prev_ok = !(status & ST_BREAK);
     }
     if (timed)
         for (int i = 0; i < FAST_NPH; ++i) atomicAdd(A.phase_clk + i, phs[i]);

@@ -74,7 +74,7 @@ struct CglsArgs {
     const int* cand_prob;   // [n_cand]
     const double* lens;     // [n_cand][7]
     const double* lambdas;  // [n_cand][max_lam]
-    const int* items;       // [n_items] packed c * MAX_LAM + k
+    const int* items;       // [n_items] packed chains (c * MAX_LAM + k_first) * MAX_LAM + k_last
     int n_items;
     int* counter;           // queue head
     double tol;
@@ -959,6 +959,33 @@ __host__ __device__ inline size_t slab_bytes(const Prob<T>& P, int place) {
     return align_up<T>(o, 256);
 }
 
+// A work item of the CGLS kernels is a chain of one candidate's lambdas,
+// solved in order by one CTA: packed = (c * MAX_LAM + k_first) * MAX_LAM +
+// k_last (a single lambda has k_first == k_last).  After the first lambda of
+// a chain, each solve starts from the previous lambda's solution, which is
+// still in the CTA's FP64 accumulator (unless that solve broke down).  Every
+// thread holds the same state and takes the same steps.
+struct ChainPos {
+    int c = 0, k = 0, k_last = -1, step = 1;
+    bool warm = false;     // the current lambda continues a chain
+    bool prev_ok = false;  // the previous lambda's solution is usable
+    __device__ bool next() {
+        if (k_last < 0 || k == k_last) return false;
+        k += step;
+        warm = true;
+        return true;
+    }
+    __device__ void start(int packed) {
+        c = packed / (MAX_LAM * MAX_LAM);
+        const int r = packed - c * (MAX_LAM * MAX_LAM);
+        k = r / MAX_LAM;
+        k_last = r - k * MAX_LAM;
+        step = k_last >= k ? 1 : -1;
+        warm = false;
+        prev_ok = false;
+    }
+};
+
 template <typename T, int K, int PLACE>
 __global__ void __launch_bounds__(NTHREADS, 1) k_cgls(CglsArgs<T> A) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -971,15 +998,18 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_cgls(CglsArgs<T> A) {
     int* slot = reinterpret_cast<int*>(smem);
     double* red = reinterpret_cast<double*>(smem + 16);
     CgCtl* ctl = reinterpret_cast<CgCtl*>(smem + 16 + 2 * 33 * sizeof(double));
+    ChainPos ch;
 
     while (true) {
         __syncthreads();
-        if (tid == 0) slot[0] = atomicAdd(A.counter, 1);
-        __syncthreads();
-        const int it_idx = slot[0];
-        if (it_idx >= A.n_items) break;
-        const int packed = A.items[it_idx];
-        const int c = packed / MAX_LAM, k = packed - c * MAX_LAM;
+        if (!ch.next()) {
+            if (tid == 0) slot[0] = atomicAdd(A.counter, 1);
+            __syncthreads();
+            const int it_idx = slot[0];
+            if (it_idx >= A.n_items) break;
+            ch.start(A.items[it_idx]);
+        }
+        const int c = ch.c, k = ch.k;
         const Prob<T>& P = A.probs[A.cand_prob[c]];
         const CandScratch<T>& cs = A.cs;
         const int nent = cs.nent[c];
@@ -1114,6 +1144,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_cgls(CglsArgs<T> A) {
                 if (A.relres) A.relres[ok] = 0.0;
                 if (A.istat) A.istat[ok] = cstat;
             }
+            ch.prev_ok = false;
             continue;
         }
 
@@ -1157,8 +1188,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_cgls(CglsArgs<T> A) {
             }
         }
 
-        // ---- starting point
-        if (A.warm_x) {
+        // ---- starting point: the previous lambda of the chain, a given
+        // warm start, or zero (the paper's blank source)
+        if (ch.warm && ch.prev_ok) {
+            // w.x64 still holds the previous lambda's solution
+        } else if (A.warm_x) {
             const T* x0 = A.warm_x + ok * A.max_ns;
             for (int i = tid; i < g.ns; i += bs) w.x64[i] = (double)x0[i];
         } else {
@@ -1325,6 +1359,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_cgls(CglsArgs<T> A) {
             if (A.relres) A.relres[ok] = rel64;
             if (A.istat) A.istat[ok] = status | cstat;
         }
+        ch.prev_ok = !(status & ST_BREAK);
     }
 }
 

@@ -20,6 +20,12 @@ generation (offspring drawn without ranking), and back on when it
 recovers.  Warm-starting the children's CG from their parents' solutions
 is available but off by default: a parent's source is a poor start for a
 different lens and measured more CG iterations, not fewer.
+
+With ``lam_chain`` the surrogate's predicted corner lambda also orders the
+exact solves: each child's lambda grid is solved as two chains from the
+grid point nearest the prediction, every lambda after a chain's first
+starting from its neighbour's solution (fewer CG iterations, but chains are
+serial work units, which costs parallelism on small populations).
 """
 from __future__ import annotations
 
@@ -54,6 +60,7 @@ class GAConfig:
     tol: float = 1e-6
     surrogate: bool = True
     warm_start: bool = False
+    lam_chain: bool = False
     hidden: int = 256
     train_steps: int = 200
     batch: int = 256
@@ -157,9 +164,9 @@ def run_ga(ctx: Context, wl: Workload, cfg: GAConfig, log=None):
     nl = np.full(cfg.pop, n_lam, np.int32)
     sur = Surrogate(cfg.hidden, cfg.seed) if cfg.surrogate else None
 
-    def evaluate(lens, warm):
+    def evaluate(lens, warm, lam_start=None):
         out = ctx.eval_batch(probs, torch.as_tensor(lens, device="cuda"), pidx, lam_dev, nl, tol=cfg.tol,
-                             warm_x=warm, want_all_x=True)
+                             warm_x=warm, lam_start=lam_start, want_all_x=True)
         chi2 = out["chi2"].cpu().numpy()
         corner = out["corner"].cpu().numpy()
         fit = chi2[np.arange(len(lens)), corner]
@@ -184,7 +191,12 @@ def run_ga(ctx: Context, wl: Workload, cfg: GAConfig, log=None):
             keep = np.argsort(pred)[:cfg.pop]
             kids, par = kids[keep], par[keep]
         warm = X_pop[par].contiguous() if cfg.warm_start else None
-        kfit, klam, kout = evaluate(kids, warm)
+        lam_start = None
+        if cfg.lam_chain and sur is not None:
+            # grid index nearest the predicted log10 lambda* of each child
+            l10 = sur.predict(kids)[:, 1] * sur.ysd[1] + sur.ymu[1]
+            lam_start = np.abs(np.log10(lam_row)[None, :] - l10[:, None]).argmin(axis=1).astype(np.int32)
+        kfit, klam, kout = evaluate(kids, warm, lam_start)
         rm = rho = None
         was_screened = screen
         if sur is not None:

@@ -331,3 +331,46 @@ def test_warm_start_converges_faster(mods, ctx32):
     warm = ctx32.eval_batch([dp], L, [0], Lm, [8], tol=1e-6, warm_x=cold["all_x"].contiguous())
     assert warm["iters"].sum().item() < 0.2 * cold["iters"].sum().item()
     np.testing.assert_allclose(warm["chi2"].cpu().numpy(), cold["chi2"].cpu().numpy(), rtol=1e-5)
+
+
+@pytest.mark.parametrize("variant", [0, 4])
+def test_lambda_chains_match_oracle(mods, ctx32, variant):
+    # every candidate's lambdas solved as two warm-started chains from a start
+    # index (the second start is the first lambda, the third lies beyond the
+    # grid and is clamped): same gates as unchained solves; fast kernel
+    # (variant 0) and general kernel (variant 4)
+    g = synth.geom_ga64()
+    prob = make_problem(g, seed=2)
+    lams = synth.lambda_grid(16)
+    rng = np.random.default_rng(5)
+    lenses = np.vstack([synth.TRUE_LENS, synth.lens_population(rng, 2)])
+    out = ctx32.eval_batch([device_problem(prob)], _lens_t(lenses), [0] * 3, _lam_t(lams, 3), [16] * 3,
+                           tol=1e-6, want_all_x=True, lam_start=[8, 0, 40], variant=variant)
+    _fp32_checks(out, prob, lenses, lams, 1e-6)
+
+
+def test_lambda_chains_ragged_grids_host_memory(mods, ctx32):
+    # chains over ragged lambda grids, through the host-memory path: results
+    # agree with the unchained device call to the solver tolerance
+    g = synth.geom_ga64()
+    prob = make_problem(g, seed=4)
+    rng = np.random.default_rng(9)
+    lenses = synth.lens_population(rng, 4)
+    nl = [16, 9, 12, 5]
+    lam = np.zeros((4, 16))
+    for c, n in enumerate(nl):
+        lam[c, :n] = synth.lambda_grid(n)
+        lam[c, n:] = lam[c, n - 1]
+    ref = ctx32.eval_batch([device_problem(prob)], _lens_t(lenses), [0] * 4,
+                           torch.as_tensor(lam, device="cuda"), nl, tol=1e-6)
+    hout = ctx32.eval_batch([host_problem(prob)], torch.as_tensor(lenses), [0] * 4, torch.as_tensor(lam), nl,
+                            tol=1e-6, lam_start=[3, 8, 11, 2])
+    for c, n in enumerate(nl):
+        a = hout["chi2"][c, :n].numpy()
+        b = ref["chi2"][c, :n].cpu().numpy()
+        assert (hout["item_status"][c, :n].numpy() & 7 == 0).all()
+        np.testing.assert_allclose(a, b, rtol=2e-5)
+        ca, cb = int(hout["corner"][c]), int(ref["corner"][c])
+        if ca != cb:  # only a near-tie of the curvature may move the corner
+            ka = hout["kappa"][c, :n].numpy()
+            assert abs(ka[ca] - ka[cb]) <= 1e-3 * ka[ca], (c, ca, cb)

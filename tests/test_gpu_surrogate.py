@@ -61,3 +61,21 @@ def test_screen_picks_better_offspring():
     # clearly better than random picks of the same offspring
     assert np.mean(gains[1:]) > 1.1, gains
     assert np.mean(rhos[1:]) > 0.4, rhos
+
+
+def test_ga_with_lambda_chains():
+    # the GA with the surrogate's predicted corner ordering the exact solves
+    # (lambda chains): every fitness finite, the best chi^2 never rises
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1101_5803_gb300 import binding
+    from paper_1101_5803_gb300.ga import GAConfig, run_ga
+    from paper_1101_5803_gb300.problems import ga64_workload
+
+    ctx = binding.Context(0, binding.MIRAGE_FP32)
+    wl = ga64_workload(ctx, 64, 16, seed=5)
+    hist, best, bchi = run_ga(ctx, wl, GAConfig(pop=64, generations=2, lam_chain=True, train_steps=50, seed=3))
+    assert np.isfinite(bchi) and len(best) == 7
+    b = [h.best_chi2 for h in hist]
+    assert all(b[i + 1] <= b[i] for i in range(len(b) - 1)), b
+    assert all(h.cg_iters > 0 for h in hist)

@@ -283,6 +283,12 @@ def run_gpu(args):
     at_clock = None
     if clocks.get("sm_mhz"):
         at_clock = nsm * 128 * 2 * clocks["sm_mhz"] * 1e6 / 1e12
+    # the FP32 FMA pipe's sustained rate, measured by the library's microbenchmark
+    ffma_tf, ffma_fc = binding.mirage_measure_ffma(local)
+    kernel_name = {1: "k_cgls_fast<9,4,smem taps FFMA2> (two CTAs/SM)",
+                   2: "k_cgls_fast<9,4,param taps FFMA> (two CTAs/SM)",
+                   3: "k_cgls_fast<9,4,param taps FFMA2> (two CTAs/SM)",
+                   4: "k_cgls<float,9,smem> (one CTA/SM)"}.get(variant, "k_cgls_fast<9,4,*>")
 
     # DRAM bytes per launch: the per-item traffic of the ncu capture of this
     # kernel (profiles/k_cgls_fast_ga64.md) times the items of one launch
@@ -331,8 +337,10 @@ def run_gpu(args):
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_basis": f"FP32 FFMA: {nsm} SMs x 128 lanes x 2 x {smax:.0f} MHz ({src} max clock)",
                          "frac_at_measured_clock": (achieved / at_clock) if at_clock else None,
-                         "kernel": "k_cgls_fast<9,4,param-taps FFMA2> (two CTAs/SM)", "kernel_ms": phase[1],
-                         "flops_per_launch": flops},
+                         "kernel": kernel_name, "kernel_ms": phase[1], "flops_per_launch": flops,
+                         "ffma_microbench": {"tflops": ffma_tf, "flop_per_clk_per_sm_at_max_clock": ffma_fc,
+                                             "frac_of_nominal": ffma_fc / 256.0,
+                                             "kernel_frac_of_measured": achieved / ffma_tf}},
             "cpu_baseline": cpu,
             "plain": {"value": plain, "unit": UNIT, "sample": n_plain, "speedup_batched_vs_plain": value / plain,
                       "chi2_identical": same},

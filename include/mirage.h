@@ -277,6 +277,14 @@ const char* mirage_noalloc_last_error(void);
 /* Size in bytes of the fixed scratch array of mirage_forward_noalloc. */
 size_t mirage_noalloc_capacity(void);
 
+/* FP32 FMA-pipe microbenchmark on `device`: sixteen independent FMA chains
+ * per thread on every SM, timed with CUDA events after a warm-up launch.
+ * Writes the sustained FP32 TFLOP/s and the flops per clock per SM at the
+ * device's maximum SM clock (nominal 256 = 128 lanes x 2).  The binding
+ * roof of the CGLS kernels, measured rather than derived.  Synchronous;
+ * allocates and frees a small output buffer. */
+int mirage_measure_ffma(int device, double* tflops, double* flop_per_clk_sm);
+
 #ifdef __cplusplus
 }
 #endif

@@ -51,9 +51,9 @@ def _save(d):
     os.replace(tmp, p)
 
 
-def tune(ctx, probs, lens, prob_idx, lambdas, n_lam, *, tol=1e-6, n_probe=64, retune=False) -> int:
-    """Fastest variant for this shape class, timed on the first n_probe
-    candidates at two lambdas from the middle of their grids (items of
+def tune(ctx, probs, lens, prob_idx, lambdas, n_lam, *, tol=1e-6, n_probe=64, reps=3, retune=False) -> int:
+    """Fastest variant for this shape class (best of ``reps`` timed runs), timed
+    on the first n_probe candidates at two lambdas from the middle of their grids (items of
     typical length: the largest lambdas converge in a few dozen iterations
     and would time mostly the fixed per-item work)."""
     key = shape_key(ctx, probs)
@@ -71,12 +71,15 @@ def tune(ctx, probs, lens, prob_idx, lambdas, n_lam, *, tol=1e-6, n_probe=64, re
             continue
         kw = dict(tol=tol, variant=v, want_s=False, want_kappa=False)
         ctx.eval_batch(probs, lens[:n].contiguous(), prob_idx[:n], lam, nl, **kw)  # warm-up
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        ctx.eval_batch(probs, lens[:n].contiguous(), prob_idx[:n], lam, nl, **kw)
-        e1.record()
-        torch.cuda.synchronize()
-        times[v] = e0.elapsed_time(e1)
+        best = float("inf")
+        for _ in range(reps):  # the fastest of a few runs: variants can be within a few percent
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            ctx.eval_batch(probs, lens[:n].contiguous(), prob_idx[:n], lam, nl, **kw)
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        times[v] = best
     best = min(times, key=times.get)
     db[key] = {"variant": int(best), "ms": {str(k): round(t, 4) for k, t in times.items()}}
     _save(db)

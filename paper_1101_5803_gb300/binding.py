@@ -78,6 +78,8 @@ def load_library():
     lib.mirage_lcurve.restype = ip
     lib.mirage_forward.argtypes = [vp, ctypes.POINTER(mirage_problem_t), vp, vp, i, vp, vp, vp, vp]
     lib.mirage_forward.restype = ip
+    lib.mirage_measure_ffma.argtypes = [i, vp, vp]
+    lib.mirage_measure_ffma.restype = ip
     lib.mirage_last_launch_count.argtypes = [vp]
     lib.mirage_last_launch_count.restype = ip
     lib.mirage_last_phase_clocks.argtypes = [vp, vp]
@@ -228,6 +230,13 @@ def mirage_last_phase_ms(ctx):
     buf = (ctypes.c_double * 3)()
     _check(load_library().mirage_last_phase_ms(ctx, buf), "mirage_last_phase_ms")
     return list(buf)
+
+
+def mirage_measure_ffma(device=0):
+    """(TFLOP/s, flops per clock per SM) the FP32 FMA pipe sustains (mirage.h)."""
+    tf, fc = ctypes.c_double(), ctypes.c_double()
+    _check(load_library().mirage_measure_ffma(int(device), ctypes.byref(tf), ctypes.byref(fc)), "mirage_measure_ffma")
+    return tf.value, fc.value
 
 
 def mirage_last_phase_clocks(ctx):

@@ -188,7 +188,6 @@ __device__ __forceinline__ float hrow_fast(const float* __restrict__ v, int i, u
 // Per-item constants of the fast kernel, written by thread 0 into shared
 // memory (read back where needed instead of being held in registers).
 struct FastItem {
-    float psf2;             // sum of squared PSF taps
     int R;                  // rays per thread in the L^T walk (odd)
     int nfz, top, mfr, W4;  // P2 frame float4s overlapped by the L^T planes
     int xl;                 // xoff / 4
@@ -346,12 +345,8 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_cgls_fast(const __grid_constant
             w.Pa[i] = 0.0;
             w.Pb[i] = 0.0;
         }
-        if (tid < 32) {
-            float a = 0.f;
-            for (int i = tid; i < K * K; i += 32) a = fmaf(P.psf[i], P.psf[i], a);
-            for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+        {
             if (tid == 0) {
-                fi->psf2 = a;
                 // L^T walk: R consecutive rays per thread, R odd so that the
                 // lanes' reads at stride R fall on distinct banks
                 fi->R = ((nent + bs - 1) / bs) | 1;
@@ -488,32 +483,52 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_cgls_fast(const __grid_constant
 
         // ---- Jacobi preconditioner of the inner solves: an approximation of
         // diag(A~^T A~) = diag(L^T B^T W B L) + lam diag(H^T H), taking
-        // diag(L^T B^T W B L)_i ~ sum_rays weight_i^2 w_pixel * sum(psf^2)
-        // (exact for a delta PSF; cross terms between rays are dropped).
-        // Any positive diagonal leaves the solution unchanged; this one cuts
-        // the CGLS iterations two- to threefold.
+        // diag(L^T B^T W B L)_i ~ sum_rays weight_i^2 omega(pixel), where
+        // omega_p = diag(B^T W B)_p = sum_k psf_k^2 W_{p+k-c} (exact for a delta
+        // PSF; the off-diagonal terms of B^T W B and the cross terms between
+        // rays are dropped).  Any positive diagonal leaves the solution
+        // unchanged; this one cuts the CGLS iterations two- to threefold.
         float minv[NSP];
         {
+            // W of the owned tile into P1 (its frame is zero)
+            if (own) {
+#pragma unroll
+                for (int r = 0; r < TILE; ++r) {
+                    V4<float> o;
+#pragma unroll
+                    for (int cc = 0; cc < 4; ++cc) o.v[cc] = sw[r * 4 + cc] * sw[r * 4 + cc];
+                    st4(P1 + pp0 + r * g.Wp, o);
+                }
+            }
+            __syncthreads();
             float4* cellp = reinterpret_cast<float4*>(P2);
+            const float2* ptap = taps2 + K * K;  // the PSF itself (B^T taps)
             for (int cell = tid; cell < g.ncells; cell += bs) {
                 const int k0 = cst16[cell], k1 = cst16[cell + 1];
                 float c00 = 0.f, c10 = 0.f, c01 = 0.f, c11 = 0.f;
                 for (int e = k0; e < k1; ++e) {
                     const unsigned id = eidx[e];
                     const float2 uv = euv[e];
-                    const float sw1 = w.swp[id & 0xffffu];
-                    const float W2 = sw1 * sw1;
+                    const float* wrow = P1 + (int)(id & 0xffffu) - g.hk * g.Wp - g.hk;
+                    float om = 0.f;
+#pragma unroll 1
+                    for (int a = 0; a < K; ++a) {
+#pragma unroll
+                        for (int b = 0; b < K; ++b) {
+                            const float f = ptap[a * K + b].x;
+                            om = fmaf(f * f, wrow[a * g.Wp + b], om);
+                        }
+                    }
                     const float u1 = uv.x * uv.x, u0 = (1.f - uv.x) * (1.f - uv.x);
                     const float v1 = uv.y * uv.y, v0 = (1.f - uv.y) * (1.f - uv.y);
-                    c00 = fmaf(u0 * v0, W2, c00);
-                    c10 = fmaf(u1 * v0, W2, c10);
-                    c01 = fmaf(u0 * v1, W2, c01);
-                    c11 = fmaf(u1 * v1, W2, c11);
+                    c00 = fmaf(u0 * v0, om, c00);
+                    c10 = fmaf(u1 * v0, om, c10);
+                    c01 = fmaf(u0 * v1, om, c01);
+                    c11 = fmaf(u1 * v1, om, c11);
                 }
                 cellp[cell] = make_float4(c00, c10, c01, c11);
             }
             __syncthreads();
-            const float psf2 = fi->psf2;
             const float* cp = reinterpret_cast<const float*>(cellp);
 #pragma unroll
             for (int kk = 0; kk < NSP; ++kk) {
@@ -530,11 +545,15 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_cgls_fast(const __grid_constant
                     float h = 1.f;
                     if (g.reg == 2)
                         h = 16.f + (float)((ia > 0) + (ia < g.sx - 1) + (ib > 0) + (ib < g.sy - 1));
-                    minv[kk] = 1.f / (dsum * psf2 + (float)lam * h);
+                    minv[kk] = 1.f / (dsum + (float)lam * h);
                 }
             }
             __syncthreads();
             for (int cell = tid; cell < g.ncells; cell += bs) cellp[cell] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (own) {
+#pragma unroll
+                for (int r = 0; r < TILE; ++r) st4(P1 + pp0 + r * g.Wp, V4<float>{{0.f, 0.f, 0.f, 0.f}});
+            }
             __syncthreads();
         }
 

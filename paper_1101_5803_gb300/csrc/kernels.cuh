@@ -740,13 +740,16 @@ __device__ __forceinline__ V apply_HT_at(const Geo<T>& g, const V* __restrict__ 
     return acc;
 }
 
-// Approximate diagonal of the inner normal operator at source pixel (ia, ib):
-//   sum over the rays of its cells of (bilinear weight / N_p)^2 w_pixel,
-// the diagonal of L^T W L (times sum(psf^2) it approximates that of
-// L^T B^T W B L; exact for a delta PSF).
+// Approximate diagonal of the inner normal operator L^T B^T W B L at source
+// pixel (ia, ib): sum over the rays of its cells of (bilinear weight / N_p)^2
+// times omega at the ray's pixel, omega_p = diag(B^T W B)_p = sum_k psf_k^2
+// W_{p+k-c} (the weight the PSF spreads pixel p's light over).  It drops the
+// off-diagonal terms of B^T W B and the cross terms between rays; it is exact
+// for a delta PSF, and near a mask edge it keeps the light the PSF carries
+// into unmasked pixels.
 template <typename T>
 __device__ __forceinline__ T lwl_diag_at(const Geo<T>& g, const Entry<T>* __restrict__ Ent, const int* __restrict__ cst,
-                                         const T* __restrict__ swp, int ia, int ib) {
+                                         const double* __restrict__ omega, int ia, int ib) {
     T acc = 0;
 #pragma unroll
     for (int dy = 0; dy < 2; ++dy) {
@@ -762,9 +765,8 @@ __device__ __forceinline__ T lwl_diag_at(const Geo<T>& g, const Entry<T>* __rest
                 const Entry<T> en = Ent[k];
                 const T wu = dx ? en.u : (T)1 - en.u;
                 const T wv = dy ? en.v : (T)1 - en.v;
-                const T sw = swp[en.ppos];
                 const T wt = wu * wv * g.invNp;
-                acc += wt * wt * sw * sw;
+                acc += wt * wt * (T)omega[en.ppos];
             }
         }
     }
@@ -1177,15 +1179,33 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_cgls(CglsArgs<T> A) {
         const double rhsn = sqrt(block_sum(rs, red, which));
         which ^= 1;
 
-        // ---- Jacobi preconditioner of the inner solves (see lwl_diag_at)
-        {
-            T psf2 = 0;
-            for (int i = 0; i < g.K * g.K; ++i) psf2 = fma(P.psf[i], P.psf[i], psf2);
-            for (int i = tid; i < g.ns; i += bs) {
-                const int ib = i / g.sx, ia = i - ib * g.sx;
-                w.minv[i] = (T)1 / (lwl_diag_at<T>(g, w.E, w.cst, w.swp, ia, ib) * psf2 +
-                                    (T)lam * hth_diag_at<T>(g, ia, ib));
+        // ---- Jacobi preconditioner of the inner solves (see lwl_diag_at):
+        // omega at every image pixel into Pa (free until the first residual;
+        // sqrt(W) is zero in the padding frame), in FP32 like the inner solves
+        for (int t = tid; t < g.ntiles * (TILE * TILE); t += bs) {
+            const int tile = t >> 4, q = t & 15;
+            const int ty = tile / g.tiles_x, tx = tile - ty * g.tiles_x;
+            const int pp = (ty * TILE + (q >> 2) + g.hk) * g.Wp + tx * TILE + (q & 3) + g.xoff;
+            float om = 0.f;
+            for (int a = 0; a < g.K; ++a) {
+                const T* srow = w.swp + pp + (a - g.hk) * g.Wp - g.hk;
+                for (int b = 0; b < g.K; ++b) {
+                    const float f = (float)P.psf[a * g.K + b], sv = (float)srow[b];
+                    om = fmaf(f * f, sv * sv, om);
+                }
             }
+            w.Pa[pp] = (double)om;
+        }
+        __syncthreads();
+        for (int i = tid; i < g.ns; i += bs) {
+            const int ib = i / g.sx, ia = i - ib * g.sx;
+            w.minv[i] = (T)1 / (lwl_diag_at<T>(g, w.E, w.cst, w.Pa, ia, ib) + (T)lam * hth_diag_at<T>(g, ia, ib));
+        }
+        __syncthreads();
+        for (int t = tid; t < g.ntiles * (TILE * TILE); t += bs) {  // Pa back to zero
+            const int tile = t >> 4, q = t & 15;
+            const int ty = tile / g.tiles_x, tx = tile - ty * g.tiles_x;
+            w.Pa[(ty * TILE + (q >> 2) + g.hk) * g.Wp + tx * TILE + (q & 3) + g.xoff] = 0.0;
         }
 
         // ---- starting point: the previous lambda of the chain, a given

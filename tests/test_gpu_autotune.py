@@ -31,3 +31,14 @@ def test_tune_caches_and_variants_agree(tmp_path, monkeypatch):
     c1, c4 = outs[1]["chi2"].cpu().numpy(), outs[4]["chi2"].cpu().numpy()
     assert np.abs(c4 / c1 - 1).max() < 1e-4
     ctx.close()
+
+
+def test_ffma_microbenchmark():
+    # the FP32 FMA pipe sustains a large share of its nominal 256 flops per
+    # clock per SM (the binding roof of the CGLS kernels), and never more
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1101_5803_gb300 import binding
+    tf, fc = binding.mirage_measure_ffma(0)
+    assert 0.3 * 256 < fc < 1.05 * 256, fc
+    assert tf > 0

@@ -299,6 +299,25 @@ def run_gpu(args):
             if line.startswith("traffic_bytes_per_item:"):
                 traffic = float(line.split(":")[1]) * float(iters.size)
 
+    # the paper's own fitness: 40 CGLS iterations per candidate, L-curve over
+    # the iterations, Monte Carlo degrees of freedom (FP64 arithmetic)
+    bh = torch.as_tensor(np.random.default_rng(5).standard_normal((1, wl.geom.nx * wl.geom.ny)),
+                         dtype=ctx.real, device="cuda")
+    iter_res = {"n_iter": 40}
+    for key, b in (("evals_per_s", None), ("evals_per_s_with_dof", bh)):
+        ctx.eval_iter(probs, wl.lens, wl.prob_idx, 40, bhat=b)  # warm-up
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        io = ctx.eval_iter(probs, wl.lens, wl.prob_idx, 40, bhat=b)
+        e1.record()
+        torch.cuda.synchronize()
+        iter_res[key] = N_CAND / (e0.elapsed_time(e1) / 1e3)
+    cn = io["corner"].cpu().numpy()
+    chi_c = io["chi2"].cpu().numpy()[np.arange(N_CAND), cn]
+    dof_c = io["dof"].cpu().numpy()[np.arange(N_CAND), cn]
+    iter_res.update({"corner_iteration_median": float(np.median(cn)),
+                     "reduced_chi2_at_corner_median": float(np.median(chi_c / dof_c))})
+
     # GA generations on the same problem: surrogate screen vs none
     from paper_1101_5803_gb300.ga import GAConfig, run_ga
     n_gen = int(os.environ.get("MIRAGE_GA_GENERATIONS", "4"))
@@ -351,7 +370,8 @@ def run_gpu(args):
                    "items_converged_frac": float(((item_status & 7) == 0).mean()),
                    "status_bits_any": int(np.bitwise_or.reduce(status))},
             "phase_ms": {"raytrace": phase[0], "cgls": phase[1], "finalize": phase[2]},
-            "ga_surrogate": ga_res}
+            "ga_surrogate": ga_res,
+            "iter_lcurve": iter_res}
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()

@@ -166,6 +166,37 @@ int mirage_eval_batch(mirage_ctx_t* ctx, const mirage_problem_t* probs, int n_pr
                       int* corner, double* kappa, void* s_out, void* all_x, int* status,
                       void* stream);
 
+/* The paper's own inner loop (Sections 2.4-2.6): for each candidate, CGLS on
+ * the weighted least-squares problem min ||sqrt(W)(B L s - d)|| from a blank
+ * source (no explicit regulariser) for exactly n_iter iterations; after
+ * iteration k (k = 0..n_iter, k = 0 being s = 0) it records the image chi^2
+ * of s_k and the zeroth-order regularisation measure sum s_k^2, and picks the
+ * corner of the L-curve (log10 sum s_k^2, log10 chi^2_k) over k = 1..n_iter
+ * by the rule of mirage_lcurve.  With bhat it also runs the twin CGLS of
+ * Section 2.5 on m * bhat (m = mask and mapped) with the same step
+ * coefficients and records dof_k = bhat^T (bhat - A xhat_k), the Monte Carlo
+ * estimate of the residual degrees of freedom (reduced chi^2 = chi^2_k /
+ * dof_k).  Device memory; asynchronous on `stream` after a short host sync of
+ * the uploads.
+ *  probs, n_probs, lens, prob_idx (HOST), n_cand: as for mirage_eval_batch
+ *  n_iter        1 .. MIRAGE_MAX_LAM-1 (the paper uses 40)
+ *  bhat          nullable [n_probs*bhat_stride] real: one standard-normal
+ *                image per problem, row-major (y slow), bhat_stride >= nx*ny
+ *  chi2, reg     [n_cand*(n_iter+1)] double
+ *  dof           nullable [n_cand*(n_iter+1)] double (needs bhat)
+ *  corner        [n_cand] int: the corner iteration (1..n_iter)
+ *  kappa         nullable [n_cand*(n_iter+1)] double: curvature at each k
+ *  s_out         nullable [n_cand*max_ns] real: s at the corner iteration
+ *  status        [n_cand] int: MIRAGE_ST_* bits (BREAKDOWN when a step
+ *                coefficient is not finite; LCURVE_FLAT)
+ * The iteration is unpreconditioned by design: the iteration count is the
+ * regulariser, and a preconditioner would change which solution it selects. */
+int mirage_eval_iter(mirage_ctx_t* ctx, const mirage_problem_t* probs, int n_probs,
+                     const double* lens, const int* prob_idx, int n_cand, int n_iter,
+                     const void* bhat, long long bhat_stride,
+                     double* chi2, double* reg, double* dof, int* corner, double* kappa,
+                     void* s_out, int* status, void* stream);
+
 /* L-curve corner (Section 2.6) for n_cand curves of n_lam[c] points each:
  * points (log10 reg, log10 chi2) in lambda order, chord-length parameter,
  * natural cubic splines, curvature |x'y'' - y'x''| / (x'^2 + y'^2)^1.5 at

@@ -78,6 +78,9 @@ def load_library():
     lib.mirage_lcurve.restype = ip
     lib.mirage_forward.argtypes = [vp, ctypes.POINTER(mirage_problem_t), vp, vp, i, vp, vp, vp, vp]
     lib.mirage_forward.restype = ip
+    lib.mirage_eval_iter.argtypes = [vp, ctypes.POINTER(mirage_problem_t), i, vp, vp, i, i, vp, ctypes.c_longlong,
+                                     vp, vp, vp, vp, vp, vp, vp, vp]
+    lib.mirage_eval_iter.restype = ip
     lib.mirage_measure_ffma.argtypes = [i, vp, vp]
     lib.mirage_measure_ffma.restype = ip
     lib.mirage_last_launch_count.argtypes = [vp]
@@ -232,6 +235,33 @@ def mirage_last_phase_ms(ctx):
     return list(buf)
 
 
+def mirage_eval_iter(ctx, probs, lens, prob_idx, n_iter=40, *, bhat=None, stream=None, real=torch.float32):
+    """Fixed-iteration CGLS with the L-curve over iterations and, given ``bhat``
+    (device tensor [n_probs, >= nx*ny] of the context's real type), the Monte
+    Carlo degrees of freedom (mirage.h).  Returns a dict of device tensors."""
+    lib = load_library()
+    n = int(lens.shape[0])
+    dev = lens.device
+    max_ns = max(int(p.geom.sx) * int(p.geom.sy) for p in probs)
+    pidx = np.ascontiguousarray(np.asarray(prob_idx, dtype=np.int32))
+    mk = lambda shape, dt: torch.empty(shape, dtype=dt, device=dev)
+    out = {"chi2": mk((n, n_iter + 1), torch.float64), "reg": mk((n, n_iter + 1), torch.float64),
+           "kappa": mk((n, n_iter + 1), torch.float64), "corner": mk((n,), torch.int32),
+           "s": mk((n, max_ns), real), "status": mk((n,), torch.int32)}
+    stride = 0
+    if bhat is not None:
+        bhat = bhat.contiguous()
+        stride = int(bhat.shape[-1])
+        out["dof"] = mk((n, n_iter + 1), torch.float64)
+    arr = (mirage_problem_t * len(probs))(*[p.c_struct() for p in probs])
+    rc = lib.mirage_eval_iter(ctx, arr, len(probs), _ptr(lens.contiguous()), pidx.ctypes.data_as(ctypes.c_void_p), n,
+                              int(n_iter), _ptr(bhat), stride, _ptr(out["chi2"]), _ptr(out["reg"]),
+                              _ptr(out.get("dof")), _ptr(out["corner"]), _ptr(out["kappa"]), _ptr(out["s"]),
+                              _ptr(out["status"]), _stream_ptr(stream))
+    _check(rc, "mirage_eval_iter")
+    return out
+
+
 def mirage_measure_ffma(device=0):
     """(TFLOP/s, flops per clock per SM) the FP32 FMA pipe sustains (mirage.h)."""
     tf, fc = ctypes.c_double(), ctypes.c_double()
@@ -380,6 +410,10 @@ class Context:
     def eval_batch(self, probs, lens, prob_idx, lambdas, n_lam, **kw):
         kw.setdefault("real", self.real)
         return mirage_eval_batch(self.handle, probs, lens, prob_idx, lambdas, n_lam, **kw)
+
+    def eval_iter(self, probs, lens, prob_idx, n_iter=40, **kw):
+        kw.setdefault("real", self.real)
+        return mirage_eval_iter(self.handle, probs, lens, prob_idx, n_iter, **kw)
 
     def forward(self, prob, lens, S, **kw):
         return mirage_forward(self.handle, prob, lens, S, **kw)

@@ -14,6 +14,7 @@
 
 #include "../../include/mirage.h"
 #include "fast.cuh"
+#include "iterlc.cuh"
 #include "kernels.cuh"
 #include "table.h"
 
@@ -55,6 +56,7 @@ const KernelTable& table() {
         fill_f32_gen(k);
         fill_f64(k);
         fill_fast(k);
+        fill_iter(k);
         return k;
     }();
     return t;
@@ -918,6 +920,108 @@ int forward_impl(mirage_ctx* ctx, const mirage_problem_t* prob, const double* le
     return MIRAGE_OK;
 }
 
+// fixed-iteration CGLS with the iteration L-curve (mirage_eval_iter)
+template <typename T>
+int iter_impl(mirage_ctx* ctx, const mirage_problem_t* probs, int n_probs, const double* lens, const int* prob_idx,
+              int n_cand, int n_iter, const void* bhat, long long bhat_stride, double* chi2, double* reg,
+              double* dof, int* corner, double* kappa, void* s_out, int* status, cudaStream_t st) {
+    constexpr int prec = prec_of<T>();
+    ctx->last_launches = 0;
+    if (n_cand == 0) return MIRAGE_OK;
+    if (!probs || n_probs < 1 || !lens || !prob_idx || !chi2 || !reg || !corner || !status || n_cand < 0 ||
+        n_iter < 1 || n_iter > MAX_LAM - 1 || (bhat && bhat_stride < 1)) {
+        set_error("eval_iter: null pointer or size out of range (1 <= n_iter <= %d)", MAX_LAM - 1);
+        return MIRAGE_ERR_ARG;
+    }
+    std::vector<Prob<T>> hp(n_probs);
+    long long max_rays = 0, max_cells = 0, max_plen = 0, max_ns = 0;
+    size_t smem = 0, slab = 0;
+    int k_all = -1;
+    for (int p = 0; p < n_probs; ++p) {
+        if (check_geom(probs[p].geom) != MIRAGE_OK || !probs[p].d || !probs[p].sigma || !probs[p].mask ||
+            !probs[p].psf) {
+            set_error("eval_iter: bad problem %d", p);
+            return MIRAGE_ERR_ARG;
+        }
+        hp[p] = make_prob<T>(probs[p], probs[p].d, probs[p].sigma, probs[p].mask, probs[p].psf);
+        if (bhat && (long long)probs[p].geom.nx * probs[p].geom.ny > bhat_stride) {
+            set_error("eval_iter: bhat_stride below the pixel count of problem %d", p);
+            return MIRAGE_ERR_ARG;
+        }
+        max_rays = std::max<long long>(max_rays, hp[p].nrays);
+        max_cells = std::max<long long>(max_cells, hp[p].ncells);
+        max_plen = std::max<long long>(max_plen, hp[p].plen);
+        max_ns = std::max<long long>(max_ns, hp[p].ns);
+        smem = std::max(smem, iter_smem_bytes<T>(hp[p].K, hp[p].kp));
+        slab = std::max(slab, iter_slab_bytes<T>(hp[p], n_iter));
+        k_all = (k_all == -1 || k_all == hp[p].K) ? hp[p].K : 0;
+    }
+    for (int c = 0; c < n_cand; ++c)
+        if (prob_idx[c] < 0 || prob_idx[c] >= n_probs) {
+            set_error("eval_iter: bad prob_idx of candidate %d", c);
+            return MIRAGE_ERR_ARG;
+        }
+    if (max_cells * 4 > ctx->max_smem - 2048) {
+        set_error("source grid too large for the ray-trace kernel");
+        return MIRAGE_ERR_UNSUPPORTED;
+    }
+    const long long sE = max_rays, sInv = max_rays, sCst = (max_cells + 1 + 3) / 4 * 4, sPad = (max_plen + 3) / 4 * 4;
+    TRY(ctx->E.ensure(sizeof(Entry<T>) * n_cand * sE));
+    if (sizeof(T) == 4) TRY(ctx->E64.ensure(sizeof(Entry<double>) * n_cand * sE));
+    TRY(ctx->Etmp.ensure(sizeof(Entry<double>) * n_cand * sE));
+    TRY(ctx->inv.ensure(sizeof(int) * n_cand * sInv));
+    TRY(ctx->cst.ensure(sizeof(int) * n_cand * sCst));
+    TRY(ctx->swp.ensure(sizeof(T) * n_cand * sPad));
+    TRY(ctx->dpad.ensure(sizeof(T) * n_cand * sPad));
+    TRY(ctx->nent.ensure(sizeof(int) * n_cand));
+    TRY(ctx->cstat.ensure(sizeof(int) * n_cand));
+    TRY(ctx->probs.ensure(sizeof(Prob<T>) * n_probs));
+    TRY(ctx->cand_prob.ensure(sizeof(int) * n_cand));
+    TRY(ctx->counters.ensure(sizeof(int)));
+    const int grid = std::min(n_cand, 2 * ctx->sm_count);
+    TRY(ctx->slab.ensure(slab * grid));
+    CK(cudaMemcpyAsync(ctx->probs.p, hp.data(), sizeof(Prob<T>) * n_probs, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(ctx->cand_prob.p, prob_idx, sizeof(int) * n_cand, cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(ctx->counters.p, 0, sizeof(int), st));
+    CK(cudaStreamSynchronize(st));  // the host arrays of the uploads may go away after the call
+    CandScratch<T> cs;
+    fill_scratch<T>(cs, ctx, false, sE, sInv, sCst, sPad);
+    const Prob<T>* dprobs = ctx->probs.as<Prob<T>>();
+    const int* dcand = ctx->cand_prob.as<int>();
+    const KernelTable& tb = table();
+    TRY(set_smem(ctx, tb.raytrace[prec], (size_t)max_cells * 4));
+    {
+        int cand0 = 0, nc = n_cand;
+        void* args[] = {(void*)&dprobs, (void*)&dcand, (void*)&lens, &cand0, &nc, &cs};
+        TRY(launch(ctx, tb.raytrace[prec], dim3(n_cand), dim3(NTHREADS), args, (size_t)max_cells * 4, st));
+    }
+    const void* fn = (k_all > 0 && tb.iter[prec][k_all]) ? tb.iter[prec][k_all] : tb.iter[prec][0];
+    TRY(set_smem(ctx, fn, smem));
+    IterArgs<T> A;
+    std::memset(&A, 0, sizeof(A));
+    A.probs = dprobs;
+    A.cand_prob = dcand;
+    A.cs = cs;
+    A.n_cand = n_cand;
+    A.n_iter = n_iter;
+    A.max_ns = (int)max_ns;
+    A.bhat = reinterpret_cast<const T*>(bhat);
+    A.bhat_stride = bhat_stride;
+    A.counter = ctx->counters.as<int>();
+    A.slab = ctx->slab.p;
+    A.slab_stride = (long long)slab;
+    A.chi2 = chi2;
+    A.reg = reg;
+    A.dof = dof;
+    A.kappa = kappa;
+    A.corner = corner;
+    A.s_out = reinterpret_cast<T*>(s_out);
+    A.status = status;
+    void* a2[] = {&A};
+    TRY(launch(ctx, fn, dim3(grid), dim3(NTHREADS), a2, smem, st));
+    return MIRAGE_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1002,6 +1106,20 @@ int mirage_forward(mirage_ctx_t* ctx, const mirage_problem_t* prob, const double
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     if (ctx->precision == MIRAGE_FP32) return forward_impl<float>(ctx, prob, lens, s, n_src, model, chi2, status, st);
     return forward_impl<double>(ctx, prob, lens, s, n_src, model, chi2, status, st);
+}
+
+int mirage_eval_iter(mirage_ctx_t* ctx, const mirage_problem_t* probs, int n_probs, const double* lens,
+                     const int* prob_idx, int n_cand, int n_iter, const void* bhat, long long bhat_stride,
+                     double* chi2, double* reg, double* dof, int* corner, double* kappa, void* s_out, int* status,
+                     void* stream) {
+    if (!ctx) return MIRAGE_ERR_ARG;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return MIRAGE_ERR_CUDA;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (ctx->precision == MIRAGE_FP32)
+        return iter_impl<float>(ctx, probs, n_probs, lens, prob_idx, n_cand, n_iter, bhat, bhat_stride, chi2, reg,
+                                dof, corner, kappa, s_out, status, st);
+    return iter_impl<double>(ctx, probs, n_probs, lens, prob_idx, n_cand, n_iter, bhat, bhat_stride, chi2, reg, dof,
+                             corner, kappa, s_out, status, st);
 }
 
 int mirage_last_launch_count(const mirage_ctx_t* ctx) { return ctx ? ctx->last_launches : 0; }

@@ -16,6 +16,8 @@ struct KernelTable {
     // fast[K][v][mode]: two-CTA-per-SM FP32 kernel, v = 0 for ns <= 1024,
     // 1 for ns <= 2304; mode = tap source (0 shared, 1 params FFMA, 2 params FFMA2)
     const void* fast[MAX_K][2][3];
+    // iter[prec][K]: fixed-iteration CGLS with the iteration L-curve
+    const void* iter[2][MAX_K];
 };
 
 void fill_f32_k5(KernelTable& t);
@@ -27,5 +29,6 @@ void fill_f32_k21(KernelTable& t);
 void fill_f32_gen(KernelTable& t);
 void fill_f64(KernelTable& t);
 void fill_fast(KernelTable& t);
+void fill_iter(KernelTable& t);
 
 }  // namespace mirage

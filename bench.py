@@ -318,6 +318,35 @@ def run_gpu(args):
     iter_res.update({"corner_iteration_median": float(np.median(cn)),
                      "reduced_chi2_at_corner_median": float(np.median(chi_c / dof_c))})
 
+    # forward batch (B L s and chi^2 of 1024 sources at one lens): 256x256
+    # image at 0.02"/px, 128x128 source over +-1.2", 21x21 PSF; sources
+    # |N(0,1)| times an analytic template
+    import synth
+    from paper_1101_5803_gb300.problems import large_workload
+    lw = large_workload(ctx, n_cand=1, n_lam=1, seed=3)
+    lg = lw.geom
+    hx = (lg.sxmax - lg.sxmin) / lg.sx
+    cxs = lg.sxmin + (np.arange(lg.sx) + 0.5) * hx
+    tmpl = synth.eval_source(synth.drawn_source(np.random.default_rng(9)), *np.meshgrid(cxs, cxs)).ravel()
+    n_src = 1024
+    S = torch.as_tensor(np.abs(np.random.default_rng(10).standard_normal((n_src, tmpl.size))) * tmpl[None, :],
+                        dtype=ctx.real, device="cuda")
+    ctx.forward(lw.problem, lw.lens[0], S, want_model=False)  # warm-up
+    fms = []
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ctx.forward(lw.problem, lw.lens[0], S, want_model=False)
+        e1.record()
+        torch.cuda.synchronize()
+        fms.append(e0.elapsed_time(e1))
+    npx = lg.nx * lg.ny
+    fwd_flops = n_src * (2.0 * lg.kpsf * lg.kpsf * npx + 11.0 * npx)
+    fwd_res = {"workload": "256x256 image, 128x128 source, 21x21 PSF, 1024 sources at one lens",
+               "ms": min(fms), "sources_per_s": n_src / (min(fms) / 1e3),
+               "tflops": fwd_flops / (min(fms) / 1e3) / 1e12}
+    del S
+
     # GA generations on the same problem: surrogate screen vs none
     from paper_1101_5803_gb300.ga import GAConfig, run_ga
     n_gen = int(os.environ.get("MIRAGE_GA_GENERATIONS", "4"))
@@ -371,7 +400,8 @@ def run_gpu(args):
                    "status_bits_any": int(np.bitwise_or.reduce(status))},
             "phase_ms": {"raytrace": phase[0], "cgls": phase[1], "finalize": phase[2]},
             "ga_surrogate": ga_res,
-            "iter_lcurve": iter_res}
+            "iter_lcurve": iter_res,
+            "forward_batch": fwd_res}
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()

@@ -14,6 +14,7 @@
 
 #include "../../include/mirage.h"
 #include "fast.cuh"
+#include "forward.cuh"
 #include "iterlc.cuh"
 #include "kernels.cuh"
 #include "table.h"
@@ -57,6 +58,7 @@ const KernelTable& table() {
         fill_f64(k);
         fill_fast(k);
         fill_iter(k);
+        fill_fwd_band(k);
         return k;
     }();
     return t;
@@ -908,6 +910,34 @@ int forward_impl(mirage_ctx* ctx, const mirage_problem_t* prob, const double* le
     int cand0 = 0, nc = 1;
     void* a1[] = {(void*)&dprob, (void*)&dcand, (void*)&lens, &cand0, &nc, &cs};
     TRY(launch(ctx, tb.raytrace[prec], dim3(1), dim3(NTHREADS), a1, (size_t)P.ncells * 4, st));
+    if constexpr (sizeof(T) == 4) {
+        // banded kernel: taps as kernel parameters, L s gathered into shared memory
+        const void* fb = (P.Np == 1 && P.K < MAX_K && P.K * P.K <= MAX_FTAP) ? tb.fwdb[P.K] : nullptr;
+        if (fb && P.tiles_x <= FWD_THREADS) {
+            const int bt = std::min(FWD_THREADS / P.tiles_x, P.tiles_y);
+            const size_t smb = fwd_band_smem(P, bt);
+            if ((long long)smb <= ctx->max_smem) {
+                std::vector<float> psf((size_t)P.K * P.K);
+                CK(cudaMemcpy(psf.data(), P.psf, sizeof(float) * psf.size(), cudaMemcpyDeviceToHost));
+                std::vector<unsigned char> fab(sizeof(FwdArgs), 0);
+                FwdArgs* fa = reinterpret_cast<FwdArgs*>(fab.data());
+                fa->probs = dprob;
+                fa->cs = cs;
+                fa->S = reinterpret_cast<const float*>(s);
+                fa->n_src = n_src;
+                fa->model = reinterpret_cast<float*>(model);
+                fa->chi2 = chi2;
+                fa->status = status;
+                fa->band_tiles = bt;
+                for (int a = 0; a < P.K; ++a)
+                    for (int b = 0; b < P.K; ++b) fa->ptap[a * P.K + b] = psf[(P.K - 1 - a) * P.K + (P.K - 1 - b)];
+                TRY(set_smem(ctx, fb, smb));
+                void* a3[] = {fa};
+                TRY(launch(ctx, fb, dim3(std::min(n_src, ctx->sm_count)), dim3(FWD_THREADS), a3, smb, st));
+                return MIRAGE_OK;
+            }
+        }
+    }
     const void* fn = pick_fwd(prec, P.K);
     const size_t smem = align_up<T>(sizeof(T) * P.K * P.kp, 16) + 2 * 33 * sizeof(double) + 16;
     TRY(set_smem(ctx, fn, smem));

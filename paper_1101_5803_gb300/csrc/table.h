@@ -18,6 +18,8 @@ struct KernelTable {
     const void* fast[MAX_K][2][3];
     // iter[prec][K]: fixed-iteration CGLS with the iteration L-curve
     const void* iter[2][MAX_K];
+    // fwdb[K]: banded FP32 forward batch (one ray per pixel)
+    const void* fwdb[MAX_K];
 };
 
 void fill_f32_k5(KernelTable& t);
@@ -30,5 +32,6 @@ void fill_f32_gen(KernelTable& t);
 void fill_f64(KernelTable& t);
 void fill_fast(KernelTable& t);
 void fill_iter(KernelTable& t);
+void fill_fwd_band(KernelTable& t);
 
 }  // namespace mirage

@@ -65,6 +65,7 @@ def _lam_t(lams, n):
     Geometry(24, 20, 0.1, 12, 10, -0.8, 0.8, -0.7, 0.7, 5, 1, REG_LAPLACIAN),
     Geometry(30, 27, 0.09, 11, 13, -0.9, 0.7, -0.8, 0.9, 7, 2, REG_GRADIENT),   # ragged, sub-pixels
     Geometry(64, 64, 0.05, 32, 32, -0.8, 0.8, -0.8, 0.8, 9, 1, REG_LAPLACIAN),
+    Geometry(96, 90, 0.034, 48, 40, -0.8, 0.8, -0.7, 0.7, 21, 1, REG_LAPLACIAN),  # banded kernel, 21x21, ragged bands
 ])
 def test_forward_matches_oracle(mods, ctx32, ctx64, precision, geom):
     ctx = ctx32 if precision == "fp32" else ctx64
@@ -374,3 +375,31 @@ def test_lambda_chains_ragged_grids_host_memory(mods, ctx32):
         if ca != cb:  # only a near-tie of the curvature may move the corner
             ka = hout["kappa"][c, :n].numpy()
             assert abs(ka[ca] - ka[cb]) <= 1e-3 * ka[ca], (c, ca, cb)
+
+
+def test_forward_batch_256_full_size(mods, ctx32):
+    # the forward batch at full size (256x256 image, 128x128 source, 21x21
+    # PSF, sources |N(0,1)| x template) against the oracle's sparse L and the
+    # zero-padded 'same' convolution its B is pinned to, on every pixel
+    import scipy.signal
+    from oracle.operators import lens_matrix
+    from oracle.solve import Problem
+    g = synth.geom_large256()
+    prob = make_problem(g, seed=8, psf_sigma=synth.PSF_SIGMA["large256"])
+    L, mapped = lens_matrix(g, synth.TRUE_LENS)
+    rng = np.random.default_rng(12)
+    hx = (g.sxmax - g.sxmin) / g.sx
+    c = g.sxmin + (np.arange(g.sx) + 0.5) * hx
+    tmpl = synth.eval_source(synth.drawn_source(rng), *np.meshgrid(c, c)).ravel()
+    S = (np.abs(rng.standard_normal((3, g.ns))) * tmpl[None, :]).astype(np.float32).astype(np.float64)
+    m_g, c_g, st = ctx32.forward(device_problem(prob), _lens_t(synth.TRUE_LENS)[0],
+                                 torch.as_tensor(S, dtype=torch.float32, device="cuda"))
+    assert int(st.item()) == 0
+    w = np.where(mapped & (prob.mask.ravel() > 0), 1.0 / prob.sigma.ravel() ** 2, 0.0)
+    for k in range(S.shape[0]):
+        img = (L @ S[k]).reshape(g.ny, g.nx)
+        mo = scipy.signal.convolve2d(img, prob.psf, mode="same").ravel()
+        mg = m_g[k].double().cpu().numpy()
+        assert np.abs(mg - mo).max() <= 2e-6 * np.abs(mo).max(), k
+        co = float(np.sum(w * (mo - prob.d.ravel()) ** 2))
+        assert abs(float(c_g[k]) - co) <= 1e-4 * co, k

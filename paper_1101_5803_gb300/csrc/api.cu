@@ -279,6 +279,13 @@ int launch(mirage_ctx* ctx, const void* fn, dim3 grid, dim3 block, void** args, 
     return MIRAGE_OK;
 }
 
+// ray trace of candidates [cand0, cand0 + n_cand): one CTA per candidate,
+// or, for fewer candidates than SMs on large images, the split trace (many
+// CTAs per candidate trace and count, one CTA per candidate places)
+template <typename T>
+int launch_raytrace(mirage_ctx* ctx, const Prob<T>* dprobs, const int* dcand, const double* d_lens, int cand0,
+                    int n_cand, const CandScratch<T>& cs, long long max_cells, long long max_npix, cudaStream_t st);
+
 #define TRY(x)                      \
     do {                            \
         int r_ = (x);               \
@@ -303,6 +310,34 @@ struct Stager {
         return o;
     }
 };
+
+template <typename T>
+int launch_raytrace(mirage_ctx* ctx, const Prob<T>* dprobs, const int* dcand, const double* d_lens, int cand0,
+                    int n_cand, const CandScratch<T>& cs, long long max_cells, long long max_npix, cudaStream_t st) {
+    constexpr int prec = prec_of<T>();
+    const KernelTable& tb = table();
+    const size_t cells_smem = (size_t)max_cells * 4;
+    if (n_cand < ctx->sm_count && max_npix >= 128 * 128) {
+        const int chunk = 2 * NTHREADS;
+        const int n_chunks = (int)((max_npix + chunk - 1) / chunk);
+        CK(cudaMemsetAsync(cs.swp + (long long)cand0 * cs.sPad, 0, sizeof(T) * cs.sPad * n_cand, st));
+        CK(cudaMemsetAsync(cs.dpad + (long long)cand0 * cs.sPad, 0, sizeof(T) * cs.sPad * n_cand, st));
+        CK(cudaMemsetAsync(cs.cst + (long long)cand0 * cs.sCst, 0, sizeof(int) * cs.sCst * n_cand, st));
+        CK(cudaMemsetAsync(cs.cstat + cand0, 0, sizeof(int) * n_cand, st));
+        int c0 = cand0, ch = chunk;
+        CandScratch<T> csv = cs;
+        void* a1[] = {(void*)&dprobs, (void*)&dcand, (void*)&d_lens, &c0, &ch, &csv};
+        TRY(launch(ctx, tb.rt_trace[prec], dim3(n_chunks, n_cand), dim3(NTHREADS), a1, 0, st));
+        TRY(set_smem(ctx, tb.rt_place[prec], cells_smem));
+        void* a2[] = {(void*)&dprobs, (void*)&dcand, (void*)&d_lens, &c0, &csv};
+        return launch(ctx, tb.rt_place[prec], dim3(n_cand), dim3(NTHREADS), a2, cells_smem, st);
+    }
+    TRY(set_smem(ctx, tb.raytrace[prec], cells_smem));
+    int c0 = cand0, nc = n_cand;
+    CandScratch<T> csv = cs;
+    void* args[] = {(void*)&dprobs, (void*)&dcand, (void*)&d_lens, &c0, &nc, &csv};
+    return launch(ctx, tb.raytrace[prec], dim3(n_cand), dim3(NTHREADS), args, cells_smem, st);
+}
 
 // work item of the CGLS kernels: lambdas k_first..k_last of candidate c,
 // solved in order by one CTA (see ChainPos)
@@ -346,9 +381,10 @@ int eval_impl(mirage_ctx* ctx, const mirage_problem_t* probs, int n_probs, const
 
     // sizes over the problems
     std::vector<Prob<T>> hp(n_probs);
-    long long max_rays = 0, max_cells = 0, max_plen = 0, max_ns = 0;
+    long long max_rays = 0, max_cells = 0, max_plen = 0, max_ns = 0, max_npix = 0;
     for (int p = 0; p < n_probs; ++p) {
         hp[p] = make_prob<T>(probs[p], probs[p].d, probs[p].sigma, probs[p].mask, probs[p].psf);
+        max_npix = std::max<long long>(max_npix, hp[p].npix);
         max_rays = std::max<long long>(max_rays, hp[p].nrays);
         max_cells = std::max<long long>(max_cells, hp[p].ncells);
         max_plen = std::max<long long>(max_plen, hp[p].plen);
@@ -656,6 +692,7 @@ int eval_impl(mirage_ctx* ctx, const mirage_problem_t* probs, int n_probs, const
 
     for (Group* g : glist) TRY(set_smem(ctx, g->fn, g->smem));
     TRY(set_smem(ctx, tb.raytrace[prec], (size_t)max_cells * 4));
+    TRY(set_smem(ctx, tb.rt_place[prec], (size_t)max_cells * 4));
 
     CglsArgs<T> A;
     std::memset(&A, 0, sizeof(A));
@@ -699,12 +736,8 @@ int eval_impl(mirage_ctx* ctx, const mirage_problem_t* probs, int n_probs, const
         if (o.mode == MIRAGE_MODE_BATCHED) {
             if (timing) cudaEventRecord(ctx->ev[0], st);
             // 1) ray trace every candidate
-            {
-                int cand0 = 0, nc = n_cand;
-                void* args[] = {(void*)&dprobs, (void*)&dcand, (void*)&d_lens, &cand0, &nc, &cs};
-                rc = launch(ctx, tb.raytrace[prec], dim3(n_cand), dim3(NTHREADS), args, (size_t)max_cells * 4, st);
-                if (rc) break;
-            }
+            rc = launch_raytrace<T>(ctx, dprobs, dcand, d_lens, 0, n_cand, cs, max_cells, max_npix, st);
+            if (rc) break;
             // 2) CGLS items, one persistent launch per kernel class
             if (cudaMemsetAsync(dcnt, 0, sizeof(int) * n_counters, st) != cudaSuccess) {
                 set_error("cudaMemsetAsync failed");
@@ -794,8 +827,7 @@ int eval_impl(mirage_ctx* ctx, const mirage_problem_t* probs, int n_probs, const
                 }
                 TRY(set_smem(ctx, fn, item_smem));
                 int cand0 = c, nc = 1;
-                void* a1[] = {(void*)&dprobs, (void*)&dcand, (void*)&d_lens, &cand0, &nc, &cs};
-                rc = launch(ctx, tb.raytrace[prec], dim3(1), dim3(NTHREADS), a1, (size_t)max_cells * 4, st);
+                rc = launch_raytrace<T>(ctx, dprobs, dcand, d_lens, c, 1, cs, max_cells, max_npix, st);
                 if (rc) break;
                 A.items = ditems + plain_off[c];
                 A.n_items = plain_off[c + 1] - plain_off[c];
@@ -906,10 +938,7 @@ int forward_impl(mirage_ctx* ctx, const mirage_problem_t* prob, const double* le
     CandScratch<T> cs;
     fill_scratch<T>(cs, ctx, true, sE, sInv, sCst, sPad);
     const KernelTable& tb = table();
-    TRY(set_smem(ctx, tb.raytrace[prec], (size_t)P.ncells * 4));
-    int cand0 = 0, nc = 1;
-    void* a1[] = {(void*)&dprob, (void*)&dcand, (void*)&lens, &cand0, &nc, &cs};
-    TRY(launch(ctx, tb.raytrace[prec], dim3(1), dim3(NTHREADS), a1, (size_t)P.ncells * 4, st));
+    TRY(launch_raytrace<T>(ctx, dprob, dcand, lens, 0, 1, cs, P.ncells, (long long)P.npix, st));
     if constexpr (sizeof(T) == 4) {
         // banded kernel: taps as kernel parameters, L s gathered into shared memory
         const void* fb = (P.Np == 1 && P.K < MAX_K && P.K * P.K <= MAX_FTAP) ? tb.fwdb[P.K] : nullptr;
@@ -964,7 +993,7 @@ int iter_impl(mirage_ctx* ctx, const mirage_problem_t* probs, int n_probs, const
         return MIRAGE_ERR_ARG;
     }
     std::vector<Prob<T>> hp(n_probs);
-    long long max_rays = 0, max_cells = 0, max_plen = 0, max_ns = 0;
+    long long max_rays = 0, max_cells = 0, max_plen = 0, max_ns = 0, max_npix = 0;
     size_t smem = 0, slab = 0;
     int k_all = -1;
     for (int p = 0; p < n_probs; ++p) {
@@ -982,6 +1011,7 @@ int iter_impl(mirage_ctx* ctx, const mirage_problem_t* probs, int n_probs, const
         max_cells = std::max<long long>(max_cells, hp[p].ncells);
         max_plen = std::max<long long>(max_plen, hp[p].plen);
         max_ns = std::max<long long>(max_ns, hp[p].ns);
+        max_npix = std::max<long long>(max_npix, hp[p].npix);
         smem = std::max(smem, iter_smem_bytes<T>(hp[p].K, hp[p].kp));
         slab = std::max(slab, iter_slab_bytes<T>(hp[p], n_iter));
         k_all = (k_all == -1 || k_all == hp[p].K) ? hp[p].K : 0;
@@ -1019,12 +1049,7 @@ int iter_impl(mirage_ctx* ctx, const mirage_problem_t* probs, int n_probs, const
     const Prob<T>* dprobs = ctx->probs.as<Prob<T>>();
     const int* dcand = ctx->cand_prob.as<int>();
     const KernelTable& tb = table();
-    TRY(set_smem(ctx, tb.raytrace[prec], (size_t)max_cells * 4));
-    {
-        int cand0 = 0, nc = n_cand;
-        void* args[] = {(void*)&dprobs, (void*)&dcand, (void*)&lens, &cand0, &nc, &cs};
-        TRY(launch(ctx, tb.raytrace[prec], dim3(n_cand), dim3(NTHREADS), args, (size_t)max_cells * 4, st));
-    }
+    TRY(launch_raytrace<T>(ctx, dprobs, dcand, lens, 0, n_cand, cs, max_cells, max_npix, st));
     const void* fn = (k_all > 0 && tb.iter[prec][k_all]) ? tb.iter[prec][k_all] : tb.iter[prec][0];
     TRY(set_smem(ctx, fn, smem));
     IterArgs<T> A;

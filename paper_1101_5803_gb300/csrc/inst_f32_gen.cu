@@ -10,6 +10,8 @@ void fill_f32_gen(KernelTable& t) {
     t.fwd[0][0] = (const void*)k_forward<float, 0>;
     t.fwd[0][9] = (const void*)k_forward<float, 9>;
     t.raytrace[0] = (const void*)k_raytrace<float>;
+    t.rt_trace[0] = (const void*)k_rt_trace<float>;
+    t.rt_place[0] = (const void*)k_rt_place<float>;
     t.finalize[0] = (const void*)k_finalize<float>;
 }
 }  // namespace mirage

@@ -9,6 +9,8 @@ void fill_f64(KernelTable& t) {
     t.cgls[1][1][0] = (const void*)k_cgls<double, 0, PLACE_GLOBAL>;
     t.fwd[1][0] = (const void*)k_forward<double, 0>;
     t.raytrace[1] = (const void*)k_raytrace<double>;
+    t.rt_trace[1] = (const void*)k_rt_trace<double>;
+    t.rt_place[1] = (const void*)k_rt_place<double>;
     t.finalize[1] = (const void*)k_finalize<double>;
 }
 }  // namespace mirage

@@ -328,55 +328,27 @@ __device__ __forceinline__ void trace_ray(const LensT<T>& L, T tx, T ty, T& bx, 
 }
 
 // ---------------------------------------------------------------------------
-// k_raytrace: one CTA per candidate
+// Ray trace of one candidate, in two parts shared by the kernels below:
+//   rt_trace_pixels : trace the rays of image pixels [j0, j1) (this CTA's
+//                     threads), write them in ray order, sqrt(W) and the
+//                     padded data, and count rays per cell into `counts`
+//                     and active pixels into `active` (shared or global);
+//   rt_place        : scan the cell counts and place the rays sorted by
+//                     cell, stable within a cell (one warp, in ray order).
+// Rays are traced in FP64 whatever T is: the refinement residual uses these
+// weights, and FP32-rounded weights would perturb the operator by ~1e-7,
+// which the conditioning of small-lambda systems amplifies.
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(NTHREADS) k_raytrace(const Prob<T>* __restrict__ probs,
-                                                       const int* __restrict__ cand_prob,
-                                                       const double* __restrict__ lens, int cand0,
-                                                       int n_cand, CandScratch<T> cs) {
-    const int c = cand0 + blockIdx.x;
-    if (c >= cand0 + n_cand) return;
-    const Prob<T>& P = probs[cand_prob[c]];
-    extern __shared__ int sh_counts[];  // [ncells] counts, then starts/cursors
-    __shared__ int s_active, s_chunk[NTHREADS];
-
-    Entry<T>* E = cs.E + (long long)c * cs.sE;
-    Entry<double>* E64 = cs.E64 + (long long)c * cs.sE;
+__device__ __forceinline__ void rt_trace_pixels(const Prob<T>& P, const LensT<double>& L, const CandScratch<T>& cs,
+                                                int c, int j0, int j1, int* counts, int* active) {
     Entry<double>* Et = cs.Etmp + (long long)c * cs.sE;
-    int* inv = cs.inv + (long long)c * cs.sInv;
-    int* cst = cs.cst + (long long)c * cs.sCst;
     T* swp = cs.swp + (long long)c * cs.sPad;
     T* dpad = cs.dpad + (long long)c * cs.sPad;
-    const int tid = threadIdx.x, bs = blockDim.x;
-    // rays are traced in FP64 whatever T is: the refinement residual uses
-    // these weights, and FP32-rounded weights would perturb the operator by
-    // ~1e-7, which the conditioning of small-lambda systems amplifies
-    const LensT<double> L = make_lens<double>(lens + 7LL * c);
-
-    for (int i = tid; i < P.plen; i += bs) {
-        swp[i] = 0;
-        dpad[i] = 0;
-    }
-    for (int i = tid; i < P.ncells; i += bs) sh_counts[i] = 0;
-    if (tid == 0) s_active = 0;
-    __syncthreads();
-
-    if (L.bad) {
-        for (int r = tid; r < P.nrays; r += bs) inv[r] = -1;
-        for (int i = tid; i <= P.ncells; i += bs) cst[i] = 0;
-        if (tid == 0) {
-            cs.nent[c] = 0;
-            cs.cstat[c] = ST_BADPARAM;
-        }
-        return;
-    }
-
-    // pass 1: trace every ray once, count rays per cell, build sqrt(W)
     const double half_x = 0.5 * (double)(P.nx - 1), half_y = 0.5 * (double)(P.ny - 1);
     const double fxmax = (double)(P.sx - 1), fymax = (double)(P.sy - 1);
     int my_active = 0;
-    for (int j = tid; j < P.npix; j += bs) {
+    for (int j = j0 + (int)threadIdx.x; j < j1; j += blockDim.x) {
         const int x = j % P.nx, y = j / P.nx;
         const double tx = P.cx + ((double)x - half_x) * P.pix;
         const double ty = P.cy + ((double)y - half_y) * P.pix;
@@ -397,7 +369,7 @@ __global__ void __launch_bounds__(NTHREADS) k_raytrace(const Prob<T>* __restrict
                 e.base = iy0 * P.sx + ix0;
                 e.u = fx - (double)ix0;
                 e.v = fy - (double)iy0;
-                atomicAdd(&sh_counts[iy0 * P.ncx + ix0], 1);
+                atomicAdd(&counts[iy0 * P.ncx + ix0], 1);
                 any = true;
             } else {
                 e.base = -1;
@@ -411,8 +383,20 @@ __global__ void __launch_bounds__(NTHREADS) k_raytrace(const Prob<T>* __restrict
         dpad[pp] = P.d[j];
         my_active += (w != (T)0);
     }
-    if (my_active) atomicAdd(&s_active, my_active);
-    __syncthreads();
+    if (my_active) atomicAdd(active, my_active);
+}
+
+// sh_counts: [ncells] shared memory holding the cell counts on entry;
+// s_chunk: [NTHREADS] shared scratch; active: the candidate's active pixels
+template <typename T>
+__device__ __forceinline__ void rt_place(const Prob<T>& P, const CandScratch<T>& cs, int c, int* sh_counts,
+                                         int* s_chunk, int active) {
+    Entry<T>* E = cs.E + (long long)c * cs.sE;
+    Entry<double>* E64 = cs.E64 + (long long)c * cs.sE;
+    const Entry<double>* Et = cs.Etmp + (long long)c * cs.sE;
+    int* inv = cs.inv + (long long)c * cs.sInv;
+    int* cst = cs.cst + (long long)c * cs.sCst;
+    const int tid = threadIdx.x, bs = blockDim.x;
 
     // exclusive scan of the cell counts (chunk per thread, then the chunk sums)
     const int chunk = (P.ncells + bs - 1) / bs;
@@ -430,7 +414,7 @@ __global__ void __launch_bounds__(NTHREADS) k_raytrace(const Prob<T>* __restrict
         }
         cst[P.ncells] = run;
         cs.nent[c] = run;
-        cs.cstat[c] = (s_active > 0) ? 0 : ST_EMPTY;
+        cs.cstat[c] = (active > 0) ? 0 : ST_EMPTY;
     }
     __syncthreads();
     int run = s_chunk[tid];
@@ -478,6 +462,96 @@ __global__ void __launch_bounds__(NTHREADS) k_raytrace(const Prob<T>* __restrict
             __syncwarp();
         }
     }
+}
+
+// sets the outputs of a candidate whose lens parameters are invalid
+template <typename T>
+__device__ __forceinline__ void rt_bad(const Prob<T>& P, const CandScratch<T>& cs, int c) {
+    int* inv = cs.inv + (long long)c * cs.sInv;
+    int* cst = cs.cst + (long long)c * cs.sCst;
+    for (int r = threadIdx.x; r < P.nrays; r += blockDim.x) inv[r] = -1;
+    for (int i = threadIdx.x; i <= P.ncells; i += blockDim.x) cst[i] = 0;
+    if (threadIdx.x == 0) {
+        cs.nent[c] = 0;
+        cs.cstat[c] = ST_BADPARAM;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_raytrace: one CTA per candidate (trace, count, scan, place)
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(NTHREADS) k_raytrace(const Prob<T>* __restrict__ probs,
+                                                       const int* __restrict__ cand_prob,
+                                                       const double* __restrict__ lens, int cand0,
+                                                       int n_cand, CandScratch<T> cs) {
+    const int c = cand0 + blockIdx.x;
+    if (c >= cand0 + n_cand) return;
+    const Prob<T>& P = probs[cand_prob[c]];
+    extern __shared__ int sh_counts[];  // [ncells] counts, then starts/cursors
+    __shared__ int s_active, s_chunk[NTHREADS];
+    T* swp = cs.swp + (long long)c * cs.sPad;
+    T* dpad = cs.dpad + (long long)c * cs.sPad;
+    const int tid = threadIdx.x, bs = blockDim.x;
+    const LensT<double> L = make_lens<double>(lens + 7LL * c);
+
+    for (int i = tid; i < P.plen; i += bs) {
+        swp[i] = 0;
+        dpad[i] = 0;
+    }
+    for (int i = tid; i < P.ncells; i += bs) sh_counts[i] = 0;
+    if (tid == 0) s_active = 0;
+    __syncthreads();
+    if (L.bad) {
+        rt_bad(P, cs, c);
+        return;
+    }
+    rt_trace_pixels(P, L, cs, c, 0, P.npix, sh_counts, &s_active);
+    __syncthreads();
+    rt_place(P, cs, c, sh_counts, s_chunk, s_active);
+}
+
+// ---------------------------------------------------------------------------
+// Split ray trace for few candidates with many rays (the forward batch and
+// other small calls on large images): k_rt_trace spreads the rays of each
+// candidate over blockIdx.x chunks of `chunk` pixels, counting into the
+// candidate's cell-start array and its status word (both zeroed, with sqrt(W)
+// and the padded data, by the caller); k_rt_place then scans and places
+// them, one CTA per candidate.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(NTHREADS) k_rt_trace(const Prob<T>* __restrict__ probs,
+                                                       const int* __restrict__ cand_prob,
+                                                       const double* __restrict__ lens, int cand0, int chunk,
+                                                       CandScratch<T> cs) {
+    const int c = cand0 + blockIdx.y;
+    const Prob<T>& P = probs[cand_prob[c]];
+    const LensT<double> L = make_lens<double>(lens + 7LL * c);
+    if (L.bad) return;
+    const int j0 = blockIdx.x * chunk, j1 = min(j0 + chunk, P.npix);
+    if (j0 >= j1) return;
+    rt_trace_pixels(P, L, cs, c, j0, j1, cs.cst + (long long)c * cs.sCst, cs.cstat + c);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NTHREADS) k_rt_place(const Prob<T>* __restrict__ probs,
+                                                       const int* __restrict__ cand_prob,
+                                                       const double* __restrict__ lens, int cand0,
+                                                       CandScratch<T> cs) {
+    const int c = cand0 + blockIdx.x;
+    const Prob<T>& P = probs[cand_prob[c]];
+    extern __shared__ int sh_counts[];
+    __shared__ int s_chunk[NTHREADS];
+    const LensT<double> L = make_lens<double>(lens + 7LL * c);
+    if (L.bad) {
+        rt_bad(P, cs, c);
+        return;
+    }
+    const int* cnt = cs.cst + (long long)c * cs.sCst;
+    for (int i = threadIdx.x; i < P.ncells; i += blockDim.x) sh_counts[i] = cnt[i];
+    const int active = cs.cstat[c];
+    __syncthreads();
+    rt_place(P, cs, c, sh_counts, s_chunk, active);
 }
 
 // ---------------------------------------------------------------------------

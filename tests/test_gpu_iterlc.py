@@ -102,3 +102,20 @@ def test_iter_lcurve_statuses_and_arguments(mods, ctx32):
         ctx32.eval_iter([dp], L, [0, 0, 0], 64)
     with pytest.raises(mods.MirageError):  # bhat rows shorter than the image
         ctx32.eval_iter([dp], L, [0, 0, 0], 8, bhat=torch.zeros((1, 100), device="cuda"))
+
+
+def test_split_ray_trace_matches_fused(mods, ctx32):
+    # few candidates on a large image take the split ray trace (many CTAs per
+    # candidate trace, one places); as many candidates as SMs take the fused
+    # one.  Both place the rays in the same order: identical records.
+    g = synth.Geometry(128, 128, 0.03, 48, 48, -0.8, 0.8, -0.8, 0.8, 11, 1, synth.REG_LAPLACIAN)
+    prob = make_problem(g, seed=23, psf_sigma=1.5)
+    dp = device_problem(prob)
+    rng = np.random.default_rng(4)
+    lenses = np.vstack([synth.TRUE_LENS, synth.lens_population(rng, 1)])
+    n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+    few = ctx32.eval_iter([dp], torch.as_tensor(lenses, device="cuda"), [0, 0], 12)
+    many_l = np.vstack([lenses] * ((n_sm + 1) // 2 + 1))
+    many = ctx32.eval_iter([dp], torch.as_tensor(many_l, device="cuda"), [0] * len(many_l), 12)
+    for key in ("chi2", "reg", "corner", "s"):
+        assert torch.equal(few[key][:2].cpu(), many[key][:2].cpu()), key

@@ -112,7 +112,7 @@ struct mirage_ctx {
     // scratch
     DevBuf E, E64, Etmp, inv, cst, swp, dpad, nent, cstat, X, istat, slab, probs, cand_prob, items, counters;
     DevBuf stage;  // MIRAGE_MEM_HOST staging
-    DevBuf fE, fE64, fEtmp, finv, fcst, fswp, fdpad, fnent, fcstat, fslab, fprob, fcand;
+    DevBuf fE, fE64, fEtmp, finv, fcst, fswp, fdpad, fnent, fcstat, fslab, fprob, fcand, fpix;
     std::map<std::string, GraphEntry> graphs;
     std::map<const void*, int> smem_set;  // kernel -> dynamic smem attribute set
     cudaStream_t cap_stream = nullptr;   // graphs are captured here and launched on the caller's stream
@@ -948,10 +948,20 @@ int forward_impl(mirage_ctx* ctx, const mirage_problem_t* prob, const double* le
             if ((long long)smb <= ctx->max_smem) {
                 std::vector<float> psf((size_t)P.K * P.K);
                 CK(cudaMemcpy(psf.data(), P.psf, sizeof(float) * psf.size(), cudaMemcpyDeviceToHost));
+                TRY(ctx->fpix.ensure(sizeof(float4) * (size_t)P.npix));
+                float4* pm = ctx->fpix.as<float4>();
+                {
+                    CandScratch<float> csv = cs;
+                    const Prob<float>* dp0 = dprob;
+                    void* ap[] = {(void*)&dp0, &csv, (void*)&pm};
+                    TRY(launch(ctx, tb.pixmap, dim3(std::min((P.npix + NTHREADS - 1) / NTHREADS, 4 * ctx->sm_count)),
+                               dim3(NTHREADS), ap, 0, st));
+                }
                 std::vector<unsigned char> fab(sizeof(FwdArgs), 0);
                 FwdArgs* fa = reinterpret_cast<FwdArgs*>(fab.data());
                 fa->probs = dprob;
                 fa->cs = cs;
+                fa->pixmap = pm;
                 fa->S = reinterpret_cast<const float*>(s);
                 fa->n_src = n_src;
                 fa->model = reinterpret_cast<float*>(model);
@@ -1120,7 +1130,7 @@ int mirage_destroy(mirage_ctx_t* ctx) {
     DevBuf* bufs[] = {&ctx->E, &ctx->E64, &ctx->Etmp, &ctx->inv, &ctx->cst, &ctx->swp, &ctx->dpad, &ctx->nent, &ctx->cstat,
                       &ctx->X, &ctx->istat, &ctx->slab, &ctx->probs, &ctx->cand_prob, &ctx->items, &ctx->counters,
                       &ctx->stage, &ctx->fE, &ctx->fE64, &ctx->fEtmp, &ctx->finv, &ctx->fcst, &ctx->fswp, &ctx->fdpad,
-                      &ctx->fnent, &ctx->fcstat, &ctx->fslab, &ctx->fprob, &ctx->fcand, &ctx->clk};
+                      &ctx->fnent, &ctx->fcstat, &ctx->fslab, &ctx->fprob, &ctx->fcand, &ctx->fpix, &ctx->clk};
     for (DevBuf* b : bufs) b->release();
     delete ctx;
     return MIRAGE_OK;

@@ -5,10 +5,12 @@
 // sources).  The source vector is staged in shared memory; the image is
 // processed in bands of whole tile rows, each band's zero-padded L s values
 // (its rows plus the K-1 halo rows) gathered straight into shared memory
-// through the ray trace's pixel -> ray index, so L s never goes to global
-// memory.  Each thread owns one 4x4 tile of the band and convolves it with
-// the PSF taps held as kernel parameters (read by FFMA from the constant
-// bank); chi^2 is accumulated in FP64.
+// from a pixel-ordered map of the rays' cells and weights (k_pixmap), so
+// L s never goes to global memory.  Each thread owns one 4x4 tile of the
+// band and convolves it with the PSF taps held as kernel parameters, in a
+// loop over pairs of tap rows (each input row is loaded once per pair; the
+// loop body stays small enough for the instruction cache, which the fully
+// unrolled 21x21 tile is not).  chi^2: FP32 per tile, FP64 across tiles.
 #pragma once
 
 #include "fast.cuh"
@@ -21,6 +23,7 @@ constexpr int MAX_FTAP = 31 * 31;
 struct FwdArgs {
     const Prob<float>* probs;
     CandScratch<float> cs;
+    const float4* pixmap;  // [npix] {cell base (int bits) or -1, u, v, 0} in pixel order
     const float* S;   // [n_src][ns]
     int n_src;
     float* model;     // nullable [n_src][npix]
@@ -34,6 +37,81 @@ struct FwdArgs {
 __host__ inline size_t fwd_band_smem(const Prob<float>& P, int band_tiles) {
     return 16 + 2 * 33 * sizeof(double) + align_up<float>(sizeof(float) * P.ns, 16) +
            sizeof(float) * (size_t)(band_tiles * TILE + P.K - 1) * P.Wp;
+}
+
+// pixel-ordered ray map of candidate 0 (one ray per pixel)
+template <int UNUSED = 0>
+__global__ void __launch_bounds__(NTHREADS) k_pixmap(const Prob<float>* __restrict__ probs, CandScratch<float> cs,
+                                                   float4* __restrict__ pixmap) {
+    const Prob<float>& P = probs[0];
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < P.npix; j += gridDim.x * blockDim.x) {
+        const int e = cs.inv[j];
+        float4 m = make_float4(__int_as_float(-1), 0.f, 0.f, 0.f);
+        if (e >= 0) {
+            const Entry<float> en = cs.E[e];
+            m = make_float4(__int_as_float(en.base), en.u, en.v, 0.f);
+        }
+        pixmap[j] = m;
+    }
+}
+
+// One 4x4 output tile: out[r][c] = sum_{a,b} t[a][b] in[r + a][c + b + SHF]
+// (t = the parameter taps), looping over pairs of tap rows: rows a..a+4 of
+// the window serve tap rows a (output rows 0..3) and a+1 (output rows 0..3
+// from window rows a+1..a+4).
+template <int K>
+__device__ __forceinline__ void conv_tile_pairs(const float* __restrict__ Pb, int Wp, const float* pt, float (&out)[16]) {
+    constexpr int HK = (K - 1) / 2;
+    constexpr int SHF = xoff_of<float>(HK) - HK;
+    constexpr int W = TILE + K - 1 + SHF;
+    constexpr int NVW = (W + 3) / 4 * 4;
+    const unsigned src_a = smem_addr(Pb);
+    float acc[TILE][TILE];
+#pragma unroll
+    for (int r = 0; r < TILE; ++r)
+#pragma unroll
+        for (int c = 0; c < TILE; ++c) acc[r][c] = 0.f;
+#pragma unroll 1
+    for (int a = 0; a + 1 < K; a += 2) {
+#pragma unroll
+        for (int rr = 0; rr <= TILE; ++rr) {
+            float in[NVW];
+#pragma unroll
+            for (int v = 0; v < NVW; v += 4) lds_vec(src_a + (unsigned)(((a + rr) * Wp + v) * sizeof(float)), in + v);
+#pragma unroll
+            for (int b = 0; b < K; ++b) {
+                if (rr < TILE) {
+                    const float t = pt[a * K + b];
+#pragma unroll
+                    for (int c = 0; c < TILE; ++c) acc[rr][c] = fmaf(t, in[SHF + b + c], acc[rr][c]);
+                }
+                if (rr >= 1) {
+                    const float t = pt[(a + 1) * K + b];
+#pragma unroll
+                    for (int c = 0; c < TILE; ++c) acc[rr - 1][c] = fmaf(t, in[SHF + b + c], acc[rr - 1][c]);
+                }
+            }
+        }
+    }
+    if constexpr (K % 2 == 1) {  // the last tap row alone
+        constexpr int a = K - 1;
+#pragma unroll
+        for (int rr = 0; rr < TILE; ++rr) {
+            float in[NVW];
+#pragma unroll
+            for (int v = 0; v < NVW; v += 4) lds_vec(src_a + (unsigned)(((a + rr) * Wp + v) * sizeof(float)), in + v);
+#pragma unroll
+            for (int b = 0; b < K; ++b) {
+                const float t = pt[a * K + b];
+#pragma unroll
+                for (int c = 0; c < TILE; ++c) acc[rr][c] = fmaf(t, in[SHF + b + c], acc[rr][c]);
+            }
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < TILE; ++r)
+#pragma unroll
+        for (int c = 0; c < TILE; ++c) out[r * 4 + c] = acc[r][c];
 }
 
 template <int K>
@@ -70,22 +148,39 @@ __global__ void __launch_bounds__(FWD_THREADS, 1) k_forward_band(const __grid_co
         double chi = 0.0;
         for (int b = 0; b < n_bands; ++b) {
             __syncthreads();  // s staged / the previous band's convolution done
-            // gather L s of padded rows [b BR, b BR + rows) into the band
+            // gather L s of padded rows [b BR, b BR + rows) into the band,
+            // four columns per step (row and column advanced without division)
             const int y0 = b * BR - g.hk;  // image row of band row 0
-            for (int q = tid; q < rows * g.Wp; q += bs) {
-                const int r = q / g.Wp, col = q - r * g.Wp;
-                const int y = y0 + r, x = col - g.xoff;
-                float val = 0.f;
-                if (y >= 0 && y < g.ny && x >= 0 && x < g.nx) {
-                    const int e = cs.inv[y * g.nx + x];
-                    if (e >= 0) {
-                        const Entry<float> en = cs.E[e];
-                        const float* s0 = s_sh + en.base;
-                        val = (1.f - en.v) * ((1.f - en.u) * s0[0] + en.u * s0[1]) +
-                              en.v * ((1.f - en.u) * s0[g.sx] + en.u * s0[g.sx + 1]);
+            const int W4 = g.Wp >> 2, dr = bs / W4, dc = bs - dr * W4;
+            int r = tid / W4, c4 = tid - (tid / W4) * W4;
+            for (; r < rows;) {
+                const int y = y0 + r;
+                float4 val = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (y >= 0 && y < g.ny) {
+                    float v4[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int x = c4 * 4 + q - g.xoff;
+                        v4[q] = 0.f;
+                        if (x >= 0 && x < g.nx) {
+                            const float4 m = FA.pixmap[y * g.nx + x];
+                            const int base = __float_as_int(m.x);
+                            if (base >= 0) {
+                                const float* s0 = s_sh + base;
+                                v4[q] = (1.f - m.z) * ((1.f - m.y) * s0[0] + m.y * s0[1]) +
+                                        m.z * ((1.f - m.y) * s0[g.sx] + m.y * s0[g.sx + 1]);
+                            }
+                        }
                     }
+                    val = make_float4(v4[0], v4[1], v4[2], v4[3]);
                 }
-                band[q] = val;
+                reinterpret_cast<float4*>(band)[r * W4 + c4] = val;
+                r += dr;
+                c4 += dc;
+                if (c4 >= W4) {
+                    c4 -= W4;
+                    ++r;
+                }
             }
             __syncthreads();
             // one 4x4 output tile per thread
@@ -93,21 +188,23 @@ __global__ void __launch_bounds__(FWD_THREADS, 1) k_forward_band(const __grid_co
             const int ty = b * BT + ty_l;
             if (ty_l < BT && ty < tiles_y) {
                 float o16[16];
-                conv_tile_fast<K, TAPS_PARAM>(band + (ty_l * TILE) * g.Wp + tx * TILE, g.Wp, nullptr, FA.ptap, o16);
+                conv_tile_pairs<K>(band + (ty_l * TILE) * g.Wp + tx * TILE, g.Wp, FA.ptap, o16);
+                float ct = 0.f;  // the tile's 16 terms in FP32, then one FP64 add
 #pragma unroll
-                for (int r = 0; r < TILE; ++r) {
-                    const int y = ty * TILE + r;
+                for (int rr = 0; rr < TILE; ++rr) {
+                    const int y = ty * TILE + rr;
                     const int pp = (y + g.hk) * g.Wp + tx * TILE + g.xoff;
                     const V4<float> sw = ld4(cs.swp + pp), dv = ld4(cs.dpad + pp);
 #pragma unroll
                     for (int cc = 0; cc < TILE; ++cc) {
-                        const double res = (double)sw.v[cc] * ((double)dv.v[cc] - (double)o16[r * 4 + cc]);
-                        chi = fma(res, res, chi);
+                        const float res = sw.v[cc] * (dv.v[cc] - o16[rr * 4 + cc]);
+                        ct = fmaf(res, res, ct);
                         const int x = tx * TILE + cc;
                         if (FA.model && y < g.ny && x < g.nx)
-                            FA.model[(long long)k * g.nx * g.ny + y * g.nx + x] = o16[r * 4 + cc];
+                            FA.model[(long long)k * g.nx * g.ny + y * g.nx + x] = o16[rr * 4 + cc];
                     }
                 }
+                chi += (double)ct;
             }
         }
         const double cval = block_sum(chi, red, which);

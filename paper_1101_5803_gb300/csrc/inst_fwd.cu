@@ -8,5 +8,6 @@ void fill_fwd_band(KernelTable& t) {
     t.fwdb[11] = (const void*)k_forward_band<11>;
     t.fwdb[15] = (const void*)k_forward_band<15>;
     t.fwdb[21] = (const void*)k_forward_band<21>;
+    t.pixmap = (const void*)k_pixmap<0>;
 }
 }  // namespace mirage

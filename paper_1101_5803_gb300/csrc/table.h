@@ -22,6 +22,7 @@ struct KernelTable {
     const void* iter[2][MAX_K];
     // fwdb[K]: banded FP32 forward batch (one ray per pixel)
     const void* fwdb[MAX_K];
+    const void* pixmap;  // pixel-ordered ray map for the banded forward batch
 };
 
 void fill_f32_k5(KernelTable& t);

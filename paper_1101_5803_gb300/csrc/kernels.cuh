@@ -426,40 +426,58 @@ __device__ __forceinline__ void rt_place(const Prob<T>& P, const CandScratch<T>&
     }
     __syncthreads();
 
-    // pass 2: one warp places the rays in ray order (stable within a cell)
+    // pass 2: one warp places the rays in ray order (stable within a cell),
+    // eight 32-ray batches at a time with the next eight already loading
     if (tid < 32) {
         const int lane = tid;
         const unsigned lt = (1u << lane) - 1u;
-        for (int r0 = 0; r0 < P.nrays; r0 += 32) {
-            const int r = r0 + lane;
-            Entry<double> e;
-            e.base = -1;
-            if (r < P.nrays) e = Et[r];
-            int cell = -1;
-            if (r < P.nrays && e.base >= 0) {
-                const int iy0 = e.base / P.sx, ix0 = e.base - iy0 * P.sx;
-                cell = iy0 * P.ncx + ix0;
+        constexpr int G = 8;
+        Entry<double> nxt[G];
+#pragma unroll
+        for (int q = 0; q < G; ++q) {
+            const int r = q * 32 + lane;
+            nxt[q].base = -1;
+            if (r < P.nrays) nxt[q] = Et[r];
+        }
+        for (int g0 = 0; g0 < P.nrays; g0 += 32 * G) {
+            Entry<double> cur[G];
+#pragma unroll
+            for (int q = 0; q < G; ++q) {
+                cur[q] = nxt[q];
+                const int r = g0 + (G + q) * 32 + lane;
+                nxt[q].base = -1;
+                if (r < P.nrays) nxt[q] = Et[r];
             }
-            const unsigned peers = __match_any_sync(0xffffffffu, cell);
-            const int rank = __popc(peers & lt);
-            if (cell >= 0) {
-                const int pos = sh_counts[cell] + rank;
-                E64[pos] = e;
-                if ((void*)E != (void*)E64) {
-                    Entry<T> et;
-                    et.ppos = e.ppos;
-                    et.base = e.base;
-                    et.u = (T)e.u;
-                    et.v = (T)e.v;
-                    E[pos] = et;
+#pragma unroll
+            for (int q = 0; q < G; ++q) {
+                const int r = g0 + q * 32 + lane;
+                const Entry<double>& e = cur[q];
+                int cell = -1;
+                if (r < P.nrays && e.base >= 0) {
+                    const int iy0 = e.base / P.sx, ix0 = e.base - iy0 * P.sx;
+                    cell = iy0 * P.ncx + ix0;
                 }
-                inv[r] = pos;
-            } else if (r < P.nrays) {
-                inv[r] = -1;
+                const unsigned peers = __match_any_sync(0xffffffffu, cell);
+                const int rank = __popc(peers & lt);
+                if (cell >= 0) {
+                    const int pos = sh_counts[cell] + rank;
+                    E64[pos] = e;
+                    if ((void*)E != (void*)E64) {
+                        Entry<T> et;
+                        et.ppos = e.ppos;
+                        et.base = e.base;
+                        et.u = (T)e.u;
+                        et.v = (T)e.v;
+                        E[pos] = et;
+                    }
+                    inv[r] = pos;
+                } else if (r < P.nrays) {
+                    inv[r] = -1;
+                }
+                __syncwarp();
+                if (cell >= 0 && rank == 0) sh_counts[cell] += __popc(peers);
+                __syncwarp();
             }
-            __syncwarp();
-            if (cell >= 0 && rank == 0) sh_counts[cell] += __popc(peers);
-            __syncwarp();
         }
     }
 }

@@ -4,6 +4,7 @@
 
 #include <algorithm>
 #include <climits>
+#include <initializer_list>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -113,6 +114,13 @@ struct mirage_ctx {
     DevBuf E, E64, Etmp, inv, cst, swp, dpad, nent, cstat, X, istat, slab, probs, cand_prob, items, counters;
     DevBuf stage;  // MIRAGE_MEM_HOST staging
     DevBuf fE, fE64, fEtmp, finv, fcst, fswp, fdpad, fnent, fcstat, fslab, fprob, fcand, fpix;
+    DevBuf rt_cursor;  // per-cell cursors of the parallel ray placement
+    // pinned staging of the per-call uploads (problem descriptors, item
+    // tables): the copies stay asynchronous; the event guards reuse
+    void* pin = nullptr;
+    size_t pin_n = 0;
+    cudaEvent_t pin_ev = nullptr;
+    bool pin_pending = false;
     std::map<std::string, GraphEntry> graphs;
     std::map<const void*, int> smem_set;  // kernel -> dynamic smem attribute set
     cudaStream_t cap_stream = nullptr;   // graphs are captured here and launched on the caller's stream
@@ -279,6 +287,47 @@ int launch(mirage_ctx* ctx, const void* fn, dim3 grid, dim3 block, void** args, 
     return MIRAGE_OK;
 }
 
+// asynchronous upload of small host arrays through the context's pinned
+// staging buffer (a pageable source would make the copy synchronise the
+// stream); the host arrays may go away as soon as this returns
+struct UploadPart {
+    void* dst;
+    const void* src;
+    size_t bytes;
+};
+int upload(mirage_ctx* ctx, cudaStream_t st, std::initializer_list<UploadPart> parts) {
+    size_t total = 0;
+    for (const UploadPart& u : parts) total += (u.bytes + 15) / 16 * 16;
+    if (ctx->pin_pending) {
+        CK(cudaEventSynchronize(ctx->pin_ev));  // the previous call's copies have left the buffer
+        ctx->pin_pending = false;
+    }
+    if (!ctx->pin_ev) CK(cudaEventCreateWithFlags(&ctx->pin_ev, cudaEventDisableTiming));
+    if (total > ctx->pin_n) {
+        if (ctx->pin) cudaFreeHost(ctx->pin);
+        ctx->pin = nullptr;
+        ctx->pin_n = 0;
+        const size_t want = std::max<size_t>(total, 1 << 16);
+        if (cudaHostAlloc(&ctx->pin, want, cudaHostAllocDefault) != cudaSuccess) {
+            ctx->pin = nullptr;
+            set_error("cudaHostAlloc(%zu) failed", want);
+            return MIRAGE_ERR_NOMEM;
+        }
+        ctx->pin_n = want;
+    }
+    size_t off = 0;
+    for (const UploadPart& u : parts) {
+        if (!u.bytes) continue;
+        char* h = static_cast<char*>(ctx->pin) + off;
+        std::memcpy(h, u.src, u.bytes);
+        CK(cudaMemcpyAsync(u.dst, h, u.bytes, cudaMemcpyHostToDevice, st));
+        off += (u.bytes + 15) / 16 * 16;
+    }
+    CK(cudaEventRecord(ctx->pin_ev, st));
+    ctx->pin_pending = true;
+    return MIRAGE_OK;
+}
+
 // ray trace of candidates [cand0, cand0 + n_cand): one CTA per candidate,
 // or, for fewer candidates than SMs on large images, the split trace (many
 // CTAs per candidate trace and count, one CTA per candidate places)
@@ -330,7 +379,17 @@ int launch_raytrace(mirage_ctx* ctx, const Prob<T>* dprobs, const int* dcand, co
         TRY(launch(ctx, tb.rt_trace[prec], dim3(n_chunks, n_cand), dim3(NTHREADS), a1, 0, st));
         TRY(set_smem(ctx, tb.rt_place[prec], cells_smem));
         void* a2[] = {(void*)&dprobs, (void*)&dcand, (void*)&d_lens, &c0, &csv};
-        return launch(ctx, tb.rt_place[prec], dim3(n_cand), dim3(NTHREADS), a2, cells_smem, st);
+        TRY(launch(ctx, tb.rt_place[prec], dim3(n_cand), dim3(NTHREADS), a2, cells_smem, st));
+        // one ray per pixel: parallel placement (the place kernel only scanned)
+        TRY(ctx->rt_cursor.ensure(sizeof(int) * (size_t)cs.sCst * (cand0 + n_cand)));
+        int* cur = ctx->rt_cursor.as<int>();
+        long long cstr = cs.sCst;
+        CK(cudaMemsetAsync(cur + (long long)cand0 * cstr, 0, sizeof(int) * cstr * n_cand, st));
+        void* a3[] = {(void*)&dprobs, (void*)&dcand, (void*)&d_lens, &c0, &ch, &csv, (void*)&cur, &cstr};
+        TRY(launch(ctx, tb.rt_scatter[prec], dim3(n_chunks, n_cand), dim3(NTHREADS), a3, 0, st));
+        void* a4[] = {(void*)&dprobs, (void*)&dcand, (void*)&d_lens, &c0, &csv};
+        return launch(ctx, tb.rt_sortcells[prec], dim3((unsigned)((max_cells + NTHREADS - 1) / NTHREADS), n_cand),
+                      dim3(NTHREADS), a4, 0, st);
     }
     TRY(set_smem(ctx, tb.raytrace[prec], cells_smem));
     int c0 = cand0, nc = n_cand;
@@ -677,9 +736,8 @@ int eval_impl(mirage_ctx* ctx, const mirage_problem_t* probs, int n_probs, const
     TRY(meta_buf.ensure(sizeof(int) * meta.size()));
 
     // uploads (before any capture)
-    CK(cudaMemcpyAsync(probs_buf.p, hp.data(), sizeof(Prob<T>) * n_probs, cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(meta_buf.p, meta.data(), sizeof(int) * meta.size(), cudaMemcpyHostToDevice, st));
-    CK(cudaStreamSynchronize(st));  // the uploads' host buffers die with this call
+    TRY(upload(ctx, st, {{probs_buf.p, hp.data(), sizeof(Prob<T>) * n_probs},
+                         {meta_buf.p, meta.data(), sizeof(int) * meta.size()}}));
 
     CandScratch<T> cs;
     fill_scratch<T>(cs, ctx, false, sE, sInv, sCst, sPad);
@@ -931,8 +989,7 @@ int forward_impl(mirage_ctx* ctx, const mirage_problem_t* prob, const double* le
     TRY(ctx->fslab.ensure(sizeof(T) * stride * grid));
     std::vector<char> up(sizeof(Prob<T>) + sizeof(int), 0);
     std::memcpy(up.data(), &P, sizeof(P));
-    CK(cudaMemcpyAsync(ctx->fprob.p, up.data(), up.size(), cudaMemcpyHostToDevice, st));
-    CK(cudaStreamSynchronize(st));
+    TRY(upload(ctx, st, {{ctx->fprob.p, up.data(), up.size()}}));
     const Prob<T>* dprob = ctx->fprob.as<Prob<T>>();
     const int* dcand = reinterpret_cast<const int*>(ctx->fprob.as<char>() + sizeof(Prob<T>));
     CandScratch<T> cs;
@@ -946,8 +1003,6 @@ int forward_impl(mirage_ctx* ctx, const mirage_problem_t* prob, const double* le
             const int bt = std::min(FWD_THREADS / P.tiles_x, P.tiles_y);
             const size_t smb = fwd_band_smem(P, bt);
             if ((long long)smb <= ctx->max_smem) {
-                std::vector<float> psf((size_t)P.K * P.K);
-                CK(cudaMemcpy(psf.data(), P.psf, sizeof(float) * psf.size(), cudaMemcpyDeviceToHost));
                 TRY(ctx->fpix.ensure(sizeof(float4) * (size_t)P.npix));
                 float4* pm = ctx->fpix.as<float4>();
                 {
@@ -968,8 +1023,6 @@ int forward_impl(mirage_ctx* ctx, const mirage_problem_t* prob, const double* le
                 fa->chi2 = chi2;
                 fa->status = status;
                 fa->band_tiles = bt;
-                for (int a = 0; a < P.K; ++a)
-                    for (int b = 0; b < P.K; ++b) fa->ptap[a * P.K + b] = psf[(P.K - 1 - a) * P.K + (P.K - 1 - b)];
                 TRY(set_smem(ctx, fb, smb));
                 void* a3[] = {fa};
                 TRY(launch(ctx, fb, dim3(std::min(n_src, ctx->sm_count)), dim3(FWD_THREADS), a3, smb, st));
@@ -1050,10 +1103,9 @@ int iter_impl(mirage_ctx* ctx, const mirage_problem_t* probs, int n_probs, const
     TRY(ctx->counters.ensure(sizeof(int)));
     const int grid = std::min(n_cand, 2 * ctx->sm_count);
     TRY(ctx->slab.ensure(slab * grid));
-    CK(cudaMemcpyAsync(ctx->probs.p, hp.data(), sizeof(Prob<T>) * n_probs, cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(ctx->cand_prob.p, prob_idx, sizeof(int) * n_cand, cudaMemcpyHostToDevice, st));
+    TRY(upload(ctx, st, {{ctx->probs.p, hp.data(), sizeof(Prob<T>) * n_probs},
+                         {ctx->cand_prob.p, prob_idx, sizeof(int) * n_cand}}));
     CK(cudaMemsetAsync(ctx->counters.p, 0, sizeof(int), st));
-    CK(cudaStreamSynchronize(st));  // the host arrays of the uploads may go away after the call
     CandScratch<T> cs;
     fill_scratch<T>(cs, ctx, false, sE, sInv, sCst, sPad);
     const Prob<T>* dprobs = ctx->probs.as<Prob<T>>();
@@ -1130,8 +1182,11 @@ int mirage_destroy(mirage_ctx_t* ctx) {
     DevBuf* bufs[] = {&ctx->E, &ctx->E64, &ctx->Etmp, &ctx->inv, &ctx->cst, &ctx->swp, &ctx->dpad, &ctx->nent, &ctx->cstat,
                       &ctx->X, &ctx->istat, &ctx->slab, &ctx->probs, &ctx->cand_prob, &ctx->items, &ctx->counters,
                       &ctx->stage, &ctx->fE, &ctx->fE64, &ctx->fEtmp, &ctx->finv, &ctx->fcst, &ctx->fswp, &ctx->fdpad,
-                      &ctx->fnent, &ctx->fcstat, &ctx->fslab, &ctx->fprob, &ctx->fcand, &ctx->fpix, &ctx->clk};
+                      &ctx->fnent, &ctx->fcstat, &ctx->fslab, &ctx->fprob, &ctx->fcand, &ctx->fpix, &ctx->rt_cursor, &ctx->clk};
     for (DevBuf* b : bufs) b->release();
+    if (ctx->pin_pending) cudaEventSynchronize(ctx->pin_ev);
+    if (ctx->pin) cudaFreeHost(ctx->pin);
+    if (ctx->pin_ev) cudaEventDestroy(ctx->pin_ev);
     delete ctx;
     return MIRAGE_OK;
 }

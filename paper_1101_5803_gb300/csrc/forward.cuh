@@ -7,8 +7,8 @@
 // (its rows plus the K-1 halo rows) gathered straight into shared memory
 // from a pixel-ordered map of the rays' cells and weights (k_pixmap), so
 // L s never goes to global memory.  Each thread owns one 4x4 tile of the
-// band and convolves it with the PSF taps held as kernel parameters, in a
-// loop over pairs of tap rows (each input row is loaded once per pair; the
+// band and convolves it with the PSF taps (staged in shared memory, read as
+// warp-uniform broadcasts), in a loop over pairs of tap rows (each input row is loaded once per pair; the
 // loop body stays small enough for the instruction cache, which the fully
 // unrolled 21x21 tile is not).  chi^2: FP32 per tile, FP64 across tiles.
 #pragma once
@@ -30,13 +30,12 @@ struct FwdArgs {
     double* chi2;     // [n_src]
     int* status;      // nullable [1]
     int band_tiles;   // tile rows per band
-    float ptap[MAX_FTAP];  // flipped PSF (B), row-major K x K
 };
 
-// shared memory: source vector, then the band (band rows + K - 1) x Wp
+// shared memory: taps, source vector, then the band (band rows + K - 1) x Wp
 __host__ inline size_t fwd_band_smem(const Prob<float>& P, int band_tiles) {
-    return 16 + 2 * 33 * sizeof(double) + align_up<float>(sizeof(float) * P.ns, 16) +
-           sizeof(float) * (size_t)(band_tiles * TILE + P.K - 1) * P.Wp;
+    return 16 + 2 * 33 * sizeof(double) + align_up<float>(sizeof(float) * P.K * P.K, 16) +
+           align_up<float>(sizeof(float) * P.ns, 16) + sizeof(float) * (size_t)(band_tiles * TILE + P.K - 1) * P.Wp;
 }
 
 // pixel-ordered ray map of candidate 0 (one ray per pixel)
@@ -56,7 +55,7 @@ __global__ void __launch_bounds__(NTHREADS) k_pixmap(const Prob<float>* __restri
 }
 
 // One 4x4 output tile: out[r][c] = sum_{a,b} t[a][b] in[r + a][c + b + SHF]
-// (t = the parameter taps), looping over pairs of tap rows: rows a..a+4 of
+// (t = the taps in shared memory), looping over pairs of tap rows: rows a..a+4 of
 // the window serve tap rows a (output rows 0..3) and a+1 (output rows 0..3
 // from window rows a+1..a+4).
 template <int K>
@@ -121,9 +120,15 @@ __global__ void __launch_bounds__(FWD_THREADS, 1) k_forward_band(const __grid_co
     const CandScratch<float>& cs = FA.cs;
     const Geo<float> g = geo_of(P, cs.nent[0]);
     double* red = reinterpret_cast<double*>(smem + 16);
-    float* s_sh = reinterpret_cast<float*>(smem + 16 + 2 * 33 * sizeof(double));
+    float* taps = reinterpret_cast<float*>(smem + 16 + 2 * 33 * sizeof(double));
+    float* s_sh = taps + align_up<float>(K * K, 4);
     float* band = s_sh + align_up<float>(g.ns, 4);
     const int tid = threadIdx.x, bs = blockDim.x;
+    // taps of B: the flipped PSF, row-major K x K
+    for (int i = tid; i < K * K; i += bs) {
+        const int a = i / K, b = i - a * K;
+        taps[i] = P.psf[(K - 1 - a) * K + (K - 1 - b)];
+    }
     const int BT = FA.band_tiles, BR = BT * TILE;
     const int tiles_y = g.ntiles / g.tiles_x;
     const int n_bands = (tiles_y + BT - 1) / BT;
@@ -188,7 +193,7 @@ __global__ void __launch_bounds__(FWD_THREADS, 1) k_forward_band(const __grid_co
             const int ty = b * BT + ty_l;
             if (ty_l < BT && ty < tiles_y) {
                 float o16[16];
-                conv_tile_pairs<K>(band + (ty_l * TILE) * g.Wp + tx * TILE, g.Wp, FA.ptap, o16);
+                conv_tile_pairs<K>(band + (ty_l * TILE) * g.Wp + tx * TILE, g.Wp, taps, o16);
                 float ct = 0.f;  // the tile's 16 terms in FP32, then one FP64 add
 #pragma unroll
                 for (int rr = 0; rr < TILE; ++rr) {

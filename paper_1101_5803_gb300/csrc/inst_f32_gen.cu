@@ -12,6 +12,8 @@ void fill_f32_gen(KernelTable& t) {
     t.raytrace[0] = (const void*)k_raytrace<float>;
     t.rt_trace[0] = (const void*)k_rt_trace<float>;
     t.rt_place[0] = (const void*)k_rt_place<float>;
+    t.rt_scatter[0] = (const void*)k_rt_scatter<float>;
+    t.rt_sortcells[0] = (const void*)k_rt_sortcells<float>;
     t.finalize[0] = (const void*)k_finalize<float>;
 }
 }  // namespace mirage

@@ -11,6 +11,8 @@ void fill_f64(KernelTable& t) {
     t.raytrace[1] = (const void*)k_raytrace<double>;
     t.rt_trace[1] = (const void*)k_rt_trace<double>;
     t.rt_place[1] = (const void*)k_rt_place<double>;
+    t.rt_scatter[1] = (const void*)k_rt_scatter<double>;
+    t.rt_sortcells[1] = (const void*)k_rt_sortcells<double>;
     t.finalize[1] = (const void*)k_finalize<double>;
 }
 }  // namespace mirage

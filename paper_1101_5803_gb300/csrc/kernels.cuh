@@ -390,7 +390,7 @@ __device__ __forceinline__ void rt_trace_pixels(const Prob<T>& P, const LensT<do
 // s_chunk: [NTHREADS] shared scratch; active: the candidate's active pixels
 template <typename T>
 __device__ __forceinline__ void rt_place(const Prob<T>& P, const CandScratch<T>& cs, int c, int* sh_counts,
-                                         int* s_chunk, int active) {
+                                         int* s_chunk, int active, bool place = true) {
     Entry<T>* E = cs.E + (long long)c * cs.sE;
     Entry<double>* E64 = cs.E64 + (long long)c * cs.sE;
     const Entry<double>* Et = cs.Etmp + (long long)c * cs.sE;
@@ -425,6 +425,7 @@ __device__ __forceinline__ void rt_place(const Prob<T>& P, const CandScratch<T>&
         run += v;
     }
     __syncthreads();
+    if (!place) return;
 
     // pass 2: one warp places the rays in ray order (stable within a cell),
     // eight 32-ray batches at a time with the next eight already loading
@@ -569,7 +570,80 @@ __global__ void __launch_bounds__(NTHREADS) k_rt_place(const Prob<T>* __restrict
     for (int i = threadIdx.x; i < P.ncells; i += blockDim.x) sh_counts[i] = cnt[i];
     const int active = cs.cstat[c];
     __syncthreads();
-    rt_place(P, cs, c, sh_counts, s_chunk, active);
+    // one ray per pixel: only the scan here, the rays are placed in parallel
+    // by k_rt_scatter and k_rt_sortcells
+    rt_place(P, cs, c, sh_counts, s_chunk, active, P.Np != 1);
+}
+
+// parallel placement for one ray per pixel: each mapped ray takes a slot of
+// its cell's segment by an atomic cursor (in no particular order) ...
+template <typename T>
+__global__ void __launch_bounds__(NTHREADS) k_rt_scatter(const Prob<T>* __restrict__ probs,
+                                                         const int* __restrict__ cand_prob,
+                                                         const double* __restrict__ lens, int cand0, int chunk,
+                                                         CandScratch<T> cs, int* __restrict__ cursor,
+                                                         long long cursor_stride) {
+    const int c = cand0 + blockIdx.y;
+    const Prob<T>& P = probs[cand_prob[c]];
+    if (P.Np != 1 || make_lens<double>(lens + 7LL * c).bad) return;
+    const Entry<double>* Et = cs.Etmp + (long long)c * cs.sE;
+    Entry<double>* E64 = cs.E64 + (long long)c * cs.sE;
+    const int* cst = cs.cst + (long long)c * cs.sCst;
+    int* cur = cursor + (long long)c * cursor_stride;
+    int* inv = cs.inv + (long long)c * cs.sInv;
+    const int r1 = min((int)(blockIdx.x + 1) * chunk, P.nrays);
+    for (int r = blockIdx.x * chunk + threadIdx.x; r < r1; r += blockDim.x) {
+        const Entry<double> e = Et[r];
+        if (e.base >= 0) {
+            const int iy0 = e.base / P.sx, ix0 = e.base - iy0 * P.sx;
+            const int cell = iy0 * P.ncx + ix0;
+            E64[cst[cell] + atomicAdd(&cur[cell], 1)] = e;
+        } else {
+            inv[r] = -1;
+        }
+    }
+}
+
+// ... then each cell's segment is sorted by ray index (the pixel's padded
+// position is increasing in it), which is the stable order of the one-warp
+// placement; the FP32 copy and the ray -> position index follow
+template <typename T>
+__global__ void __launch_bounds__(NTHREADS) k_rt_sortcells(const Prob<T>* __restrict__ probs,
+                                                           const int* __restrict__ cand_prob,
+                                                           const double* __restrict__ lens, int cand0,
+                                                           CandScratch<T> cs) {
+    const int c = cand0 + blockIdx.y;
+    const Prob<T>& P = probs[cand_prob[c]];
+    if (P.Np != 1 || make_lens<double>(lens + 7LL * c).bad) return;
+    Entry<double>* E64 = cs.E64 + (long long)c * cs.sE;
+    Entry<T>* E = cs.E + (long long)c * cs.sE;
+    const int* cst = cs.cst + (long long)c * cs.sCst;
+    int* inv = cs.inv + (long long)c * cs.sInv;
+    const int cell = blockIdx.x * blockDim.x + threadIdx.x;
+    if (cell >= P.ncells) return;
+    const int k0 = cst[cell], k1 = cst[cell + 1];
+    for (int i = k0 + 1; i < k1; ++i) {  // insertion sort (cells hold few rays)
+        const Entry<double> key = E64[i];
+        int j = i - 1;
+        while (j >= k0 && E64[j].ppos > key.ppos) {
+            E64[j + 1] = E64[j];
+            --j;
+        }
+        E64[j + 1] = key;
+    }
+    for (int i = k0; i < k1; ++i) {
+        const Entry<double> e = E64[i];
+        if ((void*)E != (void*)E64) {
+            Entry<T> et;
+            et.ppos = e.ppos;
+            et.base = e.base;
+            et.u = (T)e.u;
+            et.v = (T)e.v;
+            E[i] = et;
+        }
+        const int y = e.ppos / P.Wp - P.hk, x = e.ppos - (e.ppos / P.Wp) * P.Wp - P.xoff;
+        inv[y * P.nx + x] = i;
+    }
 }
 
 // ---------------------------------------------------------------------------

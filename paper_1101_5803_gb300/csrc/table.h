@@ -14,6 +14,8 @@ struct KernelTable {
     const void* raytrace[2];
     const void* rt_trace[2];  // split ray trace: trace and count (many CTAs per candidate)
     const void* rt_place[2];  //                  scan and place (one CTA per candidate)
+    const void* rt_scatter[2];    // parallel placement, one ray per pixel
+    const void* rt_sortcells[2];
     const void* finalize[2];
     // fast[K][v][mode]: two-CTA-per-SM FP32 kernel, v = 0 for ns <= 1024,
     // 1 for ns <= 2304; mode = tap source (0 shared, 1 params FFMA, 2 params FFMA2)

@@ -13,6 +13,7 @@ Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 Modules: ``lens`` (ray trace), ``operators`` (L, B, W, H), ``solve``
 (Cholesky solve, chi^2, regularisation measure, forward batch), ``lcurve``
 (corner), ``data`` (synthetic observations), ``mlp`` (surrogate network
-forward/backward/Adam), ``cg`` (matrix-free FP64 conjugate gradient, used
-where a dense B does not fit).
+forward/backward/Adam), ``cg`` (matrix-free FP64 CGLS, used where a dense
+F = B L does not fit), ``iterlc`` (fixed-iteration CGLS, the L-curve over
+its iterations and the Monte Carlo degrees of freedom).
 """

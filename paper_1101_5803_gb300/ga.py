@@ -226,3 +226,45 @@ def run_ga(ctx: Context, wl: Workload, cfg: GAConfig, log=None):
             log(st)
     b = int(np.argmin(fit))
     return hist, pop[b], float(fit[b])
+
+
+def main(argv=None):
+    """End-to-end GA on the 128x128 system (the surrogate-screened search):
+    one JSON line per generation with the best corner chi^2, exact solves,
+    offspring decisions, seconds, surrogate RMSE and rank correlation on the
+    generation's exact results, and whether the screen was on (off = the
+    fallback)."""
+    import argparse
+    import json
+
+    from .binding import MIRAGE_FP32
+    from .problems import e2e128_workload
+
+    ap = argparse.ArgumentParser(description=main.__doc__)
+    ap.add_argument("--pop", type=int, default=512)
+    ap.add_argument("--generations", type=int, default=200)
+    ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--lam-chain", action="store_true")
+    ap.add_argument("--seed", type=int, default=0)
+    a = ap.parse_args(argv)
+    ctx = Context(0, MIRAGE_FP32)
+    wl = e2e128_workload(ctx, n_cand=a.pop, seed=a.seed)
+    cfg = GAConfig(pop=a.pop, generations=a.generations, surrogate=not a.no_surrogate, lam_chain=a.lam_chain,
+                   seed=a.seed)
+
+    def log(st):
+        print(json.dumps({"gen": st.gen, "best_chi2": st.best_chi2, "exact_evals": st.exact_evals,
+                          "decisions": st.decisions, "cg_iters": st.cg_iters, "seconds": round(st.seconds, 4),
+                          "surrogate_rmse": st.surrogate_rmse, "surrogate_rho": st.surrogate_rho,
+                          "screened": st.screened}), flush=True)
+
+    hist, best, bchi = run_ga(ctx, wl, cfg, log=log)
+    gens = hist[1:]
+    print(json.dumps({"summary": True, "best_chi2": bchi, "best_lens": [float(v) for v in best],
+                      "exact_evals_per_s": sum(h.exact_evals for h in gens) / sum(h.seconds for h in gens),
+                      "fallback_rate": 1.0 - sum(h.screened for h in gens) / max(1, len(gens)),
+                      "surrogate_rmse_last": gens[-1].surrogate_rmse if gens else None}), flush=True)
+
+
+if __name__ == "__main__":
+    main()

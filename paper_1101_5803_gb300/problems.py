@@ -73,6 +73,19 @@ def ga64_workload(ctx: Context, n_cand: int = 256, n_lam: int = 16, seed: int = 
     return Workload(g, prob, lens, lams, np.full(n_cand, n_lam, np.int32), np.zeros(n_cand, np.int32))
 
 
+def e2e128_workload(ctx: Context, n_cand: int = 512, n_lam: int = 16, seed: int = 0) -> Workload:
+    """End-to-end GA system: 128x128 image at 0.03"/px, 48x48 source over
+    +-0.8", 11x11 Gaussian PSF (sigma 1.5 px), Laplacian H, n_lam lambdas
+    log-spaced over 1e-4..1e2."""
+    rng = np.random.default_rng(seed)
+    g = synth.geom_e2e128()
+    psf = synth.gaussian_psf(g.kpsf, synth.PSF_SIGMA["e2e128"])
+    prob = observe_on_device(ctx, g, psf, synth.drawn_source(rng), synth.TRUE_LENS, rng)
+    lens = torch.as_tensor(synth.lens_population(rng, n_cand), device="cuda")
+    lams = torch.as_tensor(np.tile(synth.lambda_grid(n_lam), (n_cand, 1)), device="cuda")
+    return Workload(g, prob, lens, lams, np.full(n_cand, n_lam, np.int32), np.zeros(n_cand, np.int32))
+
+
 @dataclasses.dataclass
 class MultiWorkload:
     problems: list          # one Problem per distinct observation

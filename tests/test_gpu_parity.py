@@ -403,3 +403,31 @@ def test_forward_batch_256_full_size(mods, ctx32):
         assert np.abs(mg - mo).max() <= 2e-6 * np.abs(mo).max(), k
         co = float(np.sum(w * (mo - prob.d.ravel()) ** 2))
         assert abs(float(c_g[k]) - co) <= 1e-4 * co, k
+
+
+def test_eval_fp32_256_full_size_against_matrix_free_oracle(mods, ctx32):
+    # the large-field case (256x256 image, 128x128 source, 21x21 PSF,
+    # Laplacian): the dense oracle is infeasible, so the matrix-free FP64 CGLS
+    # oracle (pinned against the dense one) supplies the residual of the GPU
+    # solution, chi^2 at it, and the exact solution's chi^2
+    from oracle.cg import chi2_reg, cgls_solve, normal_residual, sparse_operators
+    g = synth.geom_large256()
+    prob = make_problem(g, seed=8, psf_sigma=synth.PSF_SIGMA["large256"])
+    lam = 10.0
+    out = ctx32.eval_batch([device_problem(prob)], _lens_t([synth.TRUE_LENS]), [0], _lam_t([lam], 1), [1],
+                           tol=1e-6, want_all_x=True)
+    st = int(out["item_status"][0, 0].item())
+    assert st & 7 == 0, st
+    ops = sparse_operators(prob, synth.TRUE_LENS)
+    s_g = out["all_x"][0, 0, :g.ns].double().cpu().numpy()
+    rn = np.linalg.norm(ops.rhs)
+    rr = np.linalg.norm(normal_residual(ops, s_g, lam)) / rn
+    rep = out["relres"][0, 0].item()
+    assert rr <= 1e-5 and abs(rep - rr) <= 0.5 * rr + 2e-6, (rr, rep)
+    c_at, _ = chi2_reg(ops, s_g)
+    chi_g = out["chi2"][0, 0].item()
+    assert abs(chi_g - c_at) <= 1e-6 * c_at
+    s_ref, rel_ref, _ = cgls_solve(ops, lam, tol=1e-12)
+    c_ref, r_ref = chi2_reg(ops, s_ref)
+    assert abs(chi_g - c_ref) <= 1e-5 * c_ref
+    assert abs(out["reg"][0, 0].item() - r_ref) <= 1e-4 * r_ref

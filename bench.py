@@ -363,7 +363,10 @@ def run_gpu(args):
                         "best_chi2_by_gen": [round(h.best_chi2, 2) for h in hist],
                         "screened_gens": int(sum(h.screened for h in gens)),
                         "rank_corr_by_gen": [None if h.surrogate_rho is None else round(h.surrogate_rho, 3)
-                                             for h in gens]}
+                                             for h in gens],
+                        "surrogate_rmse_by_gen": [None if h.surrogate_rmse is None else round(h.surrogate_rmse, 4)
+                                                  for h in gens],
+                        "fallback_rate": (1.0 - sum(h.screened for h in gens) / max(1, len(gens))) if sur_on else None}
     ga_res["generations"] = n_gen
     ga_res["oversample"] = 4
 

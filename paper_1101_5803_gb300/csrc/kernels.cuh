@@ -1446,6 +1446,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_cgls(CglsArgs<T> A) {
                 __syncthreads();
             }
             const int stag_window = max(4000, 2 * g.ns);
+            const bool cells_fit = 4 * g.ncells <= g.plen;  // the cell sums fit in P2
             while (!ctl->stop) {
                 // q = A~ p: image part sqrt(W) B L p, regulariser part sqrt(lam) H p
                 apply_L<T, T, T, T>(g, w.E, w.inv, w.p, w.P1);
@@ -1495,13 +1496,51 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_cgls(CglsArgs<T> A) {
                 conv_pass<T, K, SH>(w.P2, w.taps + g.K * g.kp, nullptr, w.qimg, g, CONV_RAW);
                 __syncthreads();  // u complete
                 T gs = 0;
-                for (int i = tid; i < g.ns; i += bs) {
-                    const int ib = i / g.sx, ia = i - ib * g.sx;
-                    const T v = apply_LT_at<T, T, T>(g, w.E, w.cst, w.qimg, ia, ib) +
-                                sl * apply_HT_at<T, T>(g, w.rreg, i, ia, ib);
-                    const T z = w.minv[i] * v;  // preconditioned gradient
-                    w.s[i] = z;
-                    gs = fma(v, z, gs);
+                if (cells_fit) {
+                    // L^T u in two passes: per cell, the four corner sums of its
+                    // rays (each ray read once) into P2's storage (free until the
+                    // next residual store); then per source pixel the fixed-order
+                    // sum of the corners it receives from its (up to) four cells
+                    T* cp = w.P2;
+                    for (int cell = tid; cell < g.ncells; cell += bs) {
+                        const int k1 = w.cst[cell + 1];
+                        T c00 = 0, c10 = 0, c01 = 0, c11 = 0;
+                        for (int k = w.cst[cell]; k < k1; ++k) {
+                            const Entry<T> en = w.E[k];
+                            const T U = w.qimg[en.ppos];
+                            const T uU = en.u * U, u0 = U - uU;  // u U, (1-u) U
+                            c00 = fma((T)1 - en.v, u0, c00);
+                            c10 = fma((T)1 - en.v, uU, c10);
+                            c01 = fma(en.v, u0, c01);
+                            c11 = fma(en.v, uU, c11);
+                        }
+                        cp[4 * cell + 0] = c00;
+                        cp[4 * cell + 1] = c10;
+                        cp[4 * cell + 2] = c01;
+                        cp[4 * cell + 3] = c11;
+                    }
+                    __syncthreads();
+                    for (int i = tid; i < g.ns; i += bs) {
+                        const int ib = i / g.sx, ia = i - ib * g.sx;
+                        T acc = 0;
+                        if (ib <= g.sy - 2 && ia <= g.sx - 2) acc += cp[4 * (ib * g.ncx + ia) + 0];
+                        if (ib <= g.sy - 2 && ia >= 1) acc += cp[4 * (ib * g.ncx + ia - 1) + 1];
+                        if (ib >= 1 && ia <= g.sx - 2) acc += cp[4 * ((ib - 1) * g.ncx + ia) + 2];
+                        if (ib >= 1 && ia >= 1) acc += cp[4 * ((ib - 1) * g.ncx + ia - 1) + 3];
+                        const T v = acc * g.invNp + sl * apply_HT_at<T, T>(g, w.rreg, i, ia, ib);
+                        const T z = w.minv[i] * v;  // preconditioned gradient
+                        w.s[i] = z;
+                        gs = fma(v, z, gs);
+                    }
+                } else {
+                    for (int i = tid; i < g.ns; i += bs) {
+                        const int ib = i / g.sx, ia = i - ib * g.sx;
+                        const T v = apply_LT_at<T, T, T>(g, w.E, w.cst, w.qimg, ia, ib) +
+                                    sl * apply_HT_at<T, T>(g, w.rreg, i, ia, ib);
+                        const T z = w.minv[i] * v;  // preconditioned gradient
+                        w.s[i] = z;
+                        gs = fma(v, z, gs);
+                    }
                 }
                 {
                     const double gnew = block_sum_to0<T>(gs, red);
@@ -1526,6 +1565,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_cgls(CglsArgs<T> A) {
                     }
                     __syncthreads();
                 }
+                // the cell sums overwrote part of P2's zero frame: clear them
+                if (cells_fit)
+                    for (int i = tid; i < 4 * g.ncells; i += bs) w.P2[i] = 0;
                 const T bt = sizeof(T) == 4 ? (T)ctl->b_f : (T)ctl->b_d;
                 for (int i = tid; i < g.ns; i += bs) w.p[i] = fma(bt, w.p[i], w.s[i]);
                 __syncthreads();

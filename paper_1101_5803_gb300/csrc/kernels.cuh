@@ -677,6 +677,69 @@ __device__ __forceinline__ void conv_tile(const T* __restrict__ Pb, int Wp, cons
     constexpr bool TAPREG = (K <= 9);
     const unsigned tap_a = smem_addr(taps);
     const unsigned src_a = SH ? smem_addr(Pb) : 0u;
+    if constexpr (!TAPREG) {
+        // larger PSFs: loop over pairs of tap rows; the pair's 2K taps are
+        // loaded once, and window rows a..a+4 each once, serving tap row a
+        // (output rows 0..3) and tap row a+1 (output rows 0..3 from window
+        // rows a+1..a+4)
+#pragma unroll
+        for (int r = 0; r < TILE; ++r)
+#pragma unroll
+            for (int c = 0; c < TILE; ++c) acc[r][c] = 0;
+#pragma unroll 1
+        for (int a = 0; a + 1 < K; a += 2) {
+            T t0[K], t1[K];
+#pragma unroll
+            for (int b = 0; b < K; ++b) {
+                t0[b] = lds_one(tap_a + (unsigned)((a * KP + b) * sizeof(T)), T(0));
+                t1[b] = lds_one(tap_a + (unsigned)(((a + 1) * KP + b) * sizeof(T)), T(0));
+            }
+#pragma unroll
+            for (int rr = 0; rr <= TILE; ++rr) {
+                T in[NVW];
+#pragma unroll
+                for (int v = 0; v < NVW; v += VW) {
+                    if (SH)
+                        lds_vec(src_a + (unsigned)(((a + rr) * Wp + v) * sizeof(T)), in + v);
+                    else
+                        vload(Pb + (a + rr) * Wp + v, in + v);
+                }
+#pragma unroll
+                for (int b = 0; b < K; ++b) {
+                    if (rr < TILE) {
+#pragma unroll
+                        for (int c = 0; c < TILE; ++c) acc[rr][c] = fma(t0[b], in[SHF + b + c], acc[rr][c]);
+                    }
+                    if (rr >= 1) {
+#pragma unroll
+                        for (int c = 0; c < TILE; ++c) acc[rr - 1][c] = fma(t1[b], in[SHF + b + c], acc[rr - 1][c]);
+                    }
+                }
+            }
+        }
+        if constexpr (K % 2 == 1) {  // the last tap row alone
+            constexpr int a = K - 1;
+            T t0[K];
+#pragma unroll
+            for (int b = 0; b < K; ++b) t0[b] = lds_one(tap_a + (unsigned)((a * KP + b) * sizeof(T)), T(0));
+#pragma unroll
+            for (int rr = 0; rr < TILE; ++rr) {
+                T in[NVW];
+#pragma unroll
+                for (int v = 0; v < NVW; v += VW) {
+                    if (SH)
+                        lds_vec(src_a + (unsigned)(((a + rr) * Wp + v) * sizeof(T)), in + v);
+                    else
+                        vload(Pb + (a + rr) * Wp + v, in + v);
+                }
+#pragma unroll
+                for (int b = 0; b < K; ++b)
+#pragma unroll
+                    for (int c = 0; c < TILE; ++c) acc[rr][c] = fma(t0[b], in[SHF + b + c], acc[rr][c]);
+            }
+        }
+        return;
+    }
     T tw[TAPREG ? K : 1][TAPREG ? K : 1];
     if constexpr (TAPREG) {
 #pragma unroll

@@ -3,7 +3,8 @@
 //
 // One CTA of FWD_THREADS threads per source at a time (persistent over the
 // sources).  The source vector is staged in shared memory; the image is
-// processed in bands of whole tile rows, each band's zero-padded L s values
+// processed in bands of whole tile rows (two buffers: one band is filled
+// while the previous one is convolved), each band's zero-padded L s values
 // (its rows plus the K-1 halo rows) gathered straight into shared memory
 // from a pixel-ordered map of the rays' cells and weights (k_pixmap), so
 // L s never goes to global memory.  Each thread owns one 4x4 tile of the
@@ -32,10 +33,11 @@ struct FwdArgs {
     int band_tiles;   // tile rows per band
 };
 
-// shared memory: taps, source vector, then the band (band rows + K - 1) x Wp
+// shared memory: taps, source vector, then two bands of (band rows + K - 1) x Wp
 __host__ inline size_t fwd_band_smem(const Prob<float>& P, int band_tiles) {
     return 16 + 2 * 33 * sizeof(double) + align_up<float>(sizeof(float) * P.K * P.K, 16) +
-           align_up<float>(sizeof(float) * P.ns, 16) + sizeof(float) * (size_t)(band_tiles * TILE + P.K - 1) * P.Wp;
+           align_up<float>(sizeof(float) * P.ns, 16) +
+           2 * sizeof(float) * (size_t)(band_tiles * TILE + P.K - 1) * P.Wp;
 }
 
 // pixel-ordered ray map of candidate 0 (one ray per pixel)
@@ -150,11 +152,9 @@ __global__ void __launch_bounds__(FWD_THREADS, 1) k_forward_band(const __grid_co
         } else {
             for (int i = tid; i < g.ns; i += bs) s_sh[i] = src[i];
         }
-        double chi = 0.0;
-        for (int b = 0; b < n_bands; ++b) {
-            __syncthreads();  // s staged / the previous band's convolution done
-            // gather L s of padded rows [b BR, b BR + rows) into the band,
-            // four columns per step (row and column advanced without division)
+        // band fill: L s of padded rows [b BR, b BR + rows) into dst, four
+        // columns per step (row and column advanced without division)
+        auto fill = [&](int b, float* dst) {
             const int y0 = b * BR - g.hk;  // image row of band row 0
             const int W4 = g.Wp >> 2, dr = bs / W4, dc = bs - dr * W4;
             int r = tid / W4, c4 = tid - (tid / W4) * W4;
@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(FWD_THREADS, 1) k_forward_band(const __grid_co
                     }
                     val = make_float4(v4[0], v4[1], v4[2], v4[3]);
                 }
-                reinterpret_cast<float4*>(band)[r * W4 + c4] = val;
+                reinterpret_cast<float4*>(dst)[r * W4 + c4] = val;
                 r += dr;
                 c4 += dc;
                 if (c4 >= W4) {
@@ -187,22 +187,42 @@ __global__ void __launch_bounds__(FWD_THREADS, 1) k_forward_band(const __grid_co
                     ++r;
                 }
             }
-            __syncthreads();
-            // one 4x4 output tile per thread
+        };
+        // two band buffers: while band b is convolved, band b + 1 is filled;
+        // odd warps fill first, even warps convolve first, so the fill's
+        // global loads wait while the other half of the warps keep the FMA
+        // pipe busy
+        const int bandsz = rows * g.Wp;
+        const bool fill_first = ((tid >> 5) & 1) != 0;
+        __syncthreads();  // s staged
+        fill(0, band);
+        double chi = 0.0;
+        for (int b = 0; b < n_bands; ++b) {
+            __syncthreads();  // band b filled; band b - 1's convolution done
+            float* cur = band + (b & 1) * bandsz;
+            float* nxt = band + ((b + 1) & 1) * bandsz;
+            if (fill_first && b + 1 < n_bands) fill(b + 1, nxt);
+            // one 4x4 output tile per thread; the chi^2 operands are loaded
+            // before the convolution so that their latency overlaps it
             const int ty_l = tid / g.tiles_x, tx = tid - ty_l * g.tiles_x;
             const int ty = b * BT + ty_l;
             if (ty_l < BT && ty < tiles_y) {
+                V4<float> sw[TILE], dv[TILE];
+#pragma unroll
+                for (int rr = 0; rr < TILE; ++rr) {
+                    const int pp = (ty * TILE + rr + g.hk) * g.Wp + tx * TILE + g.xoff;
+                    sw[rr] = ld4(cs.swp + pp);
+                    dv[rr] = ld4(cs.dpad + pp);
+                }
                 float o16[16];
-                conv_tile_pairs<K>(band + (ty_l * TILE) * g.Wp + tx * TILE, g.Wp, taps, o16);
+                conv_tile_pairs<K>(cur + (ty_l * TILE) * g.Wp + tx * TILE, g.Wp, taps, o16);
                 float ct = 0.f;  // the tile's 16 terms in FP32, then one FP64 add
 #pragma unroll
                 for (int rr = 0; rr < TILE; ++rr) {
                     const int y = ty * TILE + rr;
-                    const int pp = (y + g.hk) * g.Wp + tx * TILE + g.xoff;
-                    const V4<float> sw = ld4(cs.swp + pp), dv = ld4(cs.dpad + pp);
 #pragma unroll
                     for (int cc = 0; cc < TILE; ++cc) {
-                        const float res = sw.v[cc] * (dv.v[cc] - o16[rr * 4 + cc]);
+                        const float res = sw[rr].v[cc] * (dv[rr].v[cc] - o16[rr * 4 + cc]);
                         ct = fmaf(res, res, ct);
                         const int x = tx * TILE + cc;
                         if (FA.model && y < g.ny && x < g.nx)
@@ -211,6 +231,7 @@ __global__ void __launch_bounds__(FWD_THREADS, 1) k_forward_band(const __grid_co
                 }
                 chi += (double)ct;
             }
+            if (!fill_first && b + 1 < n_bands) fill(b + 1, nxt);
         }
         const double cval = block_sum(chi, red, which);
         which ^= 1;

@@ -56,6 +56,14 @@ extern "C" {
 #define MIRAGE_REG_GRADIENT 1  /* H = [Dx; Dy], forward differences, zero beyond the grid */
 #define MIRAGE_REG_LAPLACIAN 2 /* H = 5-point Laplacian, zero beyond the grid */
 
+/* Source-plane interpolation of a traced ray (Section 2.1): bilinear over the
+ * four centres of its cell (TK04), or all its weight on the nearest centre
+ * (WD03's ray shooting; a tie at mid-cell goes to the upper centre).  A ray
+ * is mapped iff it lies within the rectangle of the first and last centres,
+ * for both. */
+#define MIRAGE_INTERP_BILINEAR 0
+#define MIRAGE_INTERP_NEAREST 1
+
 /* per-(candidate, lambda) and per-candidate status bits */
 #define MIRAGE_ST_MAXIT 1        /* CG stopped at maxit above the tolerance */
 #define MIRAGE_ST_STAGNATION 2   /* CG residual stopped decreasing above the tolerance */
@@ -81,6 +89,7 @@ typedef struct {
     int kpsf;             /* PSF side, odd, 1 <= kpsf <= 31 */
     int subpix;           /* n: each pixel traced as n x n sub-pixels (1 <= n <= 8) */
     int reg;              /* MIRAGE_REG_* */
+    int interp;           /* MIRAGE_INTERP_*: source-plane interpolation of each ray */
 } mirage_geom_t;
 
 typedef struct {

@@ -60,10 +60,22 @@ def source_cell(geom, bx, by):
     return mapped, ix0, iy0, u, v
 
 
+INTERP_NEAREST = 1  # geometry.interp: all of a ray's weight on the nearest centre (WD03)
+
+
+def nearest_centre(geom, ix0, iy0, u, v):
+    """Nearest source-pixel centre of points in cell (ix0, iy0) at offsets
+    (u, v): the upper centre of an axis once the offset reaches half a cell."""
+    return ix0 + (u >= 0.5), iy0 + (v >= 0.5)
+
+
 def lens_matrix(geom, lens):
     """Explicit lens operator L as CSR [npix, ns] and the per-pixel mapped flag.
 
-    A pixel is mapped when at least one of its sub-pixel rays is mapped.
+    Bilinear (TK04): each mapped ray spreads 1/N_p over the four centres of
+    its cell with weights (1-u)(1-v), u(1-v), (1-u)v, uv.  Nearest neighbour
+    (geometry.interp == 1, WD03): each mapped ray puts 1/N_p on its nearest
+    centre.  A pixel is mapped when at least one of its sub-pixel rays is.
     """
     tx, ty = image_centres(geom)
     ox, oy = subpixel_offsets(geom.subpix, geom.pix)
@@ -74,6 +86,12 @@ def lens_matrix(geom, lens):
     bx, by = ray_trace(rx, ry, lens)
     mapped, ix0, iy0, u, v = source_cell(geom, bx, by)
     pix_of_ray = np.repeat(np.arange(npix), npsub)
+    if getattr(geom, "interp", 0) == INTERP_NEAREST:
+        jx, jy = nearest_centre(geom, ix0, iy0, u, v)
+        L = sp.csr_matrix((np.full(int(mapped.sum()), 1.0 / npsub),
+                           (pix_of_ray[mapped], (jy * geom.sx + jx)[mapped])), shape=(npix, ns))
+        L.sum_duplicates()
+        return L, mapped.reshape(npix, npsub).any(axis=1)
     rows, cols, vals = [], [], []
     for dx, dy, w in ((0, 0, (1 - u) * (1 - v)), (1, 0, u * (1 - v)),
                       (0, 1, (1 - u) * v), (1, 1, u * v)):

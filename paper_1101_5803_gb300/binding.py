@@ -25,6 +25,7 @@ MIRAGE_OK = 0
 MIRAGE_FP32, MIRAGE_FP64 = 0, 1
 MIRAGE_MEM_DEVICE, MIRAGE_MEM_HOST = 0, 1
 MIRAGE_MODE_BATCHED, MIRAGE_MODE_PLAIN = 0, 1
+MIRAGE_INTERP_BILINEAR, MIRAGE_INTERP_NEAREST = 0, 1
 ST_MAXIT, ST_STAGNATION, ST_BREAKDOWN, ST_BAD_PARAM, ST_EMPTY_MAP, ST_LCURVE_FLAT = 1, 2, 4, 8, 16, 32
 MAX_LAM = 64
 N_PHASE_CLOCKS = 12  # MIRAGE_N_PHASE_CLOCKS
@@ -39,7 +40,7 @@ class mirage_geom_t(ctypes.Structure):
                 ("cx", ctypes.c_double), ("cy", ctypes.c_double), ("sx", ctypes.c_int),
                 ("sy", ctypes.c_int), ("sxmin", ctypes.c_double), ("sxmax", ctypes.c_double),
                 ("symin", ctypes.c_double), ("symax", ctypes.c_double), ("kpsf", ctypes.c_int),
-                ("subpix", ctypes.c_int), ("reg", ctypes.c_int)]
+                ("subpix", ctypes.c_int), ("reg", ctypes.c_int), ("interp", ctypes.c_int)]
 
 
 class mirage_problem_t(ctypes.Structure):
@@ -158,7 +159,8 @@ class Problem:
         g = self.geom
         cg = mirage_geom_t(int(g.nx), int(g.ny), float(g.pix), float(getattr(g, "cx", 0.0)),
                            float(getattr(g, "cy", 0.0)), int(g.sx), int(g.sy), float(g.sxmin), float(g.sxmax),
-                           float(g.symin), float(g.symax), int(g.kpsf), int(getattr(g, "subpix", 1)), int(g.reg))
+                           float(g.symin), float(g.symax), int(g.kpsf), int(getattr(g, "subpix", 1)), int(g.reg),
+                           int(getattr(g, "interp", 0)))
         return mirage_problem_t(cg, self.d.data_ptr(), self.sigma.data_ptr(), self.mask.data_ptr(),
                                 self.psf.data_ptr())
 

@@ -157,6 +157,7 @@ int check_geom(const mirage_geom_t& g) {
     if (g.kpsf < 1 || g.kpsf > 31 || (g.kpsf % 2) == 0) return MIRAGE_ERR_ARG;
     if (g.subpix < 1 || g.subpix > 8) return MIRAGE_ERR_ARG;
     if (g.reg < 0 || g.reg > 2) return MIRAGE_ERR_ARG;
+    if (g.interp != MIRAGE_INTERP_BILINEAR && g.interp != MIRAGE_INTERP_NEAREST) return MIRAGE_ERR_ARG;
     if (!std::isfinite(g.cx) || !std::isfinite(g.cy)) return MIRAGE_ERR_ARG;
     return MIRAGE_OK;
 }
@@ -173,6 +174,7 @@ Prob<T> make_prob(const mirage_problem_t& mp, const void* d, const void* sigma, 
     P.sy = g.sy;
     P.ns = g.sx * g.sy;
     P.reg = g.reg;
+    P.interp = g.interp;
     P.nreg = g.reg == MIRAGE_REG_GRADIENT ? 2 * P.ns : P.ns;
     P.K = g.kpsf;
     P.hk = (g.kpsf - 1) / 2;

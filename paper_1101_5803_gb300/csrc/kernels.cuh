@@ -43,7 +43,7 @@ struct alignas(2 * sizeof(T) > 8 ? 2 * sizeof(T) : 16) Entry {
 // Per-problem constants (device copy).
 template <typename T>
 struct Prob {
-    int nx, ny, npix, sx, sy, ns, nreg, K, hk, n_sub, Np, nrays, ncx, ncells, reg;
+    int nx, ny, npix, sx, sy, ns, nreg, K, hk, n_sub, Np, nrays, ncx, ncells, reg, interp;
     int Wp, Hp, plen, tiles_x, tiles_y, ntiles, kp, xoff;  // padded layout, tap row pitch, left pad
     double pix, cx, cy, sub0, subd, c0x, c0y, hx, hy;  // ray-trace geometry (always FP64)
     T invNp;
@@ -369,6 +369,10 @@ __device__ __forceinline__ void rt_trace_pixels(const Prob<T>& P, const LensT<do
                 e.base = iy0 * P.sx + ix0;
                 e.u = fx - (double)ix0;
                 e.v = fy - (double)iy0;
+                if (P.interp == 1) {  // nearest centre: the one-hot bilinear weights
+                    e.u = e.u >= 0.5 ? 1.0 : 0.0;
+                    e.v = e.v >= 0.5 ? 1.0 : 0.0;
+                }
                 atomicAdd(&counts[iy0 * P.ncx + ix0], 1);
                 any = true;
             } else {

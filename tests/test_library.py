@@ -33,7 +33,7 @@ def test_binding_loads(lib):
 
 
 def test_struct_layouts_match_header():
-    # mirage_geom_t: 2 ints, 3 doubles, 2 ints, 4 doubles, 3 ints (natural alignment)
+    # mirage_geom_t: 2 ints, 3 doubles, 2 ints, 4 doubles, 4 ints (natural alignment, no padding)
     assert ctypes.sizeof(binding.mirage_geom_t) == 88
     assert ctypes.sizeof(binding.mirage_opts_t) == 40  # double + 8 ints
     assert ctypes.sizeof(binding.mirage_problem_t) == 88 + 32

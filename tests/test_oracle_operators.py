@@ -13,6 +13,7 @@ from scipy.signal import convolve2d, correlate2d
 from oracle.lens import ray_trace
 from oracle.operators import (REG_GRADIENT, REG_IDENTITY, REG_LAPLACIAN, blur_matrix, image_centres,
                               lens_matrix, reg_matrix, source_cell, weight_vector)
+import synth
 from synth import Geometry, gaussian_psf
 
 LENS = [1.0, 0.7, 0.5, 0.02, -0.03, 0.05, 1.0]
@@ -159,3 +160,41 @@ def test_hth_positive_definite(reg):
     H = reg_matrix(g, reg).toarray()
     ev = np.linalg.eigvalsh(H.T @ H)
     assert ev.min() > 1e-6
+
+
+def test_nearest_neighbour_lens_matrix_against_brute_force():
+    # every mapped ray's whole weight sits on the closest source-pixel centre
+    # (brute-force distance to all centres); unmapped rays get nothing
+    import dataclasses
+    from oracle.lens import ray_trace
+    from oracle.operators import image_centres, lens_matrix, source_cell
+    g = dataclasses.replace(synth.Geometry(20, 18, 0.09, 9, 8, -0.8, 0.8, -0.7, 0.7, 3, 1, synth.REG_IDENTITY),
+                            interp=synth.INTERP_NEAREST)
+    lens = [1.0, 0.7, 0.5, 0.02, -0.01, 0.05, 1.0]
+    L, mapped = lens_matrix(g, lens)
+    L = L.toarray()
+    tx, ty = image_centres(g)
+    bx, by = ray_trace(tx, ty, lens)
+    m, *_ = source_cell(g, bx, by)
+    hx, hy = (g.sxmax - g.sxmin) / g.sx, (g.symax - g.symin) / g.sy
+    cxs = g.sxmin + (np.arange(g.sx) + 0.5) * hx
+    cys = g.symin + (np.arange(g.sy) + 0.5) * hy
+    for j in range(g.npix):
+        if not m[j]:
+            assert not L[j].any()
+            continue
+        d2 = (cxs[None, :] - bx[j]) ** 2 + (cys[:, None] - by[j]) ** 2
+        k = int(np.argmin(d2))
+        assert L[j, k] == 1.0 and L[j].sum() == 1.0, j
+    assert m.sum() > 50
+
+
+def test_nearest_neighbour_identity_lens():
+    # centres on the pixel centres and no deflection: L = I
+    import dataclasses
+    from oracle.operators import lens_matrix
+    g = dataclasses.replace(synth.Geometry(12, 8, 0.25, 12, 8, -1.5, 1.5, -1.0, 1.0, 3, 1, synth.REG_IDENTITY),
+                            interp=synth.INTERP_NEAREST)
+    L, mapped = lens_matrix(g, [0, 0.8, 0, 0, 0, 0, 0])
+    np.testing.assert_allclose(L.toarray(), np.eye(96), atol=0)
+    assert mapped.all()

@@ -370,6 +370,16 @@ def run_gpu(args):
     ga_res["generations"] = n_gen
     ga_res["oversample"] = 4
 
+    # particle swarm (Eq. PSO) on the same problem: one batched call per step
+    from paper_1101_5803_gb300.pso import PSOConfig, batch_evaluator, run_pso
+    phist, _, _ = run_pso(batch_evaluator(ctx, wl), PSOConfig(particles=N_CAND, steps=n_gen, seed=7))
+    psteps = phist[1:]
+    t_pso = sum(h.seconds for h in psteps)
+    pso_res = {"particles": N_CAND, "steps": n_gen,
+               "exact_evals_per_s": sum(h.evals for h in psteps) / t_pso,
+               "cg_iters_per_exact_eval": sum(h.cg_iters for h in psteps) / max(1, sum(h.evals for h in psteps)),
+               "best_chi2_by_step": [round(h.best_chi2, 2) for h in phist]}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         v, done, dt = oracle_evals_per_s(64, seed=7, budget_s=float(os.environ.get("MIRAGE_CPU_BUDGET", "20")))
@@ -403,6 +413,7 @@ def run_gpu(args):
                    "status_bits_any": int(np.bitwise_or.reduce(status))},
             "phase_ms": {"raytrace": phase[0], "cgls": phase[1], "finalize": phase[2]},
             "ga_surrogate": ga_res,
+            "pso": pso_res,
             "iter_lcurve": iter_res,
             "forward_batch": fwd_res}
     if rank == 0:

@@ -57,12 +57,16 @@ extern "C" {
 #define MIRAGE_REG_LAPLACIAN 2 /* H = 5-point Laplacian, zero beyond the grid */
 
 /* Source-plane interpolation of a traced ray (Section 2.1): bilinear over the
- * four centres of its cell (TK04), or all its weight on the nearest centre
- * (WD03's ray shooting; a tie at mid-cell goes to the upper centre).  A ray
- * is mapped iff it lies within the rectangle of the first and last centres,
- * for both. */
+ * four centres of its cell (TK04); all its weight on the nearest centre
+ * (WD03's ray shooting; a tie at mid-cell goes to the upper centre); or
+ * bicubic over the 4 x 4 centres around its cell with Keys' cubic-convolution
+ * kernel (a = -1/2), centres beyond the grid holding no source.  A ray is
+ * mapped iff it lies within the rectangle of the first and last centres, for
+ * all three.  Bicubic problems run on the general CGLS kernel and the
+ * general forward kernel. */
 #define MIRAGE_INTERP_BILINEAR 0
 #define MIRAGE_INTERP_NEAREST 1
+#define MIRAGE_INTERP_BICUBIC 2
 
 /* per-(candidate, lambda) and per-candidate status bits */
 #define MIRAGE_ST_MAXIT 1        /* CG stopped at maxit above the tolerance */

@@ -61,6 +61,20 @@ def source_cell(geom, bx, by):
 
 
 INTERP_NEAREST = 1  # geometry.interp: all of a ray's weight on the nearest centre (WD03)
+INTERP_BICUBIC = 2  # geometry.interp: Keys' cubic convolution over the 4 x 4 nearby centres
+
+KEYS_A = -0.5  # the cubic-convolution parameter that makes the interpolant third-order accurate
+
+
+def keys_kernel(t):
+    """Keys' cubic-convolution kernel W(t) (Keys 1981) with a = -1/2:
+    (a+2)|t|^3 - (a+3)|t|^2 + 1 for |t| <= 1, a|t|^3 - 5a|t|^2 + 8a|t| - 4a
+    for 1 < |t| < 2, and 0 beyond."""
+    a = KEYS_A
+    t = np.abs(np.asarray(t, dtype=np.float64))
+    inner = (a + 2) * t ** 3 - (a + 3) * t ** 2 + 1
+    outer = a * t ** 3 - 5 * a * t ** 2 + 8 * a * t - 4 * a
+    return np.where(t <= 1, inner, np.where(t < 2, outer, 0.0))
 
 
 def nearest_centre(geom, ix0, iy0, u, v):
@@ -75,7 +89,12 @@ def lens_matrix(geom, lens):
     Bilinear (TK04): each mapped ray spreads 1/N_p over the four centres of
     its cell with weights (1-u)(1-v), u(1-v), (1-u)v, uv.  Nearest neighbour
     (geometry.interp == 1, WD03): each mapped ray puts 1/N_p on its nearest
-    centre.  A pixel is mapped when at least one of its sub-pixel rays is.
+    centre.  Bicubic (geometry.interp == 2, Section 2.1): each mapped ray
+    puts 1/N_p W(dx) W(dy) on every centre, dx and dy its distances to the
+    centre in cell widths and W Keys' kernel, so only the 4 x 4 centres
+    around its cell get weight; centres beyond the grid do not exist, so
+    their share is dropped.  A pixel is mapped when at least one of its
+    sub-pixel rays is.
     """
     tx, ty = image_centres(geom)
     ox, oy = subpixel_offsets(geom.subpix, geom.pix)
@@ -93,6 +112,19 @@ def lens_matrix(geom, lens):
         L.sum_duplicates()
         return L, mapped.reshape(npix, npsub).any(axis=1)
     rows, cols, vals = [], [], []
+    if getattr(geom, "interp", 0) == INTERP_BICUBIC:
+        fx, fy = ix0 + u, iy0 + v  # ray position in centre units
+        for jy in range(-1, 3):
+            for jx in range(-1, 3):
+                cx, cy = ix0 + jx, iy0 + jy
+                ok = mapped & (cx >= 0) & (cx < geom.sx) & (cy >= 0) & (cy < geom.sy)
+                rows.append(pix_of_ray[ok])
+                cols.append((cy * geom.sx + cx)[ok])
+                vals.append((keys_kernel(fx - cx) * keys_kernel(fy - cy))[ok] / npsub)
+        L = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                          shape=(npix, ns))
+        L.sum_duplicates()
+        return L, mapped.reshape(npix, npsub).any(axis=1)
     for dx, dy, w in ((0, 0, (1 - u) * (1 - v)), (1, 0, u * (1 - v)),
                       (0, 1, (1 - u) * v), (1, 1, u * v)):
         rows.append(pix_of_ray[mapped])

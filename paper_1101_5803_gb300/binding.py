@@ -25,7 +25,8 @@ MIRAGE_OK = 0
 MIRAGE_FP32, MIRAGE_FP64 = 0, 1
 MIRAGE_MEM_DEVICE, MIRAGE_MEM_HOST = 0, 1
 MIRAGE_MODE_BATCHED, MIRAGE_MODE_PLAIN = 0, 1
-MIRAGE_INTERP_BILINEAR, MIRAGE_INTERP_NEAREST = 0, 1
+MIRAGE_INTERP_BILINEAR, MIRAGE_INTERP_NEAREST, MIRAGE_INTERP_BICUBIC = 0, 1, 2
+MIRAGE_REG_IDENTITY, MIRAGE_REG_GRADIENT, MIRAGE_REG_LAPLACIAN = 0, 1, 2
 ST_MAXIT, ST_STAGNATION, ST_BREAKDOWN, ST_BAD_PARAM, ST_EMPTY_MAP, ST_LCURVE_FLAT = 1, 2, 4, 8, 16, 32
 MAX_LAM = 64
 N_PHASE_CLOCKS = 12  # MIRAGE_N_PHASE_CLOCKS

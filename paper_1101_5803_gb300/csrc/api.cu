@@ -157,7 +157,8 @@ int check_geom(const mirage_geom_t& g) {
     if (g.kpsf < 1 || g.kpsf > 31 || (g.kpsf % 2) == 0) return MIRAGE_ERR_ARG;
     if (g.subpix < 1 || g.subpix > 8) return MIRAGE_ERR_ARG;
     if (g.reg < 0 || g.reg > 2) return MIRAGE_ERR_ARG;
-    if (g.interp != MIRAGE_INTERP_BILINEAR && g.interp != MIRAGE_INTERP_NEAREST) return MIRAGE_ERR_ARG;
+    if (g.interp != MIRAGE_INTERP_BILINEAR && g.interp != MIRAGE_INTERP_NEAREST && g.interp != MIRAGE_INTERP_BICUBIC)
+        return MIRAGE_ERR_ARG;
     if (!std::isfinite(g.cx) || !std::isfinite(g.cy)) return MIRAGE_ERR_ARG;
     return MIRAGE_OK;
 }
@@ -252,7 +253,7 @@ const void* pick_fwd(int prec, int K) {
 // two-CTA-per-SM kernel when the problem qualifies (FP32 contexts only)
 template <typename T>
 const void* pick_fast(mirage_ctx* ctx, const Prob<T>& P, int mode) {
-    if (sizeof(T) != 4) return nullptr;
+    if (sizeof(T) != 4 || P.interp == MIRAGE_INTERP_BICUBIC) return nullptr;  // four-corner rays only
     const Prob<float>& Pf = *reinterpret_cast<const Prob<float>*>(&P);
     const size_t b = fast_smem_bytes(Pf);
     if (b == 0 || (long long)b > ctx->max_smem_sm / 2 - 1024 || Pf.K >= MAX_K) return nullptr;
@@ -1000,7 +1001,9 @@ int forward_impl(mirage_ctx* ctx, const mirage_problem_t* prob, const double* le
     TRY(launch_raytrace<T>(ctx, dprob, dcand, lens, 0, 1, cs, P.ncells, (long long)P.npix, st));
     if constexpr (sizeof(T) == 4) {
         // banded kernel: taps as kernel parameters, L s gathered into shared memory
-        const void* fb = (P.Np == 1 && P.K < MAX_K && P.K * P.K <= MAX_FTAP) ? tb.fwdb[P.K] : nullptr;
+        const void* fb = (P.Np == 1 && P.interp != MIRAGE_INTERP_BICUBIC && P.K < MAX_K && P.K * P.K <= MAX_FTAP)
+                             ? tb.fwdb[P.K]
+                             : nullptr;
         if (fb && P.tiles_x <= FWD_THREADS) {
             const int bt = std::min(FWD_THREADS / P.tiles_x, P.tiles_y);
             const size_t smb = fwd_band_smem(P, bt);

@@ -475,7 +475,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_cgls_fast(const __grid_constant
         double rs = 0;
         for (int i = tid; i < g.ns; i += bs) {
             const int ib = i / g.sx, ia = i - ib * g.sx;
-            const double v = apply_LT_at<T, double, double>(g, w.E64, w.cst, w.Pc, ia, ib);
+            const double v = apply_LT_at<T, double, double, false>(g, w.E64, w.cst, w.Pc, ia, ib);
             rs += v * v;
         }
         const double rhsn = sqrt(block_sum(rs, red, which));

@@ -88,6 +88,7 @@ __device__ __forceinline__ Geo<double> geo_fp64(const Geo<T>& g) {
     d.ntiles = g.ntiles;
     d.reg = g.reg;
     d.nent = g.nent;
+    d.interp = g.interp;
     d.invNp = (double)g.invNp;
     return d;
 }

@@ -811,7 +811,7 @@ __device__ __forceinline__ void conv_tile_rt(const S* __restrict__ Pb, int Wp, c
 // geometry needed inside the solver loops (passed by value)
 template <typename T>
 struct Geo {
-    int nx, ny, sx, sy, ns, nreg, K, hk, kp, xoff, sh, Np, ncx, ncells, Wp, plen, tiles_x, ntiles, reg, nent;
+    int nx, ny, sx, sy, ns, nreg, K, hk, kp, xoff, sh, Np, ncx, ncells, Wp, plen, tiles_x, ntiles, reg, nent, interp;
     T invNp;
 };
 
@@ -838,6 +838,7 @@ __device__ __forceinline__ Geo<T> geo_of(const Prob<T>& P, int nent) {
     g.ntiles = P.ntiles;
     g.reg = P.reg;
     g.nent = nent;
+    g.interp = P.interp;
     g.invNp = P.invNp;
     return g;
 }
@@ -870,12 +871,105 @@ struct Work {
     double* Pc;       // [plen] B^T sqrt(W) r64
 };
 
-// dst <- L v (Section 2.2: bilinear interpolation of the back-traced rays,
-// averaged over sub-pixels).  Only mapped pixels are written; the rest of
-// dst must hold zeros.
+// Bicubic interpolation (Section 2.1 lists it beside bilinear): Keys'
+// cubic-convolution kernel with a = -1/2, W(t) = 3/2|t|^3 - 5/2|t|^2 + 1 on
+// |t| <= 1 and -1/2|t|^3 + 5/2|t|^2 - 4|t| + 2 on 1 < |t| < 2.  A ray at
+// offset u in its cell weighs the centres at -1, 0, 1, 2 along each axis by
+// W(1 + u), W(u), W(1 - u), W(2 - u), written out below as cubics in u.
+// Centres beyond the grid hold no source and are skipped.
+template <typename V>
+__device__ __forceinline__ V keys_weight(int i, V u) {
+    const V u2 = u * u, u3 = u2 * u;
+    switch (i) {
+        case 0: return (V)0.5 * (-u3 + (V)2 * u2 - u);
+        case 1: return (V)0.5 * ((V)3 * u3 - (V)5 * u2 + (V)2);
+        case 2: return (V)0.5 * ((V)-3 * u3 + (V)4 * u2 + u);
+        default: return (V)0.5 * (u3 - u2);
+    }
+}
+
+// one ray's bicubic sample of v (without the 1/N_p)
+template <typename T, typename ET, typename V>
+__device__ __forceinline__ V bicubic_sample(const Geo<T>& g, const Entry<ET>& en, const V* __restrict__ v) {
+    const int iy0 = en.base / g.sx, ix0 = en.base - iy0 * g.sx;
+    V acc = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int y = iy0 - 1 + j;
+        if (y < 0 || y >= g.sy) continue;
+        V row = 0;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int x = ix0 - 1 + i;
+            if (x >= 0 && x < g.sx) row += keys_weight(i, (V)en.u) * v[y * g.sx + x];
+        }
+        acc += keys_weight(j, (V)en.v) * row;
+    }
+    return acc;
+}
+
+// L v for bicubic rays (out of line, like the two below: kernels that also
+// run bilinear problems keep their register allocation)
+template <typename T, typename ET, typename V, typename D>
+__device__ __noinline__ void bicubic_L(const Geo<T>& g, const Entry<ET>* __restrict__ Ent, const int* __restrict__ inv,
+                                       const V* __restrict__ v, D* __restrict__ dst) {
+    if (g.Np == 1) {
+        for (int k = threadIdx.x; k < g.nent; k += blockDim.x) {
+            const Entry<ET> en = Ent[k];
+            dst[en.ppos] = (D)bicubic_sample(g, en, v);
+        }
+        return;
+    }
+    const int npix = g.nx * g.ny;
+    for (int j = threadIdx.x; j < npix; j += blockDim.x) {
+        V val = 0;
+        int pp = -1;
+        for (int a = 0; a < g.Np; ++a) {
+            const int e = inv[j * g.Np + a];
+            if (e >= 0) {
+                const Entry<ET> en = Ent[e];
+                val += bicubic_sample(g, en, v);
+                pp = en.ppos;
+            }
+        }
+        if (pp >= 0) dst[pp] = (D)(val * (V)g.invNp);
+    }
+}
+
+// (L^T U)_i for bicubic rays: the 4 x 4 cells whose rays reach (ia, ib), in
+// a fixed order
+template <typename T, typename ET, typename V>
+__device__ __noinline__ V bicubic_LT_at(const Geo<T>& g, const Entry<ET>* __restrict__ Ent,
+                                        const int* __restrict__ cst, const V* __restrict__ U, int ia, int ib) {
+    V acc = 0;
+    for (int j = 0; j < 4; ++j) {
+        const int iy0 = ib + 1 - j;
+        if (iy0 < 0 || iy0 > g.sy - 2) continue;
+        for (int i = 0; i < 4; ++i) {
+            const int ix0 = ia + 1 - i;
+            if (ix0 < 0 || ix0 > g.sx - 2) continue;
+            const int cell = iy0 * g.ncx + ix0;
+            const int k1 = cst[cell + 1];
+            for (int k = cst[cell]; k < k1; ++k) {
+                const Entry<ET> en = Ent[k];
+                acc += keys_weight(i, (V)en.u) * keys_weight(j, (V)en.v) * U[en.ppos];
+            }
+        }
+    }
+    return acc * (V)g.invNp;
+}
+
+// dst <- L v (Section 2.2: interpolation of the back-traced rays, averaged
+// over sub-pixels; bilinear, or nearest neighbour through snapped offsets,
+// or bicubic).  Only mapped pixels are written; the rest of dst must hold
+// zeros.
 template <typename T, typename ET, typename V, typename D>
 __device__ __forceinline__ void apply_L(const Geo<T>& g, const Entry<ET>* __restrict__ Ent, const int* __restrict__ inv,
                                         const V* __restrict__ v, D* __restrict__ dst) {
+    if (g.interp == 2) {
+        bicubic_L(g, Ent, inv, v, dst);
+        return;
+    }
     if (g.Np == 1) {
         for (int k = threadIdx.x; k < g.nent; k += blockDim.x) {
             const Entry<ET> en = Ent[k];
@@ -906,9 +1000,11 @@ __device__ __forceinline__ void apply_L(const Geo<T>& g, const Entry<ET>* __rest
 
 // (L^T U)_i: gather over the rays of the (up to) four cells having source
 // pixel (ia, ib) as a corner, in sorted (deterministic) order
-template <typename T, typename ET, typename V>
+// (BICUBIC = false: a caller that never sees bicubic rays skips the branch)
+template <typename T, typename ET, typename V, bool BICUBIC = true>
 __device__ __forceinline__ V apply_LT_at(const Geo<T>& g, const Entry<ET>* __restrict__ Ent,
                                          const int* __restrict__ cst, const V* __restrict__ U, int ia, int ib) {
+    if (BICUBIC && g.interp == 2) return bicubic_LT_at(g, Ent, cst, U, ia, ib);
     V acc = 0;
 #pragma unroll
     for (int dy = 0; dy < 2; ++dy) {
@@ -973,6 +1069,30 @@ __device__ __forceinline__ V apply_HT_at(const Geo<T>& g, const V* __restrict__ 
     return acc;
 }
 
+// lwl_diag_at for bicubic rays
+template <typename T>
+__device__ __noinline__ T bicubic_diag_at(const Geo<T>& g, const Entry<T>* __restrict__ Ent,
+                                          const int* __restrict__ cst, const double* __restrict__ omega, int ia,
+                                          int ib) {
+    T acc = 0;
+    for (int j = 0; j < 4; ++j) {
+        const int iy0 = ib + 1 - j;
+        if (iy0 < 0 || iy0 > g.sy - 2) continue;
+        for (int i = 0; i < 4; ++i) {
+            const int ix0 = ia + 1 - i;
+            if (ix0 < 0 || ix0 > g.sx - 2) continue;
+            const int cell = iy0 * g.ncx + ix0;
+            const int k1 = cst[cell + 1];
+            for (int k = cst[cell]; k < k1; ++k) {
+                const Entry<T> en = Ent[k];
+                const T wt = keys_weight(i, en.u) * keys_weight(j, en.v) * g.invNp;
+                acc += wt * wt * (T)omega[en.ppos];
+            }
+        }
+    }
+    return acc;
+}
+
 // Approximate diagonal of the inner normal operator L^T B^T W B L at source
 // pixel (ia, ib): sum over the rays of its cells of (bilinear weight / N_p)^2
 // times omega at the ray's pixel, omega_p = diag(B^T W B)_p = sum_k psf_k^2
@@ -983,6 +1103,7 @@ __device__ __forceinline__ V apply_HT_at(const Geo<T>& g, const V* __restrict__ 
 template <typename T>
 __device__ __forceinline__ T lwl_diag_at(const Geo<T>& g, const Entry<T>* __restrict__ Ent, const int* __restrict__ cst,
                                          const double* __restrict__ omega, int ia, int ib) {
+    if (g.interp == 2) return bicubic_diag_at(g, Ent, cst, omega, ia, ib);
     T acc = 0;
 #pragma unroll
     for (int dy = 0; dy < 2; ++dy) {
@@ -1513,7 +1634,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_cgls(CglsArgs<T> A) {
                 __syncthreads();
             }
             const int stag_window = max(4000, 2 * g.ns);
-            const bool cells_fit = 4 * g.ncells <= g.plen;  // the cell sums fit in P2
+            // per-cell L^T sums: bilinear and nearest only, when they fit in P2
+            const bool cells_fit = g.interp != 2 && 4 * g.ncells <= g.plen;
             while (!ctl->stop) {
                 // q = A~ p: image part sqrt(W) B L p, regulariser part sqrt(lam) H p
                 apply_L<T, T, T, T>(g, w.E, w.inv, w.p, w.P1);

@@ -21,8 +21,10 @@ import numpy as np
 # 5-point Laplacian).
 REG_IDENTITY, REG_GRADIENT, REG_LAPLACIAN = 0, 1, 2
 
+# Source-plane interpolation codes (Section 2.1).
+INTERP_BILINEAR, INTERP_NEAREST, INTERP_BICUBIC = 0, 1, 2
+
 # Lens parameter vector: SIE (Eqs. SIEX/SIEY) plus external shear.
-INTERP_BILINEAR, INTERP_NEAREST = 0, 1
 LENS_KEYS = ("b", "q", "phi", "x0", "y0", "gamma", "theta_g")
 
 
@@ -50,7 +52,7 @@ class Geometry:
     reg: int = REG_LAPLACIAN
     cx: float = 0.0
     cy: float = 0.0
-    interp: int = 0  # INTERP_BILINEAR or INTERP_NEAREST
+    interp: int = 0  # INTERP_BILINEAR, INTERP_NEAREST or INTERP_BICUBIC
 
     @property
     def npix(self) -> int:

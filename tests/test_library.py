@@ -5,6 +5,7 @@ import os
 
 import pytest
 
+import synth
 from paper_1101_5803_gb300 import binding
 from paper_1101_5803_gb300.build import build
 
@@ -44,3 +45,9 @@ def test_header_constants_match_binding():
     txt = open(binding.HEADER).read()
     assert int(re.search(r"#define MIRAGE_N_PHASE_CLOCKS (\d+)", txt).group(1)) == binding.N_PHASE_CLOCKS
     assert int(re.search(r"#define MIRAGE_MAX_LAM (\d+)", txt).group(1)) == binding.MAX_LAM
+    for name in ("MIRAGE_INTERP_BILINEAR", "MIRAGE_INTERP_NEAREST", "MIRAGE_INTERP_BICUBIC",
+                 "MIRAGE_REG_IDENTITY", "MIRAGE_REG_GRADIENT", "MIRAGE_REG_LAPLACIAN"):
+        m = re.search(r"#define %s (\d+)" % name, txt)
+        assert m and int(m.group(1)) == getattr(binding, name), name
+    assert (binding.MIRAGE_INTERP_NEAREST, binding.MIRAGE_INTERP_BICUBIC) == (synth.INTERP_NEAREST,
+                                                                              synth.INTERP_BICUBIC)

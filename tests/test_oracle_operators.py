@@ -198,3 +198,113 @@ def test_nearest_neighbour_identity_lens():
     L, mapped = lens_matrix(g, [0, 0.8, 0, 0, 0, 0, 0])
     np.testing.assert_allclose(L.toarray(), np.eye(96), atol=0)
     assert mapped.all()
+
+
+# ---------------------------------------------------------------------------
+# bicubic interpolation (Keys' cubic convolution, a = -1/2)
+# ---------------------------------------------------------------------------
+def test_keys_kernel_is_an_interpolating_c1_cubic():
+    from oracle.operators import keys_kernel
+    # interpolating: 1 at the own centre, 0 at every other centre
+    np.testing.assert_array_equal(keys_kernel([0.0, 1.0, -1.0, 2.0, -2.0, 3.0]), [1, 0, 0, 0, 0, 0])
+    t = np.linspace(-2.5, 2.5, 1001)
+    np.testing.assert_allclose(keys_kernel(t), keys_kernel(-t), atol=0)
+    assert np.all(keys_kernel(t[np.abs(t) >= 2]) == 0)
+    # continuous with a continuous slope at the knots |t| = 1, 2
+    h = 1e-7
+    for k in (1.0, 2.0):
+        left, right = keys_kernel(k - h), keys_kernel(k + h)
+        assert abs(left - right) < 1e-6
+        dl = (keys_kernel(k - h) - keys_kernel(k - 2 * h)) / h
+        dr = (keys_kernel(k + 2 * h) - keys_kernel(k + h)) / h
+        assert abs(dl - dr) < 1e-5, (k, dl, dr)
+
+
+def test_keys_weights_reproduce_quadratics_and_the_midpoint_rule():
+    # sum_j W(u - j) j^m = u^m for m = 0, 1, 2 (the kernel's third-order
+    # accuracy, Keys 1981); a cubic is not reproduced
+    from oracle.operators import keys_kernel
+    j = np.arange(-1, 3)
+    for u in np.linspace(0, 1, 13):
+        w = keys_kernel(u - j)
+        for m in range(3):
+            assert abs((w * j ** m).sum() - u ** m) < 1e-14, (u, m)
+    w = keys_kernel(0.3 - j)
+    assert abs((w * j ** 3).sum() - 0.3 ** 3) > 1e-3
+    # halfway between two centres: the four-point rule (-1, 9, 9, -1)/16
+    np.testing.assert_allclose(keys_kernel(0.5 - j), np.array([-1, 9, 9, -1]) / 16.0, atol=1e-15)
+
+
+def _bicubic_geom(nx=20, ny=18, subpix=1):
+    import dataclasses
+    return dataclasses.replace(synth.Geometry(nx, ny, 0.09, 9, 8, -0.8, 0.8, -0.7, 0.7, 3, subpix, synth.REG_IDENTITY),
+                               interp=synth.INTERP_BICUBIC)
+
+
+def test_bicubic_lens_matrix_against_brute_force():
+    # every centre of the grid weighted by W(dx) W(dy) from the traced
+    # position, without using the cell of the ray
+    from oracle.lens import ray_trace
+    from oracle.operators import image_centres, keys_kernel, lens_matrix, source_cell
+    g = _bicubic_geom()
+    lens = [1.0, 0.7, 0.5, 0.02, -0.01, 0.05, 1.0]
+    L, mapped = lens_matrix(g, lens)
+    L = L.toarray()
+    tx, ty = image_centres(g)
+    bx, by = ray_trace(tx, ty, lens)
+    m, *_ = source_cell(g, bx, by)
+    hx, hy = (g.sxmax - g.sxmin) / g.sx, (g.symax - g.symin) / g.sy
+    cxs = g.sxmin + (np.arange(g.sx) + 0.5) * hx
+    cys = g.symin + (np.arange(g.sy) + 0.5) * hy
+    for j in range(g.npix):
+        if not m[j]:
+            assert not L[j].any()
+            continue
+        w = keys_kernel((cys[:, None] - by[j]) / hy) * keys_kernel((cxs[None, :] - bx[j]) / hx)
+        np.testing.assert_allclose(L[j], w.ravel(), atol=1e-14)
+    assert m.sum() > 50
+
+
+def test_bicubic_lens_matrix_reproduces_biquadratic_sources():
+    # s = f at the centres, f a product-space quadratic: L s = f at every ray
+    # whose 4 x 4 centres all lie in the grid (bilinear would miss the curvature)
+    from oracle.lens import ray_trace
+    from oracle.operators import image_centres, lens_matrix, source_cell
+    g = _bicubic_geom()
+    lens = [1.0, 0.7, 0.5, 0.02, -0.01, 0.05, 1.0]
+    L, _ = lens_matrix(g, lens)
+    hx, hy = (g.sxmax - g.sxmin) / g.sx, (g.symax - g.symin) / g.sy
+    cx = g.sxmin + (np.arange(g.sx) + 0.5) * hx
+    cy = g.symin + (np.arange(g.sy) + 0.5) * hy
+
+    def f(x, y):
+        return 1 + 0.3 * x - 0.7 * y + 0.9 * x * x - 0.4 * x * y + 0.6 * y * y + 0.8 * x * x * y * y
+
+    s = f(cx[None, :], cy[:, None]).ravel()
+    tx, ty = image_centres(g)
+    bx, by = ray_trace(tx, ty, lens)
+    m, ix0, iy0, _, _ = source_cell(g, bx, by)
+    inner = m & (ix0 >= 1) & (ix0 <= g.sx - 3) & (iy0 >= 1) & (iy0 <= g.sy - 3)
+    assert inner.sum() > 20
+    np.testing.assert_allclose((L @ s)[inner], f(bx, by)[inner], atol=1e-12)
+    # the bilinear operator does not reproduce it
+    import dataclasses
+    Lb, _ = lens_matrix(dataclasses.replace(g, interp=synth.INTERP_BILINEAR), lens)
+    assert np.abs((Lb @ s)[inner] - f(bx, by)[inner]).max() > 1e-4
+
+
+def test_bicubic_identity_lens_and_subpixel_average():
+    import dataclasses
+    from oracle.operators import lens_matrix
+    g = dataclasses.replace(synth.Geometry(12, 8, 0.25, 12, 8, -1.5, 1.5, -1.0, 1.0, 3, 1, synth.REG_IDENTITY),
+                            interp=synth.INTERP_BICUBIC)
+    L, mapped = lens_matrix(g, [0, 0.8, 0, 0, 0, 0, 0])
+    np.testing.assert_allclose(L.toarray(), np.eye(96), atol=1e-15)
+    assert mapped.all()
+    # with 2 x 2 sub-pixels each row averages its rays: rows of interior
+    # pixels (all four rays' centres in the grid) sum to one
+    g2 = _bicubic_geom(subpix=2)
+    L2, m2 = lens_matrix(g2, [1.0, 0.7, 0.5, 0.02, -0.01, 0.05, 1.0])
+    rows = np.asarray(L2.sum(axis=1)).ravel()
+    assert np.all(rows[~m2] == 0)
+    assert np.isclose(rows[m2], 1.0, atol=1e-12).sum() > 0.5 * m2.sum()

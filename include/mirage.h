@@ -90,7 +90,7 @@ typedef struct {
     int sx, sy;           /* source grid size (>= 2 each) */
     double sxmin, sxmax;  /* source grid edges on x (sxmax > sxmin) */
     double symin, symax;  /* source grid edges on y */
-    int kpsf;             /* PSF side, odd, 1 <= kpsf <= 31 */
+    int kpsf;             /* PSF side, odd, 1 <= kpsf <= MIRAGE_MAX_KPSF */
     int subpix;           /* n: each pixel traced as n x n sub-pixels (1 <= n <= 8) */
     int reg;              /* MIRAGE_REG_* */
     int interp;           /* MIRAGE_INTERP_*: source-plane interpolation of each ray */
@@ -121,8 +121,12 @@ typedef struct {
     int variant;       /* CGLS kernel choice: 0 = automatic; 1 = two-CTA kernel with taps
                           in shared memory; 2 = two-CTA kernel with taps as kernel
                           parameters (FFMA); 3 = the same with packed FFMA2; 4 = the
-                          general one-CTA kernel.  Forced choices fall back to the
-                          general kernel where they do not apply. */
+                          general one-CTA kernel; 5 = the general kernel with every
+                          convolution by FFT (Section 2.2); 6 = the general kernel
+                          with direct convolution at any PSF width.  Automatic
+                          choice: FFT for PSFs of 23 x 23 and wider, direct below.
+                          Forced choices fall back to the general kernel where
+                          they do not apply. */
 } mirage_opts_t;
 
 typedef struct mirage_ctx mirage_ctx_t;
@@ -136,6 +140,7 @@ int mirage_create(mirage_ctx_t** ctx, int device, int precision);
 int mirage_destroy(mirage_ctx_t* ctx);
 
 #define MIRAGE_MAX_LAM 64 /* longest lambda grid of one candidate */
+#define MIRAGE_MAX_KPSF 65 /* widest PSF (the 65 x 65 class of the paper's large test, Section 2.7) */
 
 /* Evaluate n_cand candidate lenses (the inner loop of Section 3: ray trace,
  * CGLS on Eq. TKReg for every lambda of the candidate, L-curve corner).

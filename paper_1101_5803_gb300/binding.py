@@ -29,6 +29,7 @@ MIRAGE_INTERP_BILINEAR, MIRAGE_INTERP_NEAREST, MIRAGE_INTERP_BICUBIC = 0, 1, 2
 MIRAGE_REG_IDENTITY, MIRAGE_REG_GRADIENT, MIRAGE_REG_LAPLACIAN = 0, 1, 2
 ST_MAXIT, ST_STAGNATION, ST_BREAKDOWN, ST_BAD_PARAM, ST_EMPTY_MAP, ST_LCURVE_FLAT = 1, 2, 4, 8, 16, 32
 MAX_LAM = 64
+MAX_KPSF = 65  # MIRAGE_MAX_KPSF
 N_PHASE_CLOCKS = 12  # MIRAGE_N_PHASE_CLOCKS
 
 

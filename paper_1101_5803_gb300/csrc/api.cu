@@ -115,6 +115,7 @@ struct mirage_ctx {
     DevBuf stage;  // MIRAGE_MEM_HOST staging
     DevBuf fE, fE64, fEtmp, finv, fcst, fswp, fdpad, fnent, fcstat, fslab, fprob, fcand, fpix;
     DevBuf rt_cursor;  // per-cell cursors of the parallel ray placement
+    DevBuf spec;       // PSF spectra of the FFT-convolution problems (FP64, then FP32)
     // pinned staging of the per-call uploads (problem descriptors, item
     // tables): the copies stay asynchronous; the event guards reuse
     void* pin = nullptr;
@@ -154,7 +155,7 @@ int check_geom(const mirage_geom_t& g) {
     if (g.nx < 1 || g.ny < 1 || g.nx > 4096 || g.ny > 4096) return MIRAGE_ERR_ARG;
     if (g.sx < 2 || g.sy < 2 || (long long)g.sx * g.sy > (1 << 20)) return MIRAGE_ERR_ARG;
     if (!(g.pix > 0) || !(g.sxmax > g.sxmin) || !(g.symax > g.symin)) return MIRAGE_ERR_ARG;
-    if (g.kpsf < 1 || g.kpsf > 31 || (g.kpsf % 2) == 0) return MIRAGE_ERR_ARG;
+    if (g.kpsf < 1 || g.kpsf > MIRAGE_MAX_KPSF || (g.kpsf % 2) == 0) return MIRAGE_ERR_ARG;
     if (g.subpix < 1 || g.subpix > 8) return MIRAGE_ERR_ARG;
     if (g.reg < 0 || g.reg > 2) return MIRAGE_ERR_ARG;
     if (g.interp != MIRAGE_INTERP_BILINEAR && g.interp != MIRAGE_INTERP_NEAREST && g.interp != MIRAGE_INTERP_BICUBIC)
@@ -232,21 +233,44 @@ int set_smem(mirage_ctx* ctx, const void* fn, size_t bytes) {
 
 const void* pick_cgls(int prec, int place, int K) {
     const KernelTable& t = table();
-    const void* f = t.cgls[prec][place][K];
+    const void* f = K < MAX_K ? t.cgls[prec][place][K] : nullptr;  // wider PSFs: the runtime-K kernel
     return f ? f : t.cgls[prec][place][0];
 }
 
 // placement of the general kernel's work buffers for one problem
 template <typename T>
 int pick_place(const mirage_ctx* ctx, const Prob<T>& P) {
+    if (P.fft_m) return PLACE_GLOBAL;  // the FFT path lives in the runtime-K global-memory kernel
     if (smem_bytes<T>(P, PLACE_SMEM) <= (size_t)ctx->max_smem) return PLACE_SMEM;
     if (sizeof(T) == 4 && smem_bytes<T>(P, PLACE_MID) <= (size_t)ctx->max_smem) return PLACE_MID;
     return PLACE_GLOBAL;
 }
 
+// FFT convolution of a problem's lambda-grid solves: forced by variant 5,
+// never with variant 6 (direct convolution at any width), otherwise for PSFs
+// of FFT_AUTO_K taps and wider.  The grid side is the
+// smallest power of two >= max(nx, ny) + (K - 1) / 2 (at least 16, at most
+// 1024); problems whose FFT buffers do not fit in shared memory keep the
+// direct convolution.
+constexpr int FFT_AUTO_K = 23;  // the first width without a compiled direct kernel; measured crossover 21..25
+
+template <typename T>
+void plan_fft(const mirage_ctx* ctx, Prob<T>& P, int variant) {
+    P.fft_m = 0;
+    P.fft_log = 0;
+    if (variant == 6 || (variant != 5 && P.K < FFT_AUTO_K)) return;
+    const int M = std::max(16, fft_size_for(std::max(P.nx, P.ny) + P.hk));
+    if (M > 1024) return;
+    Prob<T> Q = P;
+    Q.fft_m = M;
+    if (smem_bytes<T>(Q, PLACE_GLOBAL) > (size_t)ctx->max_smem) return;
+    P.fft_m = M;
+    while ((1 << P.fft_log) < M) ++P.fft_log;
+}
+
 const void* pick_fwd(int prec, int K) {
     const KernelTable& t = table();
-    const void* f = t.fwd[prec][K];
+    const void* f = K < MAX_K ? t.fwd[prec][K] : nullptr;
     return f ? f : t.fwd[prec][0];
 }
 
@@ -444,8 +468,12 @@ int eval_impl(mirage_ctx* ctx, const mirage_problem_t* probs, int n_probs, const
     // sizes over the problems
     std::vector<Prob<T>> hp(n_probs);
     long long max_rays = 0, max_cells = 0, max_plen = 0, max_ns = 0, max_npix = 0;
+    long long spec_stride = 0;
     for (int p = 0; p < n_probs; ++p) {
         hp[p] = make_prob<T>(probs[p], probs[p].d, probs[p].sigma, probs[p].mask, probs[p].psf);
+        plan_fft<T>(ctx, hp[p], o.variant);
+        if (hp[p].fft_m)
+            spec_stride = std::max<long long>(spec_stride, (long long)((hp[p].fft_m >> 1) + 1) * hp[p].fft_m);
         max_npix = std::max<long long>(max_npix, hp[p].npix);
         max_rays = std::max<long long>(max_rays, hp[p].nrays);
         max_cells = std::max<long long>(max_cells, hp[p].ncells);
@@ -569,7 +597,7 @@ int eval_impl(mirage_ctx* ctx, const mirage_problem_t* probs, int n_probs, const
     auto choose = [&](const Prob<T>& P, int& mode, bool& fast) -> const void* {
         fast = false;
         mode = 0;
-        if (want == 4) return nullptr;
+        if (want == 4 || want == 6 || P.fft_m) return nullptr;
         int m = 2;                         // automatic: parameter taps (packed FFMA2) when one PSF
         if (want == 1) m = 0;
         if (want == 2) m = 1;
@@ -590,7 +618,7 @@ int eval_impl(mirage_ctx* ctx, const mirage_problem_t* probs, int n_probs, const
         const Prob<T>& P = hp[prob_idx[c]];
         const int place = pick_place<T>(ctx, P);
         const bool big = place != PLACE_SMEM;
-        const void* fn = pick_cgls(prec, place, P.K);
+        const void* fn = pick_cgls(prec, place, P.fft_m ? 0 : P.K);
         size_t item_smem = smem_bytes<T>(P, place);
         long long item_slab = (long long)slab_bytes<T>(P, place);
         int per_sm = 1, mode = 0;
@@ -698,6 +726,7 @@ int eval_impl(mirage_ctx* ctx, const mirage_problem_t* probs, int n_probs, const
     }
     if (o.mode == MIRAGE_MODE_PLAIN) slab_slots = std::max<long long>(slab_slots, max_lam);
     TRY(ctx->slab.ensure((size_t)slab_stride * std::max<long long>(slab_slots, 1)));
+    if (spec_stride) TRY(ctx->spec.ensure((sizeof(double2) + sizeof(float2)) * (size_t)spec_stride * n_probs));
 
     // graph key: everything that shapes the launch sequence
     std::string key;
@@ -705,7 +734,8 @@ int eval_impl(mirage_ctx* ctx, const mirage_problem_t* probs, int n_probs, const
     if (graph) {
         // a grown scratch buffer invalidates every captured graph
         std::vector<void*> now = {ctx->E.p, ctx->E64.p, ctx->Etmp.p, ctx->inv.p, ctx->cst.p, ctx->swp.p, ctx->dpad.p,
-                                  ctx->nent.p, ctx->cstat.p, ctx->X.p, ctx->istat.p, ctx->slab.p, ctx->counters.p};
+                                  ctx->nent.p, ctx->cstat.p, ctx->X.p, ctx->istat.p, ctx->slab.p, ctx->counters.p,
+                                  ctx->spec.p};
         if (now != ctx->scratch_seen) {
             drop_graphs(ctx);
             ctx->scratch_seen = now;
@@ -752,6 +782,7 @@ int eval_impl(mirage_ctx* ctx, const mirage_problem_t* probs, int n_probs, const
     const KernelTable& tb = table();
 
     for (Group* g : glist) TRY(set_smem(ctx, g->fn, g->smem));
+    if (spec_stride) TRY(set_smem(ctx, tb.psf_spectra[prec], fft_smem_bytes(1024)));
     TRY(set_smem(ctx, tb.raytrace[prec], (size_t)max_cells * 4));
     TRY(set_smem(ctx, tb.rt_place[prec], (size_t)max_cells * 4));
 
@@ -777,6 +808,15 @@ int eval_impl(mirage_ctx* ctx, const mirage_problem_t* probs, int n_probs, const
     A.relres = d_relres;
     A.istat = dIst;
     A.phase_clk = nullptr;
+    double2* d_spec64 = nullptr;
+    float2* d_spec32 = nullptr;
+    if (spec_stride) {
+        d_spec64 = ctx->spec.as<double2>();
+        if (sizeof(T) == 4) d_spec32 = reinterpret_cast<float2*>(d_spec64 + spec_stride * n_probs);
+        A.spec64 = d_spec64;
+        A.spec32 = d_spec32;
+        A.spec_stride = spec_stride;
+    }
     if (!graph && o.threads == -2) {
         TRY(ctx->clk.ensure(FAST_NPH * sizeof(unsigned long long)));
         CK(cudaMemsetAsync(ctx->clk.p, 0, FAST_NPH * sizeof(unsigned long long), st));
@@ -789,7 +829,12 @@ int eval_impl(mirage_ctx* ctx, const mirage_problem_t* probs, int n_probs, const
         CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
     }
     int rc = MIRAGE_OK;
+    if (spec_stride) {  // PSF spectra of the FFT problems (once per call)
+        void* sa[] = {(void*)&dprobs, (void*)&d_spec64, (void*)&d_spec32, (void*)&spec_stride};
+        rc = launch(ctx, tb.psf_spectra[prec], dim3(n_probs), dim3(NTHREADS), sa, fft_smem_bytes(1024), st);
+    }
     do {
+        if (rc) break;
         const bool timing = !graph && o.threads < 0;
         ctx->timed = 0;
         if (timing && !ctx->ev[0])
@@ -878,7 +923,7 @@ int eval_impl(mirage_ctx* ctx, const mirage_problem_t* probs, int n_probs, const
             for (int c = 0; c < n_cand && !rc; ++c) {
                 const Prob<T>& P = hp[prob_idx[c]];
                 const int place = pick_place<T>(ctx, P);
-                const void* fn = pick_cgls(prec, place, P.K);
+                const void* fn = pick_cgls(prec, place, P.fft_m ? 0 : P.K);
                 size_t item_smem = smem_bytes<T>(P, place);
                 int pmode = 0;
                 bool pfast = false;
@@ -1117,7 +1162,7 @@ int iter_impl(mirage_ctx* ctx, const mirage_problem_t* probs, int n_probs, const
     const int* dcand = ctx->cand_prob.as<int>();
     const KernelTable& tb = table();
     TRY(launch_raytrace<T>(ctx, dprobs, dcand, lens, 0, n_cand, cs, max_cells, max_npix, st));
-    const void* fn = (k_all > 0 && tb.iter[prec][k_all]) ? tb.iter[prec][k_all] : tb.iter[prec][0];
+    const void* fn = (k_all > 0 && k_all < MAX_K && tb.iter[prec][k_all]) ? tb.iter[prec][k_all] : tb.iter[prec][0];
     TRY(set_smem(ctx, fn, smem));
     IterArgs<T> A;
     std::memset(&A, 0, sizeof(A));
@@ -1187,7 +1232,8 @@ int mirage_destroy(mirage_ctx_t* ctx) {
     DevBuf* bufs[] = {&ctx->E, &ctx->E64, &ctx->Etmp, &ctx->inv, &ctx->cst, &ctx->swp, &ctx->dpad, &ctx->nent, &ctx->cstat,
                       &ctx->X, &ctx->istat, &ctx->slab, &ctx->probs, &ctx->cand_prob, &ctx->items, &ctx->counters,
                       &ctx->stage, &ctx->fE, &ctx->fE64, &ctx->fEtmp, &ctx->finv, &ctx->fcst, &ctx->fswp, &ctx->fdpad,
-                      &ctx->fnent, &ctx->fcstat, &ctx->fslab, &ctx->fprob, &ctx->fcand, &ctx->fpix, &ctx->rt_cursor, &ctx->clk};
+                      &ctx->fnent, &ctx->fcstat, &ctx->fslab, &ctx->fprob, &ctx->fcand, &ctx->fpix, &ctx->rt_cursor, &ctx->clk,
+                      &ctx->spec};
     for (DevBuf* b : bufs) b->release();
     if (ctx->pin_pending) cudaEventSynchronize(ctx->pin_ev);
     if (ctx->pin) cudaFreeHost(ctx->pin);

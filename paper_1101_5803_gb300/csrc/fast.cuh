@@ -271,7 +271,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_cgls_fast(const __grid_constant
         unsigned char* sp = smem + FAST_HDR;
         float2* taps2 = reinterpret_cast<float2*>(sp);
         sp += align_up<T>(sizeof(float2) * 2 * K * K, 16);
-        Work<T> w;
+        Work<T> w;  // w.fft starts null (default member initialiser): the shared FP64 passes test it
         w.taps = nullptr;
         w.taps64 = reinterpret_cast<double*>(sp);
         sp += align_up<T>(sizeof(double) * 2 * K * g.kp, 16);
@@ -470,7 +470,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_cgls_fast(const __grid_constant
             }
         }
         __syncthreads();
-        conv64_pass<T>(w, g, 1);
+        conv64_pass<T, false>(w, g, 1);
         __syncthreads();
         double rs = 0;
         for (int i = tid; i < g.ns; i += bs) {
@@ -578,7 +578,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_cgls_fast(const __grid_constant
         const int zq = (int)(&fi->zero - Q);
         for (int outer = 0;; ++outer) {
             PHASE(11);
-            chi2 = residual64<T>(w, g, lam, red, which, reg2, g64);
+            chi2 = residual64<T, false>(w, g, lam, red, which, reg2, g64);
             PHASE(10);
             rel64 = rhsn > 0 ? sqrt(g64) / rhsn : 0.0;
             if (!isfinite(rel64)) {

@@ -15,5 +15,6 @@ void fill_f32_gen(KernelTable& t) {
     t.rt_scatter[0] = (const void*)k_rt_scatter<float>;
     t.rt_sortcells[0] = (const void*)k_rt_sortcells<float>;
     t.finalize[0] = (const void*)k_finalize<float>;
+    t.psf_spectra[0] = (const void*)k_psf_spectra<float>;
 }
 }  // namespace mirage

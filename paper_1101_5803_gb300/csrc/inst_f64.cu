@@ -14,5 +14,6 @@ void fill_f64(KernelTable& t) {
     t.rt_scatter[1] = (const void*)k_rt_scatter<double>;
     t.rt_sortcells[1] = (const void*)k_rt_sortcells<double>;
     t.finalize[1] = (const void*)k_finalize<double>;
+    t.psf_spectra[1] = (const void*)k_psf_spectra<double>;
 }
 }  // namespace mirage

@@ -20,6 +20,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "fftconv.cuh"
+
 namespace mirage {
 
 constexpr int TILE = 4;        // each thread owns TILE x TILE image pixels in the convolutions
@@ -45,6 +47,7 @@ template <typename T>
 struct Prob {
     int nx, ny, npix, sx, sy, ns, nreg, K, hk, n_sub, Np, nrays, ncx, ncells, reg, interp;
     int Wp, Hp, plen, tiles_x, tiles_y, ntiles, kp, xoff;  // padded layout, tap row pitch, left pad
+    int fft_m, fft_log;  // FFT convolution grid side and its log2 (0: direct convolution)
     double pix, cx, cy, sub0, subd, c0x, c0y, hx, hy;  // ray-trace geometry (always FP64)
     T invNp;
     const T* d;
@@ -92,6 +95,9 @@ struct CglsArgs {
     double* relres;
     int* istat;
     unsigned long long* phase_clk;  // nullable [8]: per-phase SM clock totals (instrumented runs)
+    const float2* spec32;   // PSF spectra of the FFT problems, [n_probs][spec_stride] (FP32 contexts)
+    const double2* spec64;  // the same in FP64
+    long long spec_stride;  // elements per problem
 };
 
 // ---------------------------------------------------------------------------
@@ -844,6 +850,14 @@ __device__ __forceinline__ Geo<T> geo_of(const Prob<T>& P, int nent) {
 }
 
 // work buffers of one item
+// FFT plans of one item: inner solves (T) and refinement (FP64)
+template <typename T>
+struct FftPair {
+    FftPlan<T> t;
+    FftPlan<double> d;
+};
+static_assert(sizeof(FftPair<float>) <= 128 && sizeof(FftPair<double>) <= 128, "FFT plans exceed their 128 bytes");
+
 template <typename T>
 struct Work {
     T* taps;          // [2][K][kp]: flipped PSF (B), PSF (B^T)
@@ -869,6 +883,7 @@ struct Work {
     double* Pa;       // [plen] L x64
     double* Pb;       // [plen] sqrt(W) r64
     double* Pc;       // [plen] B^T sqrt(W) r64
+    const FftPair<T>* fft = nullptr;  // shared: the FFT plans when the problem convolves by FFT, else null
 };
 
 // Bicubic interpolation (Section 2.1 lists it beside bilinear): Keys'
@@ -1199,9 +1214,27 @@ __device__ __noinline__ T conv_pass(const T* __restrict__ src, const T* __restri
 // FP64 convolution pass of the refinement:
 //   mode 0: res = sqrt(W)(d - conv(Pa)); rimg = (T)res; Pb = sqrt(W) res; returns sum res^2
 //   mode 1: Pc = conv(Pb)
-template <typename T>
+template <typename T, bool FFT_OK = true>  // FFT_OK = false: callers that never convolve by FFT
 __device__ __noinline__ double conv64_pass(const Work<T> w, Geo<T> g, int mode) {
     double ss = 0;
+    if (FFT_OK && w.fft) {  // the same passes through the FFT convolution
+        const double* src = mode == 0 ? w.Pa : w.Pb;
+        auto load = [&](int y, int n) -> double { return n < g.nx ? src[(y + g.hk) * g.Wp + n + g.xoff] : 0.0; };
+        auto store = [&](int y, int n, double v) {
+            const int pp = (y + g.hk) * g.Wp + n + g.xoff;
+            if (mode == 0) {
+                const double sw = (double)w.swp[pp];
+                const double res = sw * ((double)w.dpad[pp] - v);
+                w.rimg[pp] = (T)res;
+                w.Pb[pp] = sw * res;
+                ss += res * res;
+            } else {
+                w.Pc[pp] = v;
+            }
+        };
+        fft_convolve<double>(w.fft->d, load, g.ny, store, g.ny, g.nx, mode != 0);
+        return ss;
+    }
     const double* src = mode == 0 ? w.Pa : w.Pb;
     const double* taps = w.taps64 + (mode == 0 ? 0 : g.K * g.kp);
     for (int t = threadIdx.x; t < g.ntiles; t += blockDim.x) {
@@ -1228,11 +1261,32 @@ __device__ __noinline__ double conv64_pass(const Work<T> w, Geo<T> g, int mode) 
     return ss;
 }
 
+// conv_pass through the FFT convolution (B for CONV_Q, B^T for CONV_RAW);
+// writes image pixels only (the frame keeps the zeros set at item start)
+template <typename T>
+__device__ __noinline__ T conv_pass_fft(const FftPlan<T>* f, const T* __restrict__ src, const T* __restrict__ swp,
+                                        T* __restrict__ dst, Geo<T> g, int mode) {
+    T ss = 0;
+    auto load = [&](int y, int n) -> T { return n < g.nx ? src[(y + g.hk) * g.Wp + n + g.xoff] : (T)0; };
+    auto store = [&](int y, int n, T v) {
+        const int pp = (y + g.hk) * g.Wp + n + g.xoff;
+        if (mode == CONV_Q) {
+            const T o = swp[pp] * v;
+            dst[pp] = o;
+            ss = fma(o, o, ss);
+        } else {
+            dst[pp] = v;
+        }
+    };
+    fft_convolve<T>(*f, load, g.ny, store, g.ny, g.nx, mode != CONV_Q);
+    return ss;
+}
+
 // FP64 residual of the current solution x64 (the refinement step):
 //   r = [sqrt(W)(d - B L x64); -sqrt(lam) H x64],  s = A~^T r = rhs - A x64.
 // Writes the inner-solve start: rimg, rreg, s (type T).  Returns chi2 =
 // ||r_img||^2 and sets reg2 = ||H x64||^2 and g64 = ||s||^2.
-template <typename T>
+template <typename T, bool FFT_OK = true>
 __device__ __forceinline__ double residual64(const Work<T>& w, const Geo<T>& g, double lam, double* red,
                                              int& which, double& reg2, double& g64) {
     apply_L<T, double, double, double>(g, w.E64, w.inv, w.x64, w.Pa);
@@ -1245,9 +1299,9 @@ __device__ __forceinline__ double residual64(const Work<T>& w, const Geo<T>& g, 
         rg += h * h;
     }
     __syncthreads();
-    const double chi2 = block_sum(conv64_pass<T>(w, g, 0), red, which);
+    const double chi2 = block_sum(conv64_pass<T, FFT_OK>(w, g, 0), red, which);
     which ^= 1;
-    conv64_pass<T>(w, g, 1);
+    conv64_pass<T, FFT_OK>(w, g, 1);
     __syncthreads();
     double ss = 0;
     for (int i = threadIdx.x; i < g.ns; i += blockDim.x) {
@@ -1302,6 +1356,7 @@ __host__ __device__ inline size_t smem_bytes(const Prob<T>& P, int place) {
         o += 4 * align_up<T>(sizeof(T) * P.ns, 16);                    // x p s minv
         o += 2 * align_up<T>(sizeof(T) * P.nreg, 16);                  // rreg qreg
     }
+    if (P.fft_m) o += fft_smem_bytes(P.fft_m);                         // FFT twiddles and batch buffers
     return o;
 }
 
@@ -1312,6 +1367,7 @@ __host__ __device__ inline size_t slab_bytes(const Prob<T>& P, int place) {
     if (place == PLACE_GLOBAL)
         o += sizeof(T) * (4 * align_up<T>(P.plen, 4) + 4 * align_up<T>(P.ns, 4) + 2 * align_up<T>(P.nreg, 4));
     if (place == PLACE_MID) o += sizeof(T) * 2 * align_up<T>(P.plen, 4);  // rimg qimg
+    if (P.fft_m) o += 16 + sizeof(double2) * (size_t)((P.fft_m >> 1) + 1) * P.fft_m;  // FFT work spectra
     return align_up<T>(o, 256);
 }
 
@@ -1373,6 +1429,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_cgls(CglsArgs<T> A) {
 
         // ---- carve buffers
         Work<T> w;
+        unsigned char* fslab = nullptr;
         unsigned char* sp = smem + 16 + 2 * 33 * sizeof(double) + 128;
         w.taps = reinterpret_cast<T*>(sp);
         sp += align_up<T>(sizeof(T) * 2 * g.K * g.kp, 16);
@@ -1467,6 +1524,54 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_cgls(CglsArgs<T> A) {
             w.E = g_E;
             w.inv = g_inv;
             w.cst = g_cst;
+            fslab = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(ts) + 15) & ~uintptr_t(15));
+        }
+        // FFT convolution (runtime-K global-memory kernel only): twiddles and
+        // batch buffers after the taps in shared memory, the work spectra at
+        // the end of the slab, the problem's PSF spectra from the arguments
+        w.fft = nullptr;
+        if constexpr (K == 0 && BIG) {
+            if (P.fft_m) {
+                const int M = P.fft_m, pi = A.cand_prob[c];
+                unsigned char* fs = sp;
+                FftPair<T>* pp = reinterpret_cast<FftPair<T>*>(fs);
+                fs += 128;
+                float2* tw32 = reinterpret_cast<float2*>(fs);
+                fs += align_up<T>(sizeof(float2) * (M - 1), 16);
+                double2* tw64 = reinterpret_cast<double2*>(fs);
+                fs += align_up<T>(sizeof(double2) * (M - 1), 16);
+                using CT = typename CxOf<T>::type;
+                if (tid == 0) {  // read after the barrier that ends the item set-up
+                    FftPlan<T> a;
+                    FftPlan<double> b;
+                    a.M = b.M = M;
+                    a.logM = b.logM = P.fft_log;
+                    a.nb = fft_batch_count<CT>(M);
+                    b.nb = fft_batch_count<double2>(M);
+                    a.b0 = reinterpret_cast<CT*>(fs);
+                    a.b1 = a.b0 + a.nb * (M + 1);
+                    b.b0 = reinterpret_cast<double2*>(fs);
+                    b.b1 = b.b0 + b.nb * (M + 1);
+                    a.F = reinterpret_cast<CT*>(fslab);
+                    b.F = reinterpret_cast<double2*>(fslab);
+                    b.S = A.spec64 + (long long)pi * A.spec_stride;
+                    b.tw = tw64;
+                    if constexpr (sizeof(T) == 4) {
+                        a.S = A.spec32 + (long long)pi * A.spec_stride;
+                        a.tw = tw32;
+                    } else {
+                        a.S = A.spec64 + (long long)pi * A.spec_stride;
+                        a.tw = tw64;
+                    }
+                    pp->t = a;
+                    pp->d = b;
+                }
+                w.fft = pp;
+                if (c != last_c) {
+                    fft_twiddles<float>(tw32, M);
+                    fft_twiddles<double>(tw64, M);
+                }
+            }
         }
         if (c != last_c) {
             // taps: [0] flipped PSF for B, [1] PSF for B^T; rows padded to kp
@@ -1485,6 +1590,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_cgls(CglsArgs<T> A) {
             w.P2[i] = 0;
             w.Pa[i] = 0;
             w.Pb[i] = 0;
+            if (w.fft) {  // the FFT passes write image pixels only: the frame stays zero
+                w.rimg[i] = 0;
+                w.qimg[i] = 0;
+            }
         }
         __syncthreads();
 
@@ -1646,7 +1755,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_cgls(CglsArgs<T> A) {
                     dqr = fma(q, q, dqr);
                 }
                 __syncthreads();
-                const T dq = dqr + conv_pass<T, K, SH>(w.P1, w.taps, w.swp, w.qimg, g, CONV_Q);
+                T cq;
+                if constexpr (K == 0 && BIG)
+                    cq = w.fft ? conv_pass_fft<T>(&w.fft->t, w.P1, w.swp, w.qimg, g, CONV_Q)
+                               : conv_pass<T, K, SH>(w.P1, w.taps, w.swp, w.qimg, g, CONV_Q);
+                else
+                    cq = conv_pass<T, K, SH>(w.P1, w.taps, w.swp, w.qimg, g, CONV_Q);
+                const T dq = dqr + cq;
                 {
                     const double delta = block_sum_to0<T>(dq, red);
                     if (tid == 0) {
@@ -1682,7 +1797,14 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_cgls(CglsArgs<T> A) {
                     }
                 }
                 __syncthreads();  // P2 complete
-                conv_pass<T, K, SH>(w.P2, w.taps + g.K * g.kp, nullptr, w.qimg, g, CONV_RAW);
+                if constexpr (K == 0 && BIG) {
+                    if (w.fft)
+                        conv_pass_fft<T>(&w.fft->t, w.P2, nullptr, w.qimg, g, CONV_RAW);
+                    else
+                        conv_pass<T, K, SH>(w.P2, w.taps + g.K * g.kp, nullptr, w.qimg, g, CONV_RAW);
+                } else {
+                    conv_pass<T, K, SH>(w.P2, w.taps + g.K * g.kp, nullptr, w.qimg, g, CONV_RAW);
+                }
                 __syncthreads();  // u complete
                 T gs = 0;
                 if (cells_fit) {
@@ -1973,6 +2095,35 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_forward(const Prob<T>* __restri
         const double cval = block_sum(chi, red, which);
         which ^= 1;
         if (tid == 0) chi2[k] = cval;
+    }
+}
+
+// PSF spectra of the problems that convolve by FFT, one CTA per problem:
+// the FP64 spectrum (fft_psf_spectrum) and, for FP32 contexts, its rounding
+// to float.  Problems with fft_m == 0 are skipped.
+template <typename T>
+__global__ void __launch_bounds__(NTHREADS) k_psf_spectra(const Prob<T>* __restrict__ probs, double2* spec64,
+                                                        float2* spec32, long long stride) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const Prob<T>& P = probs[blockIdx.x];
+    if (P.fft_m == 0) return;
+    const int M = P.fft_m;
+    double2* tw = reinterpret_cast<double2*>(smem);
+    FftPlan<double> f;
+    f.M = M;
+    f.logM = P.fft_log;
+    f.nb = fft_batch_count<double2>(M);
+    f.tw = tw;
+    f.b0 = reinterpret_cast<double2*>(smem + align_up<T>(sizeof(double2) * (M - 1), 16));
+    f.b1 = f.b0 + f.nb * (M + 1);
+    f.F = spec64 + (long long)blockIdx.x * stride;
+    fft_twiddles<double>(tw, M);
+    __syncthreads();
+    fft_psf_spectrum<double>(f, P.psf, P.K);
+    if (spec32) {
+        const int n = ((M >> 1) + 1) * M;
+        float2* o = spec32 + (long long)blockIdx.x * stride;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) o[i] = make_float2((float)f.F[i].x, (float)f.F[i].y);
     }
 }
 

@@ -144,7 +144,7 @@ int forward_noalloc_impl(const mirage_problem_t* prob, const double* lens, const
     void* a1[] = {(void*)&dprob, (void*)&dcand, (void*)&lens, &cand0, &nc, &cs};
     if (cudaLaunchKernel(rt, dim3(1), dim3(NTHREADS), a1, rt_smem, st) != cudaSuccess)
         return fail(MIRAGE_ERR_CUDA, "forward_noalloc: ray-trace launch failed");
-    const void* fn = tb.fwd[prec][P.K] ? tb.fwd[prec][P.K] : tb.fwd[prec][0];
+    const void* fn = (P.K < MAX_K && tb.fwd[prec][P.K]) ? tb.fwd[prec][P.K] : tb.fwd[prec][0];
     const size_t smem = align_up<T>(sizeof(T) * P.K * P.kp, 16) + 2 * 33 * sizeof(double) + 16;
     const T* S = reinterpret_cast<const T*>(s);
     T* M = reinterpret_cast<T*>(model);

@@ -25,6 +25,7 @@ struct KernelTable {
     // fwdb[K]: banded FP32 forward batch (one ray per pixel)
     const void* fwdb[MAX_K];
     const void* pixmap;  // pixel-ordered ray map for the banded forward batch
+    const void* psf_spectra[2];  // PSF spectra of the FFT-convolution problems
 };
 
 void fill_f32_k5(KernelTable& t);

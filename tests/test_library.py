@@ -45,6 +45,7 @@ def test_header_constants_match_binding():
     txt = open(binding.HEADER).read()
     assert int(re.search(r"#define MIRAGE_N_PHASE_CLOCKS (\d+)", txt).group(1)) == binding.N_PHASE_CLOCKS
     assert int(re.search(r"#define MIRAGE_MAX_LAM (\d+)", txt).group(1)) == binding.MAX_LAM
+    assert int(re.search(r"#define MIRAGE_MAX_KPSF (\d+)", txt).group(1)) == binding.MAX_KPSF
     for name in ("MIRAGE_INTERP_BILINEAR", "MIRAGE_INTERP_NEAREST", "MIRAGE_INTERP_BICUBIC",
                  "MIRAGE_REG_IDENTITY", "MIRAGE_REG_GRADIENT", "MIRAGE_REG_LAPLACIAN"):
         m = re.search(r"#define %s (\d+)" % name, txt)

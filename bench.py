@@ -424,6 +424,27 @@ def run_gpu(args):
     return 0
 
 
+def run_profile_case(variant: int) -> int:
+    """The small case the ncu captures of the CGLS kernel run: 20 candidates
+    x the 16-lambda grid of the 64x64 workload (320 items), two evaluations
+    with one kernel variant, no timing."""
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1101_5803_gb300 import binding
+    from paper_1101_5803_gb300.problems import ga64_workload
+    ctx = binding.Context(0, binding.MIRAGE_FP32)
+    wl = ga64_workload(ctx, 20, 16, seed=3)
+    for _ in range(2):
+        out = ctx.eval_batch([wl.problem], wl.lens, wl.prob_idx, wl.lambdas, wl.n_lam, tol=1e-6, variant=variant)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": True, "variant": variant, "items": int(out["iters"].numel()),
+                      "cg_iterations": int(out["iters"].sum().item())}), flush=True)
+    ctx.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -431,7 +452,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--profile-case", type=int, default=None, metavar="VARIANT",
+                    help="run only the small case of the ncu captures (20 candidates x 16 lambdas, two "
+                         "evaluations with this kernel variant) and exit")
     args = ap.parse_args()
+    if args.profile_case is not None:
+        return run_profile_case(args.profile_case)
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)

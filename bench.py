@@ -439,8 +439,18 @@ def run_profile_case(variant: int) -> int:
     for _ in range(2):
         out = ctx.eval_batch([wl.problem], wl.lens, wl.prob_idx, wl.lambdas, wl.n_lam, tol=1e-6, variant=variant)
     torch.cuda.synchronize()
+    # one more evaluation with the two-CTA kernel's per-phase SM clocks
+    ctx.eval_batch([wl.problem], wl.lens, wl.prob_idx, wl.lambdas, wl.n_lam, tol=1e-6, variant=variant,
+                   phase_clocks=True)
+    torch.cuda.synchronize()
+    clk = [float(v) for v in ctx.phase_clocks()]
+    its = float(out["iters"].sum().item())
+    names = ["L p + H p", "B convolution", "q reduction", "vector updates", "B^T convolution", "L^T walk",
+             "L^T join", "L^T gather + H^T", "gamma reduction", "p update", "FP64 refinement", "item set-up"]
     print(json.dumps({"profile_case": True, "variant": variant, "items": int(out["iters"].numel()),
-                      "cg_iterations": int(out["iters"].sum().item())}), flush=True)
+                      "cg_iterations": int(its),
+                      "phase_clk_per_iteration": {n: round(c / max(its, 1.0), 1) for n, c in zip(names, clk)}}),
+          flush=True)
     ctx.close()
     return 0
 

@@ -202,6 +202,99 @@ static_assert(sizeof(FastItem) <= 128, "fast-kernel item constants must fit the 
 constexpr int FAST_NPH = 12;  // per-phase clock slots (see mirage_last_phase_clocks)
 constexpr size_t FAST_HDR = 16 + 2 * 33 * sizeof(double) + 128 + 16 * sizeof(unsigned long long);
 
+// The refinement's FP64 convolution passes (conv64_pass's contract) on the
+// FP32 pipe.  The taps are FP32 numbers, so each product with an FP64 input
+// x = hi + lo (hi = x rounded to float, lo = the float nearest x - hi) is
+// formed as t hi = p + e exactly (FMA error-free product), the p summed
+// with Knuth's error-free TwoSum into a float pair (s, c) and t lo + e
+// added to c: a double-float accumulation, ~2^-44 relative instead of FP64's
+// 2^-53, at about 11 FP32 operations per tap against one FP64 FMA (which
+// the GPU issues at 1/64 of the FP32 rate).  hi and lo are staged in the
+// two shared image buffers, which are cleared again afterwards (they must
+// hold zeros outside the pixels each iteration writes).
+template <int K>
+__device__ __noinline__ double conv64_df(const double* __restrict__ src, float* __restrict__ hi,
+                                         float* __restrict__ lo, const float2* __restrict__ taps,
+                                         const float* __restrict__ swp, const float* __restrict__ dpad,
+                                         float* __restrict__ rimg, double* __restrict__ Pb, double* __restrict__ Pc,
+                                         const Geo<float> g, int mode) {
+    for (int i = threadIdx.x; i < g.plen; i += blockDim.x) {
+        const double v = src[i];
+        const float h = (float)v;
+        hi[i] = h;
+        lo[i] = (float)(v - (double)h);
+    }
+    __syncthreads();
+    double ss = 0.0;
+    for (int t = threadIdx.x; t < g.ntiles; t += blockDim.x) {
+        const int ty = t / g.tiles_x, tx = t - ty * g.tiles_x;
+        const int base = (ty * TILE) * g.Wp + tx * TILE + g.sh;
+#pragma unroll 1
+        for (int r = 0; r < TILE; ++r) {
+            float s[TILE], c[TILE];
+#pragma unroll
+            for (int q = 0; q < TILE; ++q) s[q] = c[q] = 0.f;
+#pragma unroll 1
+            for (int a = 0; a < K; ++a) {
+                const float* hrow = hi + base + (r + a) * g.Wp;
+                const float* lrow = lo + base + (r + a) * g.Wp;
+                float xh[K + TILE - 1], xl[K + TILE - 1];
+#pragma unroll
+                for (int j = 0; j < K + TILE - 1; ++j) {
+                    xh[j] = hrow[j];
+                    xl[j] = lrow[j];
+                }
+#pragma unroll
+                for (int b = 0; b < K; ++b) {
+                    const float tt = taps[a * K + b].x;
+#pragma unroll
+                    for (int q = 0; q < TILE; ++q) {
+                        const float pr = tt * xh[b + q];
+                        const float e = fmaf(tt, xh[b + q], -pr);  // t hi - pr, exactly
+                        const float sn = s[q] + pr;                 // TwoSum(s, pr) = sn + er
+                        const float bv = sn - s[q];
+                        const float er = (s[q] - (sn - bv)) + (pr - bv);
+                        s[q] = sn;
+                        c[q] = fmaf(tt, xl[b + q], c[q] + (er + e));
+                    }
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < TILE; ++q) {
+                const int pp = (ty * TILE + r + g.hk) * g.Wp + tx * TILE + q + g.xoff;
+                const double v = (double)s[q] + (double)c[q];
+                if (mode == 0) {
+                    const double sw = (double)swp[pp];
+                    const double res = sw * ((double)dpad[pp] - v);
+                    rimg[pp] = (float)res;
+                    Pb[pp] = sw * res;
+                    ss += res * res;
+                } else {
+                    Pc[pp] = v;
+                }
+            }
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < g.plen; i += blockDim.x) {
+        hi[i] = 0.f;
+        lo[i] = 0.f;
+    }
+    return ss;
+}
+
+// residual64's convolution functor for the two-CTA kernel
+template <int K>
+struct Conv64DF {
+    float* hi;
+    float* lo;
+    const float2* taps;  // [0, K*K): flipped PSF (B); [K*K, 2 K*K): PSF (B^T)
+    __device__ double operator()(const Work<float>& w, const Geo<float>& g, int mode) const {
+        return conv64_df<K>(mode == 0 ? w.Pa : w.Pb, hi, lo, taps + (mode == 0 ? 0 : K * K), w.swp, w.dpad, w.rimg,
+                            w.Pb, w.Pc, g, mode);
+    }
+};
+
 template <int K, int NSP, int MODE>
 __global__ void __launch_bounds__(NTHREADS, 2) k_cgls_fast(const __grid_constant__ FastArgs FA) {
     static_assert(NSP <= 4, "the per-thread masks describe at most four source pixels");
@@ -470,7 +563,8 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_cgls_fast(const __grid_constant
             }
         }
         __syncthreads();
-        conv64_pass<T, false>(w, g, 1);
+        const Conv64DF<K> conv_df{P1, P2, taps2};
+        conv_df(w, g, 1);
         __syncthreads();
         double rs = 0;
         for (int i = tid; i < g.ns; i += bs) {
@@ -578,7 +672,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_cgls_fast(const __grid_constant
         const int zq = (int)(&fi->zero - Q);
         for (int outer = 0;; ++outer) {
             PHASE(11);
-            chi2 = residual64<T, false>(w, g, lam, red, which, reg2, g64);
+            chi2 = residual64<T, false>(w, g, lam, red, which, reg2, g64, conv_df);
             PHASE(10);
             rel64 = rhsn > 0 ? sqrt(g64) / rhsn : 0.0;
             if (!isfinite(rel64)) {

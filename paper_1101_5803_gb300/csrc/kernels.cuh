@@ -1286,9 +1286,19 @@ __device__ __noinline__ T conv_pass_fft(const FftPlan<T>* f, const T* __restrict
 //   r = [sqrt(W)(d - B L x64); -sqrt(lam) H x64],  s = A~^T r = rhs - A x64.
 // Writes the inner-solve start: rimg, rreg, s (type T).  Returns chi2 =
 // ||r_img||^2 and sets reg2 = ||H x64||^2 and g64 = ||s||^2.
-template <typename T, bool FFT_OK = true>
+// the refinement's two FP64 convolution passes (mode 0: the image residual
+// from L x64, mode 1: B^T of the weighted residual); kernels with their own
+// form of these passes hand residual64 another functor
+template <typename T, bool FFT_OK>
+struct Conv64Pass {
+    __device__ double operator()(const Work<T>& w, const Geo<T>& g, int mode) const {
+        return conv64_pass<T, FFT_OK>(w, g, mode);
+    }
+};
+
+template <typename T, bool FFT_OK = true, class Conv = Conv64Pass<T, FFT_OK>>
 __device__ __forceinline__ double residual64(const Work<T>& w, const Geo<T>& g, double lam, double* red,
-                                             int& which, double& reg2, double& g64) {
+                                             int& which, double& reg2, double& g64, const Conv& conv = Conv()) {
     apply_L<T, double, double, double>(g, w.E64, w.inv, w.x64, w.Pa);
     const double sl = sqrt(lam);
     double rg = 0;
@@ -1299,9 +1309,9 @@ __device__ __forceinline__ double residual64(const Work<T>& w, const Geo<T>& g, 
         rg += h * h;
     }
     __syncthreads();
-    const double chi2 = block_sum(conv64_pass<T, FFT_OK>(w, g, 0), red, which);
+    const double chi2 = block_sum(conv(w, g, 0), red, which);
     which ^= 1;
-    conv64_pass<T, FFT_OK>(w, g, 1);
+    conv(w, g, 1);
     __syncthreads();
     double ss = 0;
     for (int i = threadIdx.x; i < g.ns; i += blockDim.x) {

@@ -1286,6 +1286,111 @@ __device__ __noinline__ T conv_pass_fft(const FftPlan<T>* f, const T* __restrict
 //   r = [sqrt(W)(d - B L x64); -sqrt(lam) H x64],  s = A~^T r = rhs - A x64.
 // Writes the inner-solve start: rimg, rreg, s (type T).  Returns chi2 =
 // ||r_img||^2 and sets reg2 = ||H x64||^2 and g64 = ||s||^2.
+// The refinement's FP64 convolution passes in FP32 contexts as double-float
+// sums on the FP32 pipe: the taps are FP32 numbers, each FP64 input x is
+// split into hi = float(x) and lo = float(x - hi), t hi is formed exactly as
+// p + e (FMA error-free product) and the p are summed with Knuth's
+// error-free TwoSum into a float pair (s, c), t lo + e going to c.  About
+// 11 FP32 operations per tap instead of one FP64 FMA at 1/64 of the FP32
+// rate, ~2^-44 relative.  hi and lo are staged in the P1/P2 image buffers,
+// which hold zeros again on return.  KT > 0: compiled tap count.
+template <int KT>
+__device__ __noinline__ double conv64_df_gen(const double* __restrict__ src, float* __restrict__ hi,
+                                             float* __restrict__ lo, const float* __restrict__ taps,
+                                             const float* __restrict__ swp, const float* __restrict__ dpad,
+                                             float* __restrict__ rimg, double* __restrict__ Pb,
+                                             double* __restrict__ Pc, const Geo<float> g, int mode) {
+    for (int i = threadIdx.x; i < g.plen; i += blockDim.x) {
+        const double v = src[i];
+        const float h = (float)v;
+        hi[i] = h;
+        lo[i] = (float)(v - (double)h);
+    }
+    __syncthreads();
+    const int K = KT > 0 ? KT : g.K, kp = g.kp;
+    double ss = 0.0;
+    for (int t = threadIdx.x; t < g.ntiles; t += blockDim.x) {
+        const int ty = t / g.tiles_x, tx = t - ty * g.tiles_x;
+        const int base = (ty * TILE) * g.Wp + tx * TILE + g.sh;
+#pragma unroll 1
+        for (int r = 0; r < TILE; ++r) {
+            float s[TILE], c[TILE];
+#pragma unroll
+            for (int q = 0; q < TILE; ++q) s[q] = c[q] = 0.f;
+#pragma unroll 1
+            for (int a = 0; a < K; ++a) {
+                const float* hrow = hi + base + (r + a) * g.Wp;
+                const float* lrow = lo + base + (r + a) * g.Wp;
+                const float* trow = taps + a * kp;
+                auto step = [&](float tt, float xh, float xl, int q) {
+                    const float pr = tt * xh;
+                    const float e = fmaf(tt, xh, -pr);  // t hi - pr, exactly
+                    const float sn = s[q] + pr;          // TwoSum(s, pr) = sn + er
+                    const float bv = sn - s[q];
+                    const float er = (s[q] - (sn - bv)) + (pr - bv);
+                    s[q] = sn;
+                    c[q] = fmaf(tt, xl, c[q] + (er + e));
+                };
+                if constexpr (KT > 0) {
+                    float xh[KT + TILE - 1], xl[KT + TILE - 1];
+#pragma unroll
+                    for (int j = 0; j < KT + TILE - 1; ++j) {
+                        xh[j] = hrow[j];
+                        xl[j] = lrow[j];
+                    }
+#pragma unroll
+                    for (int b = 0; b < KT; ++b) {
+                        const float tt = trow[b];
+#pragma unroll
+                        for (int q = 0; q < TILE; ++q) step(tt, xh[b + q], xl[b + q], q);
+                    }
+                } else {
+#pragma unroll 1
+                    for (int b = 0; b < K; ++b) {
+                        const float tt = trow[b];
+#pragma unroll
+                        for (int q = 0; q < TILE; ++q) step(tt, hrow[b + q], lrow[b + q], q);
+                    }
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < TILE; ++q) {
+                const int pp = (ty * TILE + r + g.hk) * g.Wp + tx * TILE + q + g.xoff;
+                const double v = (double)s[q] + (double)c[q];
+                if (mode == 0) {
+                    const double sw = (double)swp[pp];
+                    const double res = sw * ((double)dpad[pp] - v);
+                    rimg[pp] = (float)res;
+                    Pb[pp] = sw * res;
+                    ss += res * res;
+                } else {
+                    Pc[pp] = v;
+                }
+            }
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < g.plen; i += blockDim.x) {
+        hi[i] = 0.f;
+        lo[i] = 0.f;
+    }
+    return ss;
+}
+
+// the general kernel's refinement passes: double-float for direct
+// convolution in FP32 contexts, conv64_pass otherwise (FP64 contexts, FFT)
+template <typename T, int KT>
+struct Conv64Gen {
+    __device__ double operator()(const Work<T>& w, const Geo<T>& g, int mode) const {
+        if constexpr (sizeof(T) == 4) {
+            if (!w.fft)
+                return conv64_df_gen<KT>(mode == 0 ? w.Pa : w.Pb, w.P1, w.P2, w.taps + (mode == 0 ? 0 : g.K * g.kp),
+                                         w.swp, w.dpad, w.rimg, w.Pb, w.Pc, g, mode);
+        }
+        return conv64_pass<T, true>(w, g, mode);
+    }
+};
+
 // the refinement's two FP64 convolution passes (mode 0: the image residual
 // from L x64, mode 1: B^T of the weighted residual); kernels with their own
 // form of these passes hand residual64 another functor
@@ -1641,7 +1746,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_cgls(CglsArgs<T> A) {
             }
         }
         __syncthreads();
-        conv64_pass<T>(w, g, 1);
+        const Conv64Gen<T, K> conv_ref{};
+        conv_ref(w, g, 1);
         __syncthreads();
         double rs = 0;
         for (int i = tid; i < g.ns; i += bs) {
@@ -1700,7 +1806,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_cgls(CglsArgs<T> A) {
         // solve short (FP32 loses orthogonality on long ones) at few FP64 passes
         const double eta_min = sizeof(T) == 4 ? 0.03 : 0.3 * A.tol;
         for (int outer = 0;; ++outer) {
-            chi2 = residual64<T>(w, g, lam, red, which, reg2, g64);
+            chi2 = residual64<T, true, Conv64Gen<T, K>>(w, g, lam, red, which, reg2, g64, conv_ref);
             rel64 = rhsn > 0 ? sqrt(g64) / rhsn : 0.0;
             if (!isfinite(rel64)) {
                 status |= ST_BREAK;

@@ -347,6 +347,25 @@ def run_gpu(args):
                "tflops": fwd_flops / (min(fms) / 1e3) / 1e12}
     del S
 
+    # a 65 x 65 PSF on the 64x64 system: the FFT blur (the automatic choice
+    # at this width) against direct convolution (variant 6)
+    from paper_1101_5803_gb300.problems import widepsf_workload
+    ww = widepsf_workload(ctx, 16, 8, seed=5)
+    wide = {"workload": "64x64 image, 32x32 source, 65x65 PSF, 16 candidates x 8 lambdas (1e-3..1e1)"}
+    for name, var in (("fft", 0), ("direct", 6)):
+        ctx.eval_batch([ww.problem], ww.lens[:2], ww.prob_idx[:2], ww.lambdas[:2], ww.n_lam[:2], tol=1e-6,
+                       variant=var)  # warm-up
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        wout = ctx.eval_batch([ww.problem], ww.lens, ww.prob_idx, ww.lambdas, ww.n_lam, tol=1e-6, variant=var)
+        e1.record()
+        torch.cuda.synchronize()
+        wms = e0.elapsed_time(e1)
+        wit = wout["iters"].cpu().numpy()
+        wide[name] = {"ms": wms, "evals_per_s": 16 / (wms / 1e3), "cg_iterations": int(wit.sum()),
+                      "us_per_iteration_of_slowest_item": wms * 1e3 / max(1, int(wit.max())),
+                      "status_bits_any": int(np.bitwise_or.reduce(wout["status"].cpu().numpy()))}
+
     # GA generations on the same problem: surrogate screen vs none
     from paper_1101_5803_gb300.ga import GAConfig, run_ga
     n_gen = int(os.environ.get("MIRAGE_GA_GENERATIONS", "4"))
@@ -415,7 +434,8 @@ def run_gpu(args):
             "ga_surrogate": ga_res,
             "pso": pso_res,
             "iter_lcurve": iter_res,
-            "forward_batch": fwd_res}
+            "forward_batch": fwd_res,
+            "wide_psf": wide}
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()

@@ -672,7 +672,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_cgls_fast(const __grid_constant
         const int zq = (int)(&fi->zero - Q);
         for (int outer = 0;; ++outer) {
             PHASE(11);
-            chi2 = residual64<T, false>(w, g, lam, red, which, reg2, g64, conv_df);
+            chi2 = residual64<T>(w, g, lam, red, which, reg2, g64, conv_df);
             PHASE(10);
             rel64 = rhsn > 0 ? sqrt(g64) / rhsn : 0.0;
             if (!isfinite(rel64)) {

@@ -1214,10 +1214,10 @@ __device__ __noinline__ T conv_pass(const T* __restrict__ src, const T* __restri
 // FP64 convolution pass of the refinement:
 //   mode 0: res = sqrt(W)(d - conv(Pa)); rimg = (T)res; Pb = sqrt(W) res; returns sum res^2
 //   mode 1: Pc = conv(Pb)
-template <typename T, bool FFT_OK = true>  // FFT_OK = false: callers that never convolve by FFT
+template <typename T>
 __device__ __noinline__ double conv64_pass(const Work<T> w, Geo<T> g, int mode) {
     double ss = 0;
-    if (FFT_OK && w.fft) {  // the same passes through the FFT convolution
+    if (w.fft) {  // the same passes through the FFT convolution
         const double* src = mode == 0 ? w.Pa : w.Pb;
         auto load = [&](int y, int n) -> double { return n < g.nx ? src[(y + g.hk) * g.Wp + n + g.xoff] : 0.0; };
         auto store = [&](int y, int n, double v) {
@@ -1387,23 +1387,15 @@ struct Conv64Gen {
                 return conv64_df_gen<KT>(mode == 0 ? w.Pa : w.Pb, w.P1, w.P2, w.taps + (mode == 0 ? 0 : g.K * g.kp),
                                          w.swp, w.dpad, w.rimg, w.Pb, w.Pc, g, mode);
         }
-        return conv64_pass<T, true>(w, g, mode);
+        return conv64_pass<T>(w, g, mode);
     }
 };
 
-// the refinement's two FP64 convolution passes (mode 0: the image residual
-// from L x64, mode 1: B^T of the weighted residual); kernels with their own
-// form of these passes hand residual64 another functor
-template <typename T, bool FFT_OK>
-struct Conv64Pass {
-    __device__ double operator()(const Work<T>& w, const Geo<T>& g, int mode) const {
-        return conv64_pass<T, FFT_OK>(w, g, mode);
-    }
-};
-
-template <typename T, bool FFT_OK = true, class Conv = Conv64Pass<T, FFT_OK>>
+// conv: the refinement's two convolution passes (mode 0: the image residual
+// from L x64, mode 1: B^T of the weighted residual) as each kernel forms them
+template <typename T, class Conv>
 __device__ __forceinline__ double residual64(const Work<T>& w, const Geo<T>& g, double lam, double* red,
-                                             int& which, double& reg2, double& g64, const Conv& conv = Conv()) {
+                                             int& which, double& reg2, double& g64, const Conv& conv) {
     apply_L<T, double, double, double>(g, w.E64, w.inv, w.x64, w.Pa);
     const double sl = sqrt(lam);
     double rg = 0;
@@ -1806,7 +1798,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_cgls(CglsArgs<T> A) {
         // solve short (FP32 loses orthogonality on long ones) at few FP64 passes
         const double eta_min = sizeof(T) == 4 ? 0.03 : 0.3 * A.tol;
         for (int outer = 0;; ++outer) {
-            chi2 = residual64<T, true, Conv64Gen<T, K>>(w, g, lam, red, which, reg2, g64, conv_ref);
+            chi2 = residual64<T>(w, g, lam, red, which, reg2, g64, conv_ref);
             rel64 = rhsn > 0 ? sqrt(g64) / rhsn : 0.0;
             if (!isfinite(rel64)) {
                 status |= ST_BREAK;

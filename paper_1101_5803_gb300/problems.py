@@ -73,6 +73,23 @@ def ga64_workload(ctx: Context, n_cand: int = 256, n_lam: int = 16, seed: int = 
     return Workload(g, prob, lens, lams, np.full(n_cand, n_lam, np.int32), np.zeros(n_cand, np.int32))
 
 
+def widepsf_workload(ctx: Context, n_cand: int = 16, n_lam: int = 8, k_psf: int = 65, seed: int = 0) -> Workload:
+    """The 64x64 system with a wide PSF (the 65 x 65 class of the paper's
+    large test): 64x64 image at 0.05"/px, 32x32 source over +-0.8", a
+    k_psf x k_psf Gaussian PSF of sigma k_psf / 6 px, Laplacian H, n_lam
+    lambdas log-spaced over 1e-3..1e1."""
+    import dataclasses as _dc
+
+    rng = np.random.default_rng(seed)
+    g = _dc.replace(synth.geom_ga64(), kpsf=k_psf)
+    psf = synth.gaussian_psf(k_psf, k_psf / 6.0)
+    comps = synth.drawn_source(rng)
+    prob = observe_on_device(ctx, g, psf, comps, synth.TRUE_LENS, rng)
+    lens = torch.as_tensor(synth.lens_population(rng, n_cand), device="cuda")
+    lams = torch.as_tensor(np.tile(synth.lambda_grid(n_lam, 1e-3, 1e1), (n_cand, 1)), device="cuda")
+    return Workload(g, prob, lens, lams, np.full(n_cand, n_lam, np.int32), np.zeros(n_cand, np.int32))
+
+
 def e2e128_workload(ctx: Context, n_cand: int = 512, n_lam: int = 16, seed: int = 0) -> Workload:
     """End-to-end GA system: 128x128 image at 0.03"/px, 48x48 source over
     +-0.8", 11x11 Gaussian PSF (sigma 1.5 px), Laplacian H, n_lam lambdas

@@ -308,3 +308,41 @@ def test_bicubic_identity_lens_and_subpixel_average():
     rows = np.asarray(L2.sum(axis=1)).ravel()
     assert np.all(rows[~m2] == 0)
     assert np.isclose(rows[m2], 1.0, atol=1e-12).sum() > 0.5 * m2.sum()
+
+
+# ---------------------------------------------------------------------------
+# the FFT blur's grid bound (the reading behind the FFT convolution path)
+# ---------------------------------------------------------------------------
+def _fft_blur(img, psf, M, corr=False):
+    """B img (or B^T img) as the crop of a circular convolution on an M x M
+    grid with the PSF centred at (0, 0), by numpy's FFT."""
+    ny, nx = img.shape
+    K = psf.shape[0]
+    c = (K - 1) // 2
+    pc = np.zeros((M, M))
+    for a in range(K):
+        for b in range(K):
+            pc[(a - c) % M, (b - c) % M] += psf[a, b]
+    S = np.fft.fft2(pc)
+    if corr:
+        S = np.conj(S)
+    X = np.zeros((M, M))
+    X[:ny, :nx] = img
+    return np.real(np.fft.ifft2(np.fft.fft2(X) * S))[:ny, :nx]
+
+
+@pytest.mark.parametrize("ny,nx,K", [(12, 10, 5), (9, 14, 9), (8, 8, 17), (20, 7, 13)])
+def test_fft_grid_bound_reproduces_the_zero_padded_blur(ny, nx, K):
+    # M >= max(nx, ny) + (K - 1)/2 gives exactly the oracle's B and B^T (the
+    # wrap of the centred PSF lands in the zero padding); one row or column
+    # less and the wrap aliases into the image
+    from oracle.operators import blur_matrix
+    rng = np.random.default_rng(K)
+    g = synth.Geometry(nx, ny, 0.1, 4, 4, -0.8, 0.8, -0.8, 0.8, K, 1, synth.REG_IDENTITY)
+    psf = rng.random((K, K))
+    B = blur_matrix(g, psf, dense=True)
+    img = rng.standard_normal((ny, nx))
+    M = max(nx, ny) + (K - 1) // 2
+    np.testing.assert_allclose(_fft_blur(img, psf, M).ravel(), B @ img.ravel(), atol=1e-12)
+    np.testing.assert_allclose(_fft_blur(img, psf, M, corr=True).ravel(), B.T @ img.ravel(), atol=1e-12)
+    assert np.abs(_fft_blur(img, psf, M - 1).ravel() - B @ img.ravel()).max() > 1e-6

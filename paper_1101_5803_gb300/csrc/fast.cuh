@@ -203,13 +203,10 @@ constexpr int FAST_NPH = 12;  // per-phase clock slots (see mirage_last_phase_cl
 constexpr size_t FAST_HDR = 16 + 2 * 33 * sizeof(double) + 128 + 16 * sizeof(unsigned long long);
 
 // The refinement's FP64 convolution passes (conv64_pass's contract) on the
-// FP32 pipe.  The taps are FP32 numbers, so each product with an FP64 input
-// x = hi + lo (hi = x rounded to float, lo = the float nearest x - hi) is
-// formed as t hi = p + e exactly (FMA error-free product), the p summed
-// with Knuth's error-free TwoSum into a float pair (s, c) and t lo + e
-// added to c: a double-float accumulation, ~2^-44 relative instead of FP64's
-// 2^-53, at about 11 FP32 operations per tap against one FP64 FMA (which
-// the GPU issues at 1/64 of the FP32 rate).  hi and lo are staged in the
+// FP32 pipe.  The taps are FP32 numbers, so the sums are double-float
+// accumulations (dfloat.cuh): ~2^-44 relative instead of FP64's 2^-53, at
+// about 11 FP32 operations per tap against one FP64 FMA (which the GPU
+// issues at 1/64 of the FP32 rate).  hi and lo are staged in the
 // two shared image buffers, which are cleared again afterwards (they must
 // hold zeros outside the pixels each iteration writes).
 template <int K>
@@ -218,12 +215,7 @@ __device__ __noinline__ double conv64_df(const double* __restrict__ src, float* 
                                          const float* __restrict__ swp, const float* __restrict__ dpad,
                                          float* __restrict__ rimg, double* __restrict__ Pb, double* __restrict__ Pc,
                                          const Geo<float> g, int mode) {
-    for (int i = threadIdx.x; i < g.plen; i += blockDim.x) {
-        const double v = src[i];
-        const float h = (float)v;
-        hi[i] = h;
-        lo[i] = (float)(v - (double)h);
-    }
+    for (int i = threadIdx.x; i < g.plen; i += blockDim.x) df_split(src[i], hi[i], lo[i]);
     __syncthreads();
     double ss = 0.0;
     for (int t = threadIdx.x; t < g.ntiles; t += blockDim.x) {
@@ -248,15 +240,7 @@ __device__ __noinline__ double conv64_df(const double* __restrict__ src, float* 
                 for (int b = 0; b < K; ++b) {
                     const float tt = taps[a * K + b].x;
 #pragma unroll
-                    for (int q = 0; q < TILE; ++q) {
-                        const float pr = tt * xh[b + q];
-                        const float e = fmaf(tt, xh[b + q], -pr);  // t hi - pr, exactly
-                        const float sn = s[q] + pr;                 // TwoSum(s, pr) = sn + er
-                        const float bv = sn - s[q];
-                        const float er = (s[q] - (sn - bv)) + (pr - bv);
-                        s[q] = sn;
-                        c[q] = fmaf(tt, xl[b + q], c[q] + (er + e));
-                    }
+                    for (int q = 0; q < TILE; ++q) df_madd(s[q], c[q], tt, xh[b + q], xl[b + q]);
                 }
             }
 #pragma unroll

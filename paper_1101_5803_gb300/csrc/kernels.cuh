@@ -20,6 +20,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "dfloat.cuh"
 #include "fftconv.cuh"
 
 namespace mirage {
@@ -1287,11 +1288,8 @@ __device__ __noinline__ T conv_pass_fft(const FftPlan<T>* f, const T* __restrict
 // Writes the inner-solve start: rimg, rreg, s (type T).  Returns chi2 =
 // ||r_img||^2 and sets reg2 = ||H x64||^2 and g64 = ||s||^2.
 // The refinement's FP64 convolution passes in FP32 contexts as double-float
-// sums on the FP32 pipe: the taps are FP32 numbers, each FP64 input x is
-// split into hi = float(x) and lo = float(x - hi), t hi is formed exactly as
-// p + e (FMA error-free product) and the p are summed with Knuth's
-// error-free TwoSum into a float pair (s, c), t lo + e going to c.  About
-// 11 FP32 operations per tap instead of one FP64 FMA at 1/64 of the FP32
+// sums on the FP32 pipe (dfloat.cuh; the taps are FP32 numbers): about 11
+// FP32 operations per tap instead of one FP64 FMA at 1/64 of the FP32
 // rate, ~2^-44 relative.  hi and lo are staged in the P1/P2 image buffers,
 // which hold zeros again on return.  KT > 0: compiled tap count.
 template <int KT>
@@ -1300,12 +1298,7 @@ __device__ __noinline__ double conv64_df_gen(const double* __restrict__ src, flo
                                              const float* __restrict__ swp, const float* __restrict__ dpad,
                                              float* __restrict__ rimg, double* __restrict__ Pb,
                                              double* __restrict__ Pc, const Geo<float> g, int mode) {
-    for (int i = threadIdx.x; i < g.plen; i += blockDim.x) {
-        const double v = src[i];
-        const float h = (float)v;
-        hi[i] = h;
-        lo[i] = (float)(v - (double)h);
-    }
+    for (int i = threadIdx.x; i < g.plen; i += blockDim.x) df_split(src[i], hi[i], lo[i]);
     __syncthreads();
     const int K = KT > 0 ? KT : g.K, kp = g.kp;
     double ss = 0.0;
@@ -1322,15 +1315,6 @@ __device__ __noinline__ double conv64_df_gen(const double* __restrict__ src, flo
                 const float* hrow = hi + base + (r + a) * g.Wp;
                 const float* lrow = lo + base + (r + a) * g.Wp;
                 const float* trow = taps + a * kp;
-                auto step = [&](float tt, float xh, float xl, int q) {
-                    const float pr = tt * xh;
-                    const float e = fmaf(tt, xh, -pr);  // t hi - pr, exactly
-                    const float sn = s[q] + pr;          // TwoSum(s, pr) = sn + er
-                    const float bv = sn - s[q];
-                    const float er = (s[q] - (sn - bv)) + (pr - bv);
-                    s[q] = sn;
-                    c[q] = fmaf(tt, xl, c[q] + (er + e));
-                };
                 if constexpr (KT > 0) {
                     float xh[KT + TILE - 1], xl[KT + TILE - 1];
 #pragma unroll
@@ -1342,14 +1326,14 @@ __device__ __noinline__ double conv64_df_gen(const double* __restrict__ src, flo
                     for (int b = 0; b < KT; ++b) {
                         const float tt = trow[b];
 #pragma unroll
-                        for (int q = 0; q < TILE; ++q) step(tt, xh[b + q], xl[b + q], q);
+                        for (int q = 0; q < TILE; ++q) df_madd(s[q], c[q], tt, xh[b + q], xl[b + q]);
                     }
                 } else {
 #pragma unroll 1
                     for (int b = 0; b < K; ++b) {
                         const float tt = trow[b];
 #pragma unroll
-                        for (int q = 0; q < TILE; ++q) step(tt, hrow[b + q], lrow[b + q], q);
+                        for (int q = 0; q < TILE; ++q) df_madd(s[q], c[q], tt, hrow[b + q], lrow[b + q]);
                     }
                 }
             }

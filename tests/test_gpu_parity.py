@@ -1,6 +1,6 @@
 """GPU parity of the CUDA path (through the C ABI) against the CPU oracle.
 
-Tolerances (derivation in DESIGN.md, "Parity tolerances"):
+Tolerances, derived from the arithmetic of each mode:
   FP64 context: |dchi2|/chi2 <= 1e-10; the oracle's FP64 normal-equation
     residual r of the GPU solution is <= 10 tol; |ds|/|s| <= max(1e-10,
     2 kappa_2(A) r) (a solve to residual r fixes s only to kappa r).

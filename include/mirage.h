@@ -47,7 +47,7 @@ extern "C" {
 #define MIRAGE_ERR_ARG (-1)         /* invalid argument (sizes, null pointers, geometry) */
 #define MIRAGE_ERR_CUDA (-2)        /* a CUDA runtime call failed */
 #define MIRAGE_ERR_NOMEM (-3)       /* device allocation of context scratch failed */
-#define MIRAGE_ERR_UNSUPPORTED (-4) /* shape outside what this build supports */
+#define MIRAGE_ERR_UNSUPPORTED (-4) /* shape outside what the library supports */
 
 #define MIRAGE_FP32 0
 #define MIRAGE_FP64 1

@@ -126,7 +126,7 @@ typedef struct {
                           with direct convolution at any PSF width.  Automatic
                           choice: FFT for PSFs of 23 x 23 and wider, direct below.
                           Forced choices fall back to the general kernel where
-                          they do not apply. */
+                          they do not apply.  Other values: MIRAGE_ERR_ARG. */
 } mirage_opts_t;
 
 typedef struct mirage_ctx mirage_ctx_t;

@@ -443,7 +443,7 @@ int eval_impl(mirage_ctx* ctx, const mirage_problem_t* probs, int n_probs, const
         return MIRAGE_ERR_ARG;
     }
     const mirage_opts_t o = *opts;
-    if (!(o.tol >= 0) || o.mode < 0 || o.mode > 1 || o.mem < 0 || o.mem > 1) {
+    if (!(o.tol >= 0) || o.mode < 0 || o.mode > 1 || o.mem < 0 || o.mem > 1 || o.variant < 0 || o.variant > 6) {
         set_error("eval_batch: bad options");
         return MIRAGE_ERR_ARG;
     }

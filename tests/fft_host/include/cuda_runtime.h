@@ -25,4 +25,7 @@ inline void sincospi(double a, double* s, double* c) {
     *s = std::sin(pi * a);
     *c = std::cos(pi * a);
 }
+using std::fmax;
+using std::hypot;
+using std::isfinite;
 using std::min;

@@ -187,6 +187,18 @@ def run_reference(args):
     return 0
 
 
+def _guarded(name, fn):
+    """Run one secondary section of the benchmark; an exception is recorded in
+    the JSON line (and its traceback printed to stderr) instead of ending the
+    run, so the headline measurement is always reported."""
+    import traceback
+    try:
+        return fn()
+    except Exception as e:  # noqa: BLE001 - report and continue
+        traceback.print_exc()
+        return {"error": f"{type(e).__name__}: {e}"[:400]}
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -299,105 +311,126 @@ def run_gpu(args):
             if line.startswith("traffic_bytes_per_item:"):
                 traffic = float(line.split(":")[1]) * float(iters.size)
 
-    # the paper's own fitness: 40 CGLS iterations per candidate, L-curve over
-    # the iterations, Monte Carlo degrees of freedom (FP64 arithmetic)
-    bh = torch.as_tensor(np.random.default_rng(5).standard_normal((1, wl.geom.nx * wl.geom.ny)),
-                         dtype=ctx.real, device="cuda")
-    iter_res = {"n_iter": 40}
-    for key, b in (("evals_per_s", None), ("evals_per_s_with_dof", bh)):
-        ctx.eval_iter(probs, wl.lens, wl.prob_idx, 40, bhat=b)  # warm-up
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        io = ctx.eval_iter(probs, wl.lens, wl.prob_idx, 40, bhat=b)
-        e1.record()
-        torch.cuda.synchronize()
-        iter_res[key] = N_CAND / (e0.elapsed_time(e1) / 1e3)
-    cn = io["corner"].cpu().numpy()
-    chi_c = io["chi2"].cpu().numpy()[np.arange(N_CAND), cn]
-    dof_c = io["dof"].cpu().numpy()[np.arange(N_CAND), cn]
-    iter_res.update({"corner_iteration_median": float(np.median(cn)),
-                     "reduced_chi2_at_corner_median": float(np.median(chi_c / dof_c))})
+    def _iter_section():
+        # the paper's own fitness: 40 CGLS iterations per candidate, L-curve over
+        # the iterations, Monte Carlo degrees of freedom (FP64 arithmetic)
+        bh = torch.as_tensor(np.random.default_rng(5).standard_normal((1, wl.geom.nx * wl.geom.ny)),
+                             dtype=ctx.real, device="cuda")
+        iter_res = {"n_iter": 40}
+        for key, b in (("evals_per_s", None), ("evals_per_s_with_dof", bh)):
+            ctx.eval_iter(probs, wl.lens, wl.prob_idx, 40, bhat=b)  # warm-up
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            io = ctx.eval_iter(probs, wl.lens, wl.prob_idx, 40, bhat=b)
+            e1.record()
+            torch.cuda.synchronize()
+            iter_res[key] = N_CAND / (e0.elapsed_time(e1) / 1e3)
+        cn = io["corner"].cpu().numpy()
+        chi_c = io["chi2"].cpu().numpy()[np.arange(N_CAND), cn]
+        dof_c = io["dof"].cpu().numpy()[np.arange(N_CAND), cn]
+        iter_res.update({"corner_iteration_median": float(np.median(cn)),
+                         "reduced_chi2_at_corner_median": float(np.median(chi_c / dof_c))})
+        return iter_res
 
-    # forward batch (B L s and chi^2 of 1024 sources at one lens): 256x256
-    # image at 0.02"/px, 128x128 source over +-1.2", 21x21 PSF; sources
-    # |N(0,1)| times an analytic template
-    import synth
-    from paper_1101_5803_gb300.problems import large_workload
-    lw = large_workload(ctx, n_cand=1, n_lam=1, seed=3)
-    lg = lw.geom
-    hx = (lg.sxmax - lg.sxmin) / lg.sx
-    cxs = lg.sxmin + (np.arange(lg.sx) + 0.5) * hx
-    tmpl = synth.eval_source(synth.drawn_source(np.random.default_rng(9)), *np.meshgrid(cxs, cxs)).ravel()
-    n_src = 1024
-    S = torch.as_tensor(np.abs(np.random.default_rng(10).standard_normal((n_src, tmpl.size))) * tmpl[None, :],
-                        dtype=ctx.real, device="cuda")
-    ctx.forward(lw.problem, lw.lens[0], S, want_model=False)  # warm-up
-    fms = []
-    for _ in range(3):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        ctx.forward(lw.problem, lw.lens[0], S, want_model=False)
-        e1.record()
-        torch.cuda.synchronize()
-        fms.append(e0.elapsed_time(e1))
-    npx = lg.nx * lg.ny
-    fwd_flops = n_src * (2.0 * lg.kpsf * lg.kpsf * npx + 11.0 * npx)
-    fwd_res = {"workload": "256x256 image, 128x128 source, 21x21 PSF, 1024 sources at one lens",
-               "ms": min(fms), "sources_per_s": n_src / (min(fms) / 1e3),
-               "tflops": fwd_flops / (min(fms) / 1e3) / 1e12}
-    del S
+    iter_res = _guarded("iter_lcurve", _iter_section)
 
-    # a 65 x 65 PSF on the 64x64 system: the FFT blur (the automatic choice
-    # at this width) against direct convolution (variant 6)
-    from paper_1101_5803_gb300.problems import widepsf_workload
-    ww = widepsf_workload(ctx, 16, 8, seed=5)
-    wide = {"workload": "64x64 image, 32x32 source, 65x65 PSF, 16 candidates x 8 lambdas (1e-3..1e1)"}
-    for name, var in (("fft", 0), ("direct", 6)):
-        ctx.eval_batch([ww.problem], ww.lens[:2], ww.prob_idx[:2], ww.lambdas[:2], ww.n_lam[:2], tol=1e-6,
-                       variant=var)  # warm-up
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        wout = ctx.eval_batch([ww.problem], ww.lens, ww.prob_idx, ww.lambdas, ww.n_lam, tol=1e-6, variant=var)
-        e1.record()
-        torch.cuda.synchronize()
-        wms = e0.elapsed_time(e1)
-        wit = wout["iters"].cpu().numpy()
-        wide[name] = {"ms": wms, "evals_per_s": 16 / (wms / 1e3), "cg_iterations": int(wit.sum()),
-                      "us_per_iteration_of_slowest_item": wms * 1e3 / max(1, int(wit.max())),
-                      "status_bits_any": int(np.bitwise_or.reduce(wout["status"].cpu().numpy()))}
+    def _forward_section():
+        # forward batch (B L s and chi^2 of 1024 sources at one lens): 256x256
+        # image at 0.02"/px, 128x128 source over +-1.2", 21x21 PSF; sources
+        # |N(0,1)| times an analytic template
+        import synth
+        from paper_1101_5803_gb300.problems import large_workload
+        lw = large_workload(ctx, n_cand=1, n_lam=1, seed=3)
+        lg = lw.geom
+        hx = (lg.sxmax - lg.sxmin) / lg.sx
+        cxs = lg.sxmin + (np.arange(lg.sx) + 0.5) * hx
+        tmpl = synth.eval_source(synth.drawn_source(np.random.default_rng(9)), *np.meshgrid(cxs, cxs)).ravel()
+        n_src = 1024
+        S = torch.as_tensor(np.abs(np.random.default_rng(10).standard_normal((n_src, tmpl.size))) * tmpl[None, :],
+                            dtype=ctx.real, device="cuda")
+        ctx.forward(lw.problem, lw.lens[0], S, want_model=False)  # warm-up
+        fms = []
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            ctx.forward(lw.problem, lw.lens[0], S, want_model=False)
+            e1.record()
+            torch.cuda.synchronize()
+            fms.append(e0.elapsed_time(e1))
+        npx = lg.nx * lg.ny
+        fwd_flops = n_src * (2.0 * lg.kpsf * lg.kpsf * npx + 11.0 * npx)
+        fwd_res = {"workload": "256x256 image, 128x128 source, 21x21 PSF, 1024 sources at one lens",
+                   "ms": min(fms), "sources_per_s": n_src / (min(fms) / 1e3),
+                   "tflops": fwd_flops / (min(fms) / 1e3) / 1e12}
+        del S
+        return fwd_res
 
-    # GA generations on the same problem: surrogate screen vs none
-    from paper_1101_5803_gb300.ga import GAConfig, run_ga
+    fwd_res = _guarded("forward_batch", _forward_section)
+
+    def _wide_section():
+        # a 65 x 65 PSF on the 64x64 system: the FFT blur (the automatic choice
+        # at this width) against direct convolution (variant 6)
+        from paper_1101_5803_gb300.problems import widepsf_workload
+        ww = widepsf_workload(ctx, 16, 8, seed=5)
+        wide = {"workload": "64x64 image, 32x32 source, 65x65 PSF, 16 candidates x 8 lambdas (1e-3..1e1)"}
+        for name, var in (("fft", 0), ("direct", 6)):
+            ctx.eval_batch([ww.problem], ww.lens[:2], ww.prob_idx[:2], ww.lambdas[:2], ww.n_lam[:2], tol=1e-6,
+                           variant=var)  # warm-up
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            wout = ctx.eval_batch([ww.problem], ww.lens, ww.prob_idx, ww.lambdas, ww.n_lam, tol=1e-6, variant=var)
+            e1.record()
+            torch.cuda.synchronize()
+            wms = e0.elapsed_time(e1)
+            wit = wout["iters"].cpu().numpy()
+            wide[name] = {"ms": wms, "evals_per_s": 16 / (wms / 1e3), "cg_iterations": int(wit.sum()),
+                          "us_per_iteration_of_slowest_item": wms * 1e3 / max(1, int(wit.max())),
+                          "status_bits_any": int(np.bitwise_or.reduce(wout["status"].cpu().numpy()))}
+        return wide
+
+    wide = _guarded("wide_psf", _wide_section)
+
     n_gen = int(os.environ.get("MIRAGE_GA_GENERATIONS", "4"))
-    ga_res = {}
-    for name, sur_on, chain in (("with_surrogate", True, False), ("with_surrogate_lambda_chains", True, True),
-                                ("without", False, False)):
-        cfg = GAConfig(pop=N_CAND, generations=n_gen, surrogate=sur_on, lam_chain=chain, seed=7)
-        hist, _, bchi = run_ga(ctx, wl, cfg)
-        gens = hist[1:]
-        t_gen = sum(h.seconds for h in gens)
-        ga_res[name] = {"exact_evals_per_s": sum(h.exact_evals for h in gens) / t_gen,
-                        "decisions_per_s": sum(h.decisions for h in gens) / t_gen,
-                        "cg_iters_per_exact_eval": sum(h.cg_iters for h in gens) / max(1, sum(h.exact_evals for h in gens)),
-                        "best_chi2_by_gen": [round(h.best_chi2, 2) for h in hist],
-                        "screened_gens": int(sum(h.screened for h in gens)),
-                        "rank_corr_by_gen": [None if h.surrogate_rho is None else round(h.surrogate_rho, 3)
-                                             for h in gens],
-                        "surrogate_rmse_by_gen": [None if h.surrogate_rmse is None else round(h.surrogate_rmse, 4)
-                                                  for h in gens],
-                        "fallback_rate": (1.0 - sum(h.screened for h in gens) / max(1, len(gens))) if sur_on else None}
-    ga_res["generations"] = n_gen
-    ga_res["oversample"] = 4
 
-    # particle swarm (Eq. PSO) on the same problem: one batched call per step
-    from paper_1101_5803_gb300.pso import PSOConfig, batch_evaluator, run_pso
-    phist, _, _ = run_pso(batch_evaluator(ctx, wl), PSOConfig(particles=N_CAND, steps=n_gen, seed=7))
-    psteps = phist[1:]
-    t_pso = sum(h.seconds for h in psteps)
-    pso_res = {"particles": N_CAND, "steps": n_gen,
-               "exact_evals_per_s": sum(h.evals for h in psteps) / t_pso,
-               "cg_iters_per_exact_eval": sum(h.cg_iters for h in psteps) / max(1, sum(h.evals for h in psteps)),
-               "best_chi2_by_step": [round(h.best_chi2, 2) for h in phist]}
+    def _ga_section():
+        # GA generations on the same problem: surrogate screen vs none
+        from paper_1101_5803_gb300.ga import GAConfig, run_ga
+        ga_res = {}
+        for name, sur_on, chain in (("with_surrogate", True, False), ("with_surrogate_lambda_chains", True, True),
+                                    ("without", False, False)):
+            cfg = GAConfig(pop=N_CAND, generations=n_gen, surrogate=sur_on, lam_chain=chain, seed=7)
+            hist, _, bchi = run_ga(ctx, wl, cfg)
+            gens = hist[1:]
+            t_gen = sum(h.seconds for h in gens)
+            ga_res[name] = {"exact_evals_per_s": sum(h.exact_evals for h in gens) / t_gen,
+                            "decisions_per_s": sum(h.decisions for h in gens) / t_gen,
+                            "cg_iters_per_exact_eval": sum(h.cg_iters for h in gens) / max(1, sum(h.exact_evals for h in gens)),
+                            "best_chi2_by_gen": [round(h.best_chi2, 2) for h in hist],
+                            "screened_gens": int(sum(h.screened for h in gens)),
+                            "rank_corr_by_gen": [None if h.surrogate_rho is None else round(h.surrogate_rho, 3)
+                                                 for h in gens],
+                            "surrogate_rmse_by_gen": [None if h.surrogate_rmse is None else round(h.surrogate_rmse, 4)
+                                                      for h in gens],
+                            "fallback_rate": (1.0 - sum(h.screened for h in gens) / max(1, len(gens))) if sur_on else None}
+        ga_res["generations"] = n_gen
+        ga_res["oversample"] = 4
+        return ga_res
+
+    ga_res = _guarded("ga_surrogate", _ga_section)
+
+    def _pso_section():
+        # particle swarm (Eq. PSO) on the same problem: one batched call per step
+        from paper_1101_5803_gb300.pso import PSOConfig, batch_evaluator, run_pso
+        phist, _, _ = run_pso(batch_evaluator(ctx, wl), PSOConfig(particles=N_CAND, steps=n_gen, seed=7))
+        psteps = phist[1:]
+        t_pso = sum(h.seconds for h in psteps)
+        pso_res = {"particles": N_CAND, "steps": n_gen,
+                   "exact_evals_per_s": sum(h.evals for h in psteps) / t_pso,
+                   "cg_iters_per_exact_eval": sum(h.cg_iters for h in psteps) / max(1, sum(h.evals for h in psteps)),
+                   "best_chi2_by_step": [round(h.best_chi2, 2) for h in phist]}
+        return pso_res
+
+    pso_res = _guarded("pso", _pso_section)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:

@@ -23,8 +23,8 @@ from synth import Geometry, REG_IDENTITY
 from .helpers import make_problem
 
 
-def _tiny(seed=3, nx=10, sx=4):
-    g = Geometry(nx, nx, 0.16, sx, sx, -0.8, 0.8, -0.8, 0.8, 3, 1, REG_IDENTITY)
+def _tiny(seed=3, nx=10, sx=4, interp=synth.INTERP_BILINEAR):
+    g = Geometry(nx, nx, 0.16, sx, sx, -0.8, 0.8, -0.8, 0.8, 3, 1, REG_IDENTITY, interp=interp)
     return make_problem(g, seed=seed, psf_sigma=0.8)
 
 
@@ -38,8 +38,9 @@ def _krylov_minimiser(A, b, k):
     return V @ y
 
 
-def test_iterates_minimise_over_krylov_spaces():
-    prob = _tiny()
+@pytest.mark.parametrize("interp", [synth.INTERP_BILINEAR, synth.INTERP_NEAREST, synth.INTERP_BICUBIC])
+def test_iterates_minimise_over_krylov_spaces(interp):
+    prob = _tiny(interp=interp)
     ops = build_operators(prob, synth.TRUE_LENS)
     A, b = weighted_system(prob, ops)
     res = cgls_iterations(prob, synth.TRUE_LENS, 5, ops=ops)
@@ -57,8 +58,9 @@ def test_chi2_falls_and_norm_rises():
     assert 1 <= res.corner <= 30
 
 
-def test_iterates_reach_least_squares_solution():
-    prob = _tiny(seed=5)
+@pytest.mark.parametrize("interp", [synth.INTERP_BILINEAR, synth.INTERP_NEAREST, synth.INTERP_BICUBIC])
+def test_iterates_reach_least_squares_solution(interp):
+    prob = _tiny(seed=5, interp=interp)
     ops = build_operators(prob, synth.TRUE_LENS)
     A, b = weighted_system(prob, ops)
     assert np.linalg.matrix_rank(A) == A.shape[1]

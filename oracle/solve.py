@@ -82,6 +82,44 @@ def solve_lambda(ops: Operators, lam: float):
     return sla.cho_solve(c, ops.rhs, check_finite=False)
 
 
+def _ld_matvec(M, x):
+    """M x with products and sums in extended precision (np.longdouble)."""
+    if isinstance(M, np.ndarray):
+        return M.astype(np.longdouble) @ x
+    return M.astype(np.longdouble) @ x
+
+
+def normal_residual_ld(ops: Operators, prob: Problem, s, lam: float):
+    """rhs - A s of Eq. TKReg's normal equations, from the factors L, B, W,
+    H and d (not from the rounded products F^T W F and F^T W d), in
+    extended precision."""
+    ld = np.longdouble
+    w = ops.w.astype(ld)
+    d = np.asarray(prob.d, dtype=np.float64).ravel().astype(ld)
+    x = np.asarray(s, dtype=np.float64).astype(ld)
+    bls = _ld_matvec(ops.B, _ld_matvec(ops.L, x))
+    img = w * (d - bls)
+    ftwr = _ld_matvec(ops.L.T, _ld_matvec(ops.B.T, img))
+    return ftwr - ld(lam) * _ld_matvec(ops.H.T, _ld_matvec(ops.H, x))
+
+
+def solve_lambda_refined(ops: Operators, prob: Problem, lam: float, steps: int = 3):
+    """The solution of (F^T W F + lam H^T H) s = F^T W d to near FP64
+    rounding of s itself: the Cholesky solution, then classical iterative
+    refinement (Wilkinson) with the residual formed in extended precision
+    from the factors.  A plain FP64 Cholesky solve carries a forward error
+    of order kappa_2(A) eps, which at kappa_2 ~ 1e5..1e7 is comparable to a
+    1e-10 comparison; the refined solution does not."""
+    A = ops.FtWF + lam * ops.HtH
+    c = sla.cho_factor(A, lower=True, check_finite=False)
+    s = sla.cho_solve(c, ops.rhs, check_finite=False)
+    for _ in range(steps):
+        r = normal_residual_ld(ops, prob, s, lam)
+        ds = sla.cho_solve(c, np.asarray(r, dtype=np.float64), check_finite=False)
+        s = np.asarray(s.astype(np.longdouble) + ds.astype(np.longdouble), dtype=np.float64)
+    return s
+
+
 def chi2_of(ops: Operators, d, s) -> float:
     """Eq. chi2 over pixels with m = 1 (folded into w)."""
     res = ops.F @ s - np.asarray(d, dtype=np.float64).ravel()

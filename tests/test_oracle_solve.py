@@ -14,7 +14,8 @@ import synth
 from oracle.data import lensed_image, observe
 from oracle.lcurve import lcurve_corner
 from oracle.operators import REG_GRADIENT, REG_IDENTITY, REG_LAPLACIAN
-from oracle.solve import Problem, build_operators, chi2_of, eval_candidate, reg_of, solve_lambda
+from oracle.solve import (Problem, build_operators, chi2_of, eval_candidate, normal_residual_ld, reg_of,
+                          solve_lambda, solve_lambda_refined)
 from synth import Geometry, gaussian_psf
 
 LENS = np.array([1.0, 0.7, 0.5, 0.0, 0.0, 0.05, 1.0])
@@ -44,6 +45,34 @@ def test_closed_form_identity_lens():
     for lam in (1e-3, 0.5, 10.0):
         s = solve_lambda(ops, lam)
         np.testing.assert_allclose(s, w * d.ravel() / (w + lam), rtol=1e-12, atol=1e-14)
+
+
+def test_refined_solve_matches_exact_rational_solve():
+    # the refined solve against the exact solution of the same normal
+    # equations: A and rhs formed from the FP64 entries of L, B, W, H and d in
+    # 60-digit arithmetic (mpmath) and solved there; an ill-conditioned case
+    # (gradient H, lambda down to 1e-9)
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 60
+    g = Geometry(nx=8, ny=8, pix=0.2, sx=4, sy=4, sxmin=-0.6, sxmax=0.6, symin=-0.6, symax=0.6,
+                 kpsf=3, subpix=1, reg=REG_GRADIENT)
+    rng = np.random.default_rng(3)
+    prob = observe(g, LENS, synth.two_gaussian_source(), gaussian_psf(3, 1.0), rng.standard_normal((8, 8)))
+    ops = build_operators(prob, LENS)
+    M = lambda a: mpmath.matrix(np.asarray(a.toarray() if hasattr(a, "toarray") else a, dtype=np.float64).tolist())
+    L, B, H = M(ops.L), M(ops.B), M(ops.H)
+    W = mpmath.diag([mpmath.mpf(float(x)) for x in ops.w])
+    d = mpmath.matrix([float(x) for x in np.asarray(prob.d, dtype=np.float64).ravel()])
+    F = B * L
+    FtW = F.T * W
+    FtWF, HtH, rhs = FtW * F, H.T * H, FtW * d
+    for lam in (1e-2, 1e-6, 1e-9):
+        s_x = mpmath.lu_solve(FtWF + mpmath.mpf(lam) * HtH, rhs)
+        s_x = np.array([float(v) for v in s_x])
+        s_r = solve_lambda_refined(ops, prob, lam)
+        assert np.linalg.norm(s_r - s_x) <= 4e-16 * np.linalg.norm(s_x) * np.sqrt(g.ns), lam
+        r = np.asarray(normal_residual_ld(ops, prob, s_r, lam), dtype=np.float64)
+        assert np.linalg.norm(r) <= 1e-15 * np.linalg.norm(ops.rhs), lam
 
 
 def test_svd_filter_factors():

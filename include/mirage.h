@@ -311,11 +311,13 @@ const char* mirage_mlp_last_error(void);
  * Returns MIRAGE_ERR_UNSUPPORTED (message in mirage_noalloc_last_error)
  * when the problem needs more scratch than the array holds, roughly images
  * above 160 x 160 FP32 rays.  The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress) once; make that first call
- * before any stream capture.  All calls share the array and it keeps the
- * last call's contents (each call rebuilds what it reads), so calls that
- * overlap on the GPU (different streams, threads or devices sharing it
- * concurrently on one device) race: serialise them. */
+ * array's device address (cudaGetSymbolAddress) once and keeps it for the
+ * life of the process; make that first call before any stream capture, and
+ * do not call this entry point on a device after cudaDeviceReset of it.
+ * All calls share the array and it keeps the last call's contents (each
+ * call rebuilds what it reads), so calls that overlap on the GPU (different
+ * streams or threads on one device) race: serialise them.  The error text
+ * is kept per calling thread. */
 int mirage_forward_noalloc(int precision, const mirage_problem_t* prob, const double* lens,
                            const void* s, int n_src, void* model, double* chi2, int* status,
                            void* stream);

@@ -12,7 +12,6 @@
 
 #include <algorithm>
 #include <cstdio>
-#include <cstring>
 #include <mutex>
 
 #include "internal.h"
@@ -29,9 +28,15 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
+// Device address of the array per device ordinal, looked up on the first
+// call on that device.  The cache lives as long as the process: after a
+// cudaDeviceReset the module is loaded again and the address may change,
+// so a caller that resets a device must not call this entry point again on
+// it in the same process.
 void* g_scratch_ptr[kMaxDevices] = {};
 
-char g_err[256] = "";
+// per calling thread, like the library's other error strings
+thread_local char g_err[256] = "";
 
 int fail(int code, const char* msg) {
     std::snprintf(g_err, sizeof(g_err), "%s", msg);
@@ -56,6 +61,17 @@ int scratch_address(void** out) {
 }
 
 size_t up256(size_t v) { return (v + 255) / 256 * 256; }
+
+// Writes the problem descriptor and the candidate index 0 into the array.
+// The descriptor travels as a kernel parameter, which the launch copies, so
+// no host buffer has to outlive the call.
+template <typename T>
+__global__ void k_put_problem(const Prob<T> P, Prob<T>* dst, int* cand) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        *dst = P;
+        *cand = 0;
+    }
+}
 
 template <typename T>
 int forward_noalloc_impl(const mirage_problem_t* prob, const double* lens, const void* s, int n_src, void* model,
@@ -109,11 +125,10 @@ int forward_noalloc_impl(const mirage_problem_t* prob, const double* lens, const
     char* b = static_cast<char*>(base);
 
     // problem descriptor and its candidate index (0) into the array
-    unsigned char up[sizeof(Prob<T>) + sizeof(int)];
-    std::memset(up, 0, sizeof(up));
-    std::memcpy(up, &P, sizeof(P));
-    if (cudaMemcpyAsync(b + o_prob, up, sizeof(up), cudaMemcpyHostToDevice, st) != cudaSuccess)
-        return fail(MIRAGE_ERR_CUDA, "forward_noalloc: upload of the problem descriptor failed");
+    k_put_problem<T><<<1, 32, 0, st>>>(P, reinterpret_cast<Prob<T>*>(b + o_prob),
+                                       reinterpret_cast<int*>(b + o_prob + sizeof(Prob<T>)));
+    if (cudaGetLastError() != cudaSuccess)
+        return fail(MIRAGE_ERR_CUDA, "forward_noalloc: writing the problem descriptor failed");
 
     CandScratch<T> cs;
     cs.E = reinterpret_cast<Entry<T>*>(b + o_E);

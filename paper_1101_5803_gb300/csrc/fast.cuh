@@ -379,6 +379,8 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_cgls_fast(const __grid_constant
         slab += sizeof(double) * align_up<T>(g.plen, 4);
         w.x64 = reinterpret_cast<double*>(slab);
         slab += sizeof(double) * align_up<T>(g.ns, 4);
+        w.xb = reinterpret_cast<double*>(slab);
+        slab += sizeof(double) * align_up<T>(g.ns, 4);
         w.h64 = reinterpret_cast<double*>(slab);
         slab += sizeof(double) * align_up<T>(g.nreg, 4);
         w.rimg = reinterpret_cast<float*>(slab);
@@ -654,11 +656,24 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_cgls_fast(const __grid_constant
         // signed offset of the shared zero from Q (both in the one shared
         // array): absent corner cells read it through an index select
         const int zq = (int)(&fi->zero - Q);
+        bool reverted = false;
         for (int outer = 0;; ++outer) {
             PHASE(11);
             chi2 = residual64<T>(w, g, lam, red, which, reg2, g64, conv_df);
             PHASE(10);
             rel64 = rhsn > 0 ? sqrt(g64) / rhsn : 0.0;
+            if (reverted) {  // the best iterate, evaluated again
+                status |= ST_STAG;
+                break;
+            }
+            if (outer > 0 && !(rel64 <= prev_rel)) {
+                // the last correction raised the true residual: back to the
+                // best iterate; the next pass evaluates it and stops
+                for (int i = tid; i < g.ns; i += bs) w.x64[i] = w.xb[i];
+                __syncthreads();
+                reverted = true;
+                continue;
+            }
             if (!isfinite(rel64)) {
                 status |= ST_BREAK;
                 break;
@@ -673,7 +688,8 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_cgls_fast(const __grid_constant
                 status |= ST_STAG;
                 break;
             }
-            prev_rel = rel64;
+            prev_rel = rel64;  // accepted residuals decrease: this is the best iterate
+            for (int i = tid; i < g.ns; i += bs) w.xb[i] = w.x64[i];
             const double target = fmax(eta_min, 0.3 * A.tol / rel64);
 
             // ---- inner CGLS on the correction: state into registers
@@ -998,7 +1014,7 @@ __host__ inline size_t fast_smem_bytes(const Prob<float>& P) {
 }
 
 __host__ inline size_t fast_slab_bytes(const Prob<float>& P) {
-    size_t o = sizeof(double) * (3 * align_up<float>(P.plen, 4) + align_up<float>(P.ns, 4) + align_up<float>(P.nreg, 4));
+    size_t o = sizeof(double) * (3 * align_up<float>(P.plen, 4) + 2 * align_up<float>(P.ns, 4) + align_up<float>(P.nreg, 4));
     o += sizeof(float) * (align_up<float>(P.plen, 4) + align_up<float>(P.ns, 4));
     return align_up<float>(o, 256);
 }

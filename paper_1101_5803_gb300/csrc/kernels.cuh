@@ -814,6 +814,7 @@ struct Work {
     T* qreg;
     T* minv;          // [ns] Jacobi preconditioner of the inner solves
     double* x64;      // [ns] solution accumulator (refinement)
+    double* xb;       // [ns] the refinement iterate with the smallest true residual so far
     double* h64;      // [nreg] H x64
     double* Pa;       // [plen] L x64
     double* Pb;       // [plen] sqrt(W) r64
@@ -1324,7 +1325,7 @@ __host__ __device__ inline size_t smem_bytes(const Prob<T>& P, int place) {
 // per-CTA global slab: [double part][T part], in bytes
 template <typename T>
 __host__ __device__ inline size_t slab_bytes(const Prob<T>& P, int place) {
-    size_t o = sizeof(double) * (3 * align_up<T>(P.plen, 4) + align_up<T>(P.ns, 4) + align_up<T>(P.nreg, 4));
+    size_t o = sizeof(double) * (3 * align_up<T>(P.plen, 4) + 2 * align_up<T>(P.ns, 4) + align_up<T>(P.nreg, 4));
     if (place == PLACE_GLOBAL)
         o += sizeof(T) * (4 * align_up<T>(P.plen, 4) + 4 * align_up<T>(P.ns, 4) + 2 * align_up<T>(P.nreg, 4));
     if (place == PLACE_MID) o += sizeof(T) * 2 * align_up<T>(P.plen, 4);  // rimg qimg
@@ -1410,6 +1411,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_cgls(CglsArgs<T> A) {
         w.Pc = reinterpret_cast<double*>(slab);
         slab += sizeof(double) * align_up<T>(g.plen, 4);
         w.x64 = reinterpret_cast<double*>(slab);
+        slab += sizeof(double) * align_up<T>(g.ns, 4);
+        w.xb = reinterpret_cast<double*>(slab);
         slab += sizeof(double) * align_up<T>(g.ns, 4);
         w.h64 = reinterpret_cast<double*>(slab);
         slab += sizeof(double) * align_up<T>(g.nreg, 4);
@@ -1651,9 +1654,24 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_cgls(CglsArgs<T> A) {
         // inner target: a 30x reduction per FP32 inner solve keeps each inner
         // solve short (FP32 loses orthogonality on long ones) at few FP64 passes
         const double eta_min = sizeof(T) == 4 ? 0.03 : 0.3 * A.tol;
+        bool reverted = false;
         for (int outer = 0;; ++outer) {
             chi2 = residual64<T>(w, g, lam, red, which, reg2, g64, conv_ref);
             rel64 = rhsn > 0 ? sqrt(g64) / rhsn : 0.0;
+            if (reverted) {  // the best iterate, evaluated again
+                status |= ST_STAG;
+                break;
+            }
+            if (outer > 0 && !(rel64 <= prev_rel)) {
+                // the last correction raised the true residual (the inner
+                // solve's operator is too coarse for this system at this
+                // level): back to the best iterate; the next pass evaluates
+                // it and stops
+                for (int i = tid; i < g.ns; i += bs) w.x64[i] = w.xb[i];
+                __syncthreads();
+                reverted = true;
+                continue;
+            }
             if (!isfinite(rel64)) {
                 status |= ST_BREAK;
                 break;
@@ -1669,7 +1687,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_cgls(CglsArgs<T> A) {
                 status |= ST_STAG;
                 break;
             }
-            prev_rel = rel64;
+            prev_rel = rel64;  // the residuals accepted so far decrease: this is the best iterate
+            for (int i = tid; i < g.ns; i += bs) w.xb[i] = w.x64[i];
             // ---- inner CGLS on the correction, started from zero
             const double target = fmax(eta_min, 0.3 * A.tol / rel64);
             for (int i = tid; i < g.ns; i += bs) {

@@ -1,15 +1,28 @@
 """GPU parity of the CUDA path (through the C ABI) against the CPU oracle.
 
-Tolerances, derived from the arithmetic of each mode:
-  FP64 context: |dchi2|/chi2 <= 1e-10; the oracle's FP64 normal-equation
-    residual r of the GPU solution is <= 10 tol; |ds|/|s| <= max(1e-10,
-    2 kappa_2(A) r) (a solve to residual r fixes s only to kappa r).
+Tolerances, derived from the arithmetic of each mode (r is the oracle's
+relative normal-equation residual of the GPU solution, kappa = kappa_2(A)):
+  FP64 context:
+    * chi2: |dchi2|/chi2 <= 1e-10 everywhere;
+    * r <= 10 tol;
+    * s and R = ||Hs||^2 at solver tolerance 1e-13 (32x32 workload, single
+      lambda and the 10-lambda grid): |ds|/|s| <= 1e-10 and |dR|/R <= 1e-10
+      literally, and the library's R equals ||H s_gpu||^2 to 1e-12.  Printed
+      beside each: kappa r and b_R = 2 kappa r ||H^T H s|| ||s|| / R +
+      (kappa r ||H||_2 ||s||)^2 / R, the worst-case first- and second-order
+      change of s and R for a solve to residual r (both above 1e-10 at small
+      lambda, so the literal gates are met, not implied, there);
+    * at the looser tolerance 1e-10, |ds|/|s| <= max(1e-10, 2 kappa r): a
+      solve stopped at residual r fixes s only to kappa r.
   FP32 context (FP32 matvecs inside an FP64 residual refinement), tol 1e-6:
-    * chi2: |dchi2|/chi2 <= 1e-5 on every (candidate, lambda);
-    * r <= 10 tol (the FP32-rounded ray-trace weights and PSF perturb A by
-      ~1e-7 relative, so the oracle's residual can sit above tol);
-    * s: |ds|/|s| <= 1e-4 where the oracle's kappa_2(A) <= 1e2, and
-      <= 2 kappa_2(A) r + 1e-5 elsewhere;
+    * chi2: |dchi2|/chi2 <= 1e-5 on every (candidate, lambda), or the change
+      the residual itself implies where that is larger; how often the
+      implied bound decided is counted and printed;
+    * r <= 10 tol (an FP32 context forms sqrt(W) = m/sigma in FP32, which
+      changes W by up to 1.2e-7 relative, and returns s rounded to FP32, so
+      the oracle's residual of the exact problem can sit above tol);
+    * s: |ds|/|s| <= 1e-4 where kappa <= 1e2, and <= 2 kappa r + 1e-5
+      elsewhere (error and kappa reported per item);
     * the library's reported residual is within 0.5 r + 2e-6 of r.
 """
 import numpy as np
@@ -18,7 +31,7 @@ import torch
 
 import synth
 from oracle.lcurve import lcurve_corner
-from oracle.solve import build_operators, eval_candidate, forward_chi2, solve_lambda
+from oracle.solve import build_operators, eval_candidate, forward_chi2, solve_lambda_refined
 from synth import Geometry, REG_GRADIENT, REG_IDENTITY, REG_LAPLACIAN
 
 from .helpers import device_problem, host_problem, make_problem, rel
@@ -111,7 +124,7 @@ def test_eval_fp64_small_single_lambda(mods, ctx64, tol):
     prob = make_problem(g, seed=0, psf_sigma=1.0, fixed_source=True)
     lens = synth.TRUE_LENS
     ops = build_operators(prob, lens)
-    s_o = solve_lambda(ops, 1e-2)
+    s_o = solve_lambda_refined(ops, prob, 1e-2)
     out = ctx64.eval_batch([device_problem(prob, torch.float64)], _lens_t(lens), [0], _lam_t([1e-2], 1), [1],
                            tol=tol, maxit=50000)
     s_g = out["s"][0].cpu().numpy()
@@ -119,8 +132,13 @@ def test_eval_fp64_small_single_lambda(mods, ctx64, tol):
     rr = np.linalg.norm(ops.rhs - A @ s_g) / np.linalg.norm(ops.rhs)
     ev = np.linalg.eigvalsh(A)
     kap = ev[-1] / ev[0]
+    err = rel(s_g, s_o)
+    print(f"fp64 32x32 tol {tol:g}: kappa {kap:.3e} r {rr:.3e} kappa*r {kap * rr:.3e} |ds|/|s| {err:.3e}")
     assert rr <= 10 * tol, rr
-    assert rel(s_g, s_o) <= max(1e-10, 2 * kap * rr), (rel(s_g, s_o), kap, rr)
+    if tol <= 1e-13:
+        assert err <= 1e-10, (err, kap, rr)   # the literal FP64 gate on s
+    else:
+        assert err <= max(1e-10, 2 * kap * rr), (err, kap, rr)
     from oracle.solve import chi2_of
     c_o = chi2_of(ops, prob.d, s_o)
     assert abs(out["chi2"][0, 0].item() - c_o) <= 1e-10 * c_o
@@ -128,30 +146,50 @@ def test_eval_fp64_small_single_lambda(mods, ctx64, tol):
 
 
 def test_eval_fp64_grid_and_corner(mods, ctx64):
+    from oracle.solve import reg_of
     g = synth.geom_small_fp64()
     prob = make_problem(g, seed=1, psf_sigma=1.0)
     lams = synth.lambda_grid(10)
     lenses = [synth.TRUE_LENS, [0.95, 0.75, 0.4, 0.02, -0.03, 0.03, 0.8]]
     out = ctx64.eval_batch([device_problem(prob, torch.float64)], _lens_t(lenses), [0, 0], _lam_t(lams, 2),
-                           [10, 10], tol=1e-12, maxit=50000, want_all_x=True)
+                           [10, 10], tol=1e-13, maxit=50000, want_all_x=True)
     for c, lens in enumerate(lenses):
         r = eval_candidate(prob, lens, lams)
         ops = build_operators(prob, lens)
         np.testing.assert_allclose(out["chi2"][c].cpu().numpy(), r.chi2, rtol=1e-10)
-        np.testing.assert_allclose(out["reg"][c].cpu().numpy(), r.reg, rtol=1e-6)
         X = out["all_x"][c].cpu().numpy()
+        reg_g = out["reg"][c].cpu().numpy()
+        hn = np.linalg.norm(ops.H.toarray(), 2)
         for k in range(10):
             A = ops.FtWF + lams[k] * ops.HtH
-            rr = np.linalg.norm(ops.rhs - A @ X[k, :g.ns]) / np.linalg.norm(ops.rhs)
+            s_o = solve_lambda_refined(ops, prob, lams[k])
+            s_g = X[k, :g.ns]
+            rr = np.linalg.norm(ops.rhs - A @ s_g) / np.linalg.norm(ops.rhs)
             ev = np.linalg.eigvalsh(A)
-            assert rr <= 1e-11, (c, k, rr)
-            assert rel(X[k, :g.ns], r.s[k]) <= max(1e-10, 2 * ev[-1] / ev[0] * rr), (c, k)
+            kr = ev[-1] / ev[0] * rr
+            assert rr <= 1e-12, (c, k, rr)
+            err = rel(s_g, s_o)
+            assert err <= 1e-10, (c, k, err, kr)   # the literal FP64 gate on s
+            # R: the library's value is ||H s_gpu||^2, and close to the exact R
+            assert abs(reg_g[k] - reg_of(ops, s_g)) <= 1e-12 * reg_g[k], (c, k)
+            reg_o = reg_of(ops, s_o)
+            ds = kr * np.linalg.norm(s_o)
+            b_r = (2 * np.linalg.norm(ops.HtH @ s_o) * ds + (hn * ds) ** 2) / reg_o
+            d_r = abs(reg_g[k] - reg_o) / reg_o
+            assert d_r <= 1e-10, (c, k, d_r, b_r)   # the literal FP64 gate on R
+            print(f"fp64 grid c{c} lam {lams[k]:.1e}: kappa*r {kr:.2e} |ds|/|s| {err:.2e} |dR|/R {d_r:.2e} "
+                  f"(b_R {b_r:.2e})")
         assert int(out["corner"][c].item()) == r.corner
         np.testing.assert_allclose(out["kappa"][c].cpu().numpy(), r.kappa, rtol=1e-6, atol=1e-9)
 
 
-def _fp32_checks(out, prob, lenses, lams, tol):
+def _fp32_checks(out, prob, lenses, lams, tol, records=None):
+    """The FP32 gates of the module docstring on every (candidate, lambda).
+
+    ``records`` collects one dict per item (kappa, residual, errors, which
+    chi2 bound decided)."""
     from oracle.solve import chi2_of
+    n_implied = 0
     for c, lens in enumerate(lenses):
         ops = build_operators(prob, lens)
         r = eval_candidate(prob, lens, lams)
@@ -178,17 +216,43 @@ def _fp32_checks(out, prob, lenses, lams, tol):
             # residual itself implies (second order in r, first order via lam)
             Ainv_r = np.linalg.solve(A, res)
             implied = 4 * abs(res @ Ainv_r) + 4 * lam * abs((ops.HtH @ r.s[k]) @ Ainv_r)
-            assert abs(chi_g - r.chi2[k]) <= max(1e-5 * r.chi2[k], implied), info + (chi_g, r.chi2[k], implied)
+            dchi = abs(chi_g - r.chi2[k])
+            assert dchi <= max(1e-5 * r.chi2[k], implied), info + (chi_g, r.chi2[k], implied)
+            n_implied += dchi > 1e-5 * r.chi2[k]
             ev = np.linalg.eigvalsh(A)
             kap = ev[-1] / ev[0]
             err = rel(s_g, r.s[k])
             bound = 1e-4 if kap <= 1e2 else 2 * kap * rr + 1e-5
             assert err <= bound, info + (err, kap)
+            if records is not None:
+                records.append({"c": c, "k": k, "lam": float(lam), "kappa": float(kap), "r": float(rr),
+                                "s_err": float(err), "chi2_err": float(dchi / r.chi2[k]),
+                                "implied_decided": bool(dchi > 1e-5 * r.chi2[k]),
+                                "iters": int(out["iters"][c, k].item()), "status": st})
         cg = int(out["corner"][c].item())
         if cg != r.corner:
             # only a near-tie of the curvature may move the corner
             kk = r.kappa
             assert abs(kk[cg] - kk[r.corner]) <= 1e-3 * kk[r.corner], (cg, r.corner)
+    print(f"fp32 checks (tol {tol:g}): the residual-implied chi2 bound decided "
+          f"{n_implied} pass(es)")
+    return n_implied
+
+
+def _report(name, tol, records):
+    """Per-item table of the FP32 parity run, written where
+    MIRAGE_PARITY_REPORT points (a directory), else only summarised."""
+    import json
+    import os
+    errs = np.array([x["s_err"] for x in records])
+    over = sum(1 for x in records if x["s_err"] > 1e-4)
+    print(f"{name} tol {tol:g}: {len(records)} items, max |ds|/|s| {errs.max():.2e}, "
+          f"{over} above 1e-4, max |dchi2|/chi2 {max(x['chi2_err'] for x in records):.2e}")
+    d = os.environ.get("MIRAGE_PARITY_REPORT")
+    if d:
+        os.makedirs(d, exist_ok=True)
+        with open(os.path.join(d, f"{name}_tol{tol:g}.json"), "w") as fh:
+            json.dump({"tol": tol, "items": records}, fh)
 
 
 def test_eval_fp32_64px(mods, ctx32):
@@ -200,7 +264,9 @@ def test_eval_fp32_64px(mods, ctx32):
     lenses = np.vstack([synth.TRUE_LENS, synth.lens_population(rng, 2)])
     out = ctx32.eval_batch([device_problem(prob)], _lens_t(lenses), [0] * 3, _lam_t(lams, 3), [16] * 3,
                            tol=1e-6, want_all_x=True)
-    _fp32_checks(out, prob, lenses, lams, 1e-6)
+    rec = []
+    _fp32_checks(out, prob, lenses, lams, 1e-6, records=rec)
+    _report("fp32_ga64", 1e-6, rec)
 
 
 def test_eval_fp32_ragged_subpix_gradient(mods, ctx32):

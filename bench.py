@@ -485,10 +485,12 @@ def run_gpu(args):
     return 0
 
 
-def run_profile_case(variant: int) -> int:
-    """The small case the ncu captures of the CGLS kernel run: 20 candidates
-    x the 16-lambda grid of the 64x64 workload (320 items), two evaluations
-    with one kernel variant, no timing."""
+def run_profile_case(variant: int, n_cand: int = 160) -> int:
+    """The case the ncu captures of the CGLS kernel run: n_cand candidates x
+    the 16-lambda grid of the 64x64 workload (160 x 16 = 2560 items, over
+    eight per CTA slot of the two-CTA kernel, so the launch is in the
+    benchmark's steady state), two evaluations with one kernel variant, then
+    one with per-phase SM clocks; no timing."""
     import torch
 
     import __graft_entry__
@@ -496,7 +498,7 @@ def run_profile_case(variant: int) -> int:
     from paper_1101_5803_gb300 import binding
     from paper_1101_5803_gb300.problems import ga64_workload
     ctx = binding.Context(0, binding.MIRAGE_FP32)
-    wl = ga64_workload(ctx, 20, 16, seed=3)
+    wl = ga64_workload(ctx, n_cand, 16, seed=3)
     for _ in range(2):
         out = ctx.eval_batch([wl.problem], wl.lens, wl.prob_idx, wl.lambdas, wl.n_lam, tol=1e-6, variant=variant)
     torch.cuda.synchronize()
@@ -506,11 +508,39 @@ def run_profile_case(variant: int) -> int:
     torch.cuda.synchronize()
     clk = [float(v) for v in ctx.phase_clocks()]
     its = float(out["iters"].sum().item())
-    names = ["L p + H p", "B convolution", "q reduction", "vector updates", "B^T convolution", "L^T walk",
-             "L^T join", "L^T gather + H^T", "gamma reduction", "p update", "FP64 refinement", "item set-up"]
+    names = ["L p + H p", "B convolution + W q + H^T H p", "delta reduction", "(unused)", "B^T convolution", "L^T walk",
+             "L^T join", "L^T gather + updates", "gamma reduction", "p update", "FP64 refinement", "item set-up"]
     print(json.dumps({"profile_case": True, "variant": variant, "items": int(out["iters"].numel()),
                       "cg_iterations": int(its),
                       "phase_clk_per_iteration": {n: round(c / max(its, 1.0), 1) for n, c in zip(names, clk)}}),
+          flush=True)
+    ctx.close()
+    return 0
+
+
+def run_profile_forward() -> int:
+    """The case the ncu captures of the forward-batch kernel run: the
+    256x256 forward batch of the benchmark (128x128 source, 21x21 PSF, 1024
+    sources |N(0,1)| x template at one lens), three calls, no timing."""
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import synth
+    from paper_1101_5803_gb300 import binding
+    from paper_1101_5803_gb300.problems import large_workload
+    ctx = binding.Context(0, binding.MIRAGE_FP32)
+    lw = large_workload(ctx, n_cand=1, n_lam=1, seed=3)
+    lg = lw.geom
+    hx = (lg.sxmax - lg.sxmin) / lg.sx
+    cxs = lg.sxmin + (np.arange(lg.sx) + 0.5) * hx
+    tmpl = synth.eval_source(synth.drawn_source(np.random.default_rng(9)), *np.meshgrid(cxs, cxs)).ravel()
+    S = torch.as_tensor(np.abs(np.random.default_rng(10).standard_normal((1024, tmpl.size))) * tmpl[None, :],
+                        dtype=ctx.real, device="cuda")
+    for _ in range(3):
+        _, chi2, _ = ctx.forward(lw.problem, lw.lens[0], S, want_model=False)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_forward": True, "sources": 1024, "chi2_median": float(chi2.median().item())}),
           flush=True)
     ctx.close()
     return 0
@@ -524,11 +554,17 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--profile-case", type=int, default=None, metavar="VARIANT",
-                    help="run only the small case of the ncu captures (20 candidates x 16 lambdas, two "
-                         "evaluations with this kernel variant) and exit")
+                    help="run only the case of the ncu captures of the CGLS kernel (--profile-cands "
+                         "candidates x 16 lambdas, two evaluations with this kernel variant) and exit")
+    ap.add_argument("--profile-cands", type=int, default=160,
+                    help="candidates of the --profile-case run (x 16 lambdas)")
+    ap.add_argument("--profile-forward", action="store_true",
+                    help="run only the forward-batch case of the ncu captures (256x256, 1024 sources) and exit")
     args = ap.parse_args()
+    if args.profile_forward:
+        return run_profile_forward()
     if args.profile_case is not None:
-        return run_profile_case(args.profile_case)
+        return run_profile_case(args.profile_case, args.profile_cands)
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)

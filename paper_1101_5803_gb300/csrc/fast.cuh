@@ -188,7 +188,6 @@ __device__ __forceinline__ float hrow_fast(const float* __restrict__ v, int i, u
 // Per-item constants of the fast kernel, written by thread 0 into shared
 // memory (read back where needed instead of being held in registers).
 struct FastItem {
-    int R;                  // rays per thread in the L^T walk (odd)
     int nfz, top, mfr, W4;  // P2 frame float4s overlapped by the L^T planes
     int xl;                 // xoff / 4
     float inv_mfr;          // 1 / mfr
@@ -426,9 +425,6 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_cgls_fast(const __grid_constant
         }
         {
             if (tid == 0) {
-                // L^T walk: R consecutive rays per thread, R odd so that the
-                // lanes' reads at stride R fall on distinct banks
-                fi->R = ((nent + bs - 1) / bs) | 1;
                 // the L^T planes occupy P2[0, 4 ns): its frame float4s there
                 // (top frame rows, then the side margins of interior rows)
                 // are cleared again before each B^T convolution
@@ -452,7 +448,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_cgls_fast(const __grid_constant
         const int pp0 = (ty * TILE + g.hk) * g.Wp + tx * TILE + g.xoff;
         const float* P1t = P1 + (ty * TILE) * g.Wp + tx * TILE;
         const float* P2t = P2 + (ty * TILE) * g.Wp + tx * TILE;
-        float sw[16], rr[16];
+        float sw[16];
         unsigned mbits = 0;
         // L applied to ones marks the mapped pixels
         for (int e = tid; e < nent; e += bs) P1[eidx[e] & 0xffffu] = 1.f;
@@ -497,22 +493,45 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_cgls_fast(const __grid_constant
                 msk |= (m | (nb << 16)) << (4 * kk);
             }
         }
-        // ---- this thread's ray range of the L^T walk: does its first cell
-        // continue from the previous range (bit 0: its partial then goes to
-        // Sq), and does it own a cell that runs on into later ranges (bits
-        // 1..: how many; it adds their partials, in range order, after the walk)
-        const int R = fi->R;
-        int wflags = 0;
+        // ---- this thread's ray range of the L^T walk.  Each warp takes a
+        // span of the cell-sorted rays that starts and ends on a cell
+        // boundary (nominally an eighth of them), cut into equal runs per
+        // lane (of odd length, so that the lanes' reads fall on distinct
+        // banks).  A cell split between runs therefore stays inside one warp
+        // and its partials are joined by shuffles, with no block barrier.
+        // wflags bit 0: this run's first cell continues from the previous run
+        // (its partial is parked in Sq); bits 1..: how many later runs continue
+        // this run's last cell (this lane adds their partials, in run order).
+        int e0, e1, wflags = 0, jmax;
         {
-            const int e0 = min(tid * R, nent), e1 = min(e0 + R, nent);
+            const int lane = tid & 31, wid = tid >> 5;
+            // start of warp wq's span: the first cell boundary at or after its
+            // nominal start
+            auto span_start = [&](int wq) -> int {
+                const int s0 = (int)(((long long)wq * nent) / (bs / 32));
+                if (s0 <= 0 || s0 >= nent) return min(max(s0, 0), nent);
+                const int b = (int)(eidx[s0] >> 16);  // lower-left source pixel of the ray's cell
+                const int iy = b / g.sx;
+                const int cell = iy * g.ncx + (b - iy * g.sx);
+                return (int)cst16[cell] == s0 ? s0 : (int)cst16[cell + 1];
+            };
+            const int a0 = span_start(wid), a1 = span_start(wid + 1);
+            const int Rw = ((a1 - a0 + 31) / 32) | 1;
+            e0 = min(a0 + lane * Rw, a1);
+            e1 = min(e0 + Rw, a1);
+            int ncont = 0;
             if (e0 < e1) {
                 const unsigned kf = eidx[e0] >> 16, kl = eidx[e1 - 1] >> 16;
-                const bool cin = e0 > 0 && (eidx[e0 - 1] >> 16) == kf;
-                int ncont = 0;
+                const bool cin = e0 > a0 && (eidx[e0 - 1] >> 16) == kf;
                 if (!(cin && kf == kl))
-                    for (int t2 = tid + 1; t2 < bs && t2 * R < nent && (eidx[t2 * R] >> 16) == kl; ++t2) ++ncont;
+                    for (int l2 = lane + 1; l2 < 32; ++l2) {
+                        const int f2 = a0 + l2 * Rw;
+                        if (f2 >= a1 || (eidx[f2] >> 16) != kl) break;
+                        ++ncont;
+                    }
                 wflags = (cin ? 1 : 0) | (ncont << 1);
             }
+            jmax = __reduce_max_sync(0xffffffffu, ncont);
         }
         __syncthreads();
 
@@ -692,36 +711,34 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_cgls_fast(const __grid_constant
             for (int i = tid; i < g.ns; i += bs) w.xb[i] = w.x64[i];
             const double target = fmax(eta_min, 0.3 * A.tol / rel64);
 
-            // ---- inner CGLS on the correction: state into registers
-            float x[NSP], s[NSP], qr[NSP];
+            // ---- inner solve of the correction equation A d = r: Jacobi-
+            // preconditioned CG on the normal equations (r = the FP64 residual
+            // rounded to FP32, A = L^T B^T W B L + lam H^T H applied in FP32),
+            // started from d = 0.  Every vector of the recursion is of the size
+            // of the correction itself, so FP32 rounding stays relative to it
+            // (an image-space CGLS residual would carry the data misfit, which
+            // is ~1e7 times larger near convergence, into every gradient).
+            float x[NSP], gv[NSP], z[NSP], hth[NSP];
             float gs = 0.f;
+            const float lamf = (float)lam;
 #pragma unroll
             for (int kk = 0; kk < NSP; ++kk) {
                 const int i = tid + kk * bs;
                 x[kk] = 0.f;
-                s[kk] = 0.f;
+                gv[kk] = 0.f;
+                z[kk] = 0.f;
                 if (i < nsv) {
-                    s[kk] = w.s[i];
-                    const float z = minv[kk] * s[kk];
-                    p[i] = z;
-                    gs = fmaf(s[kk], z, gs);
+                    gv[kk] = w.s[i];
+                    z[kk] = minv[kk] * gv[kk];
+                    p[i] = z[kk];
+                    gs = fmaf(gv[kk], z[kk], gs);
                 }
             }
-            if (own) {
-#pragma unroll
-                for (int r = 0; r < TILE; ++r) {
-                    const V4<float> r4 = ld4(w.rimg + pp0 + r * g.Wp);
-#pragma unroll
-                    for (int cc = 0; cc < 4; ++cc) rr[r * 4 + cc] = r4.v[cc];
-                }
-            } else {
-#pragma unroll
-                for (int q = 0; q < 16; ++q) rr[q] = 0.f;
-            }
+            float* hbuf = rreg;  // H p of the current direction (the CGLS residual slot is free here)
             int half = 0, it_in = 0, best_it = 0, brk = 0, stop = 0;
             float gam, g0, best = 1.f;
             {
-                const float2 gp = block_pair_tree(gs, pbuf, half);
+                const float2 gp = block_pair_tree(gs, pbuf, half);  // its barrier also completes p
                 half ^= 1;
                 gam = gp.x + gp.y;
                 g0 = gam;
@@ -752,57 +769,32 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_cgls_fast(const __grid_constant
                     for (int j = 0; j < 4; ++j)
                         if (e + j * bs < nent) P1[id[j] & 0xffffu] = val[j];
                 }
-                float dq = 0.f;
+                // H p of the owned source pixels into hbuf, and lam ||H p||^2
+                float dh = 0.f;
 #pragma unroll
                 for (int kk = 0; kk < NSP; ++kk) {
                     const int i = tid + kk * bs;
-                    qr[kk] = 0.f;
                     if (i < nsv) {
-                        qr[kk] = sl * hrow_fast(p, i, msk >> (16 + 4 * kk), sxv, regv);
-                        dq = fmaf(qr[kk], qr[kk], dq);
+                        const float h = hrow_fast(p, i, msk >> (16 + 4 * kk), sxv, regv);
+                        hbuf[i] = h;
+                        dh = fmaf(h, h, dh);
                     }
                 }
                 __syncthreads();
                 PHASE(0);
-                // q = sqrt(W) B P1 on the owned tile
-                float q[16];
+                // q = B P1 on the owned tile: delta += ||sqrt(W) q||^2, P2 <- W q
+                float dl_part = lamf * dh;
                 if (own) {
                     float o16[16];
                     conv_tile_fast<K, MODE>(P1t, g.Wp, taps2, FA.ptap[0], o16);
-#pragma unroll
-                    for (int qq = 0; qq < 16; ++qq) q[qq] = sw[qq] * o16[qq];
-#pragma unroll
-                    for (int qq = 0; qq < 16; ++qq) dq = fmaf(q[qq], q[qq], dq);
-                } else {
-#pragma unroll
-                    for (int qq = 0; qq < 16; ++qq) q[qq] = 0.f;
-                }
-                PHASE(1);
-                const float2 dl = block_pair_tree(dq, pbuf, half);
-                half ^= 1;
-                const float delta = dl.x + dl.y;
-                PHASE(2);
-                if (!(delta > 0.f) || !isfinite(delta)) {
-                    brk = 1;
-                    break;
-                }
-                const float a = gam / delta;
-#pragma unroll
-                for (int kk = 0; kk < NSP; ++kk) {
-                    const int i = tid + kk * bs;
-                    if (i < nsv) {
-                        x[kk] = fmaf(a, p[i], x[kk]);
-                        rreg[i] = fmaf(-a, qr[kk], rreg[i]);
-                    }
-                }
-                if (own) {
 #pragma unroll
                     for (int r = 0; r < TILE; ++r) {
                         V4<float> o;
 #pragma unroll
                         for (int cc = 0; cc < 4; ++cc) {
-                            rr[r * 4 + cc] = fmaf(-a, q[r * 4 + cc], rr[r * 4 + cc]);
-                            o.v[cc] = sw[r * 4 + cc] * rr[r * 4 + cc];
+                            const float t = sw[r * 4 + cc] * o16[r * 4 + cc];
+                            dl_part = fmaf(t, t, dl_part);
+                            o.v[cc] = sw[r * 4 + cc] * t;
                         }
                         st4(P2 + pp0 + r * g.Wp, o);
                     }
@@ -821,8 +813,23 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_cgls_fast(const __grid_constant
                         reinterpret_cast<float4*>(P2)[q4] = make_float4(0.f, 0.f, 0.f, 0.f);
                     }
                 }
-                __syncthreads();  // P2 complete
-                PHASE(3);
+                // H^T (H p) of the owned source pixels (neighbours' H p from hbuf)
+#pragma unroll
+                for (int kk = 0; kk < NSP; ++kk) {
+                    const int i = tid + kk * bs;
+                    hth[kk] = i < nsv ? hrow_fast(hbuf, i, msk >> (16 + 4 * kk), sxv, regv) : 0.f;
+                }
+                PHASE(1);
+                // delta = p^T A p; the reduction's barrier also completes P2
+                const float2 dl = block_pair_tree(dl_part, pbuf, half);
+                half ^= 1;
+                const float delta = dl.x + dl.y;
+                PHASE(2);
+                if (!(delta > 0.f) || !isfinite(delta)) {
+                    brk = 1;
+                    break;
+                }
+                const float a = gam / delta;
                 // u = B^T P2 on the owned tile, stored into P1 at mapped pixels
                 if (own) {
                     float o16[16];
@@ -837,83 +844,101 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_cgls_fast(const __grid_constant
                 }
                 __syncthreads();  // u complete
                 PHASE(4);
-                // L^T u, pass 1: each thread walks its R consecutive rays (sorted
-                // by cell) and sums, per cell, the four corner weights times u;
-                // a cell's total goes to the planes (indexed by the cell's base
+                // L^T u: each lane walks its run of consecutive rays (sorted by
+                // cell) and sums, per cell, the four corner weights times u; a
+                // cell's total goes to the planes (indexed by the cell's base
                 // source pixel), the partial of a cell continued from the
-                // previous range to Sq.  The next ray is loaded before the
-                // current one is used, and the sums are stored at the last ray
-                // of each cell run (known from the next ray's cell)
-                {
-                    const int e0 = min(tid * R, nent), e1 = min(e0 + R, nent);
-                    if (e0 < e1) {
-                        unsigned id = eidx[e0];
-                        unsigned cur = id >> 16;
-                        float* dst = (wflags & 1) ? Sq + tid : Q + cur;
-                        int ps = (wflags & 1) ? bs : nsv;
-                        float2 uv = euv[e0];
-                        float U = P1[id & 0xffffu];
-                        float c00 = 0.f, c10 = 0.f, c01 = 0.f, c11 = 0.f;
-                        for (int e = e0; e < e1; ++e) {
-                            const int en = min(e + 1, e1 - 1);
-                            const unsigned idn = eidx[en];
-                            const float2 uvn = euv[en];
-                            const float Un = P1[idn & 0xffffu];
-                            const unsigned key = id >> 16;
-                            if (key != cur) {  // a new cell: its sums go to the planes
-                                cur = key;
-                                dst = Q + key;
-                                ps = nsv;
-                                c00 = c10 = c01 = c11 = 0.f;
-                            }
-                            const float uU = uv.x * U, u0 = U - uU;  // u U, (1-u) U
-                            c00 = fmaf(1.f - uv.y, u0, c00);
-                            c10 = fmaf(1.f - uv.y, uU, c10);
-                            c01 = fmaf(uv.y, u0, c01);
-                            c11 = fmaf(uv.y, uU, c11);
-                            if (e == e1 - 1 || (idn >> 16) != key) {
-                                dst[0] = c00;
-                                dst[ps] = c10;
-                                dst[2 * ps] = c01;
-                                dst[3 * ps] = c11;
-                            }
-                            id = idn;
-                            uv = uvn;
-                            U = Un;
+                // previous run to Sq.  The next ray is loaded before the current
+                // one is used, and the sums are stored at the last ray of each
+                // cell run (known from the next ray's cell)
+                if (e0 < e1) {
+                    unsigned id = eidx[e0];
+                    unsigned cur = id >> 16;
+                    float* dst = (wflags & 1) ? Sq + tid : Q + cur;
+                    int ps = (wflags & 1) ? bs : nsv;
+                    float2 uv = euv[e0];
+                    float U = P1[id & 0xffffu];
+                    float c00 = 0.f, c10 = 0.f, c01 = 0.f, c11 = 0.f;
+                    for (int e = e0; e < e1; ++e) {
+                        const int en = min(e + 1, e1 - 1);
+                        const unsigned idn = eidx[en];
+                        const float2 uvn = euv[en];
+                        const float Un = P1[idn & 0xffffu];
+                        const unsigned key = id >> 16;
+                        if (key != cur) {  // a new cell: its sums go to the planes
+                            cur = key;
+                            dst = Q + key;
+                            ps = nsv;
+                            c00 = c10 = c01 = c11 = 0.f;
                         }
+                        const float uU = uv.x * U, u0 = U - uU;  // u U, (1-u) U
+                        c00 = fmaf(1.f - uv.y, u0, c00);
+                        c10 = fmaf(1.f - uv.y, uU, c10);
+                        c01 = fmaf(uv.y, u0, c01);
+                        c11 = fmaf(uv.y, uU, c11);
+                        if (e == e1 - 1 || (idn >> 16) != key) {
+                            dst[0] = c00;
+                            dst[ps] = c10;
+                            dst[2 * ps] = c01;
+                            dst[3 * ps] = c11;
+                        }
+                        id = idn;
+                        uv = uvn;
+                        U = Un;
+                    }
+                }
+                // join of split cells inside the warp: each run's parked
+                // first-cell partial (this lane's own Sq slot, so no barrier)
+                // is shuffled down to the lane owning that cell, which adds the
+                // partials in run order (a fixed order: deterministic)
+                if (jmax > 0) {
+                    float f0 = 0.f, f1 = 0.f, f2 = 0.f, f3 = 0.f;
+                    if (wflags & 1) {
+                        f0 = Sq[tid];
+                        f1 = Sq[bs + tid];
+                        f2 = Sq[2 * bs + tid];
+                        f3 = Sq[3 * bs + tid];
+                    }
+                    const int nc = wflags >> 1;
+                    unsigned kl = 0;
+                    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+                    if (nc) {
+                        kl = eidx[e1 - 1] >> 16;
+                        a0 = Q[kl];
+                        a1 = Q[nsv + kl];
+                        a2 = Q[2 * nsv + kl];
+                        a3 = Q[3 * nsv + kl];
+                    }
+                    for (int j = 1; j <= jmax; ++j) {
+                        const float v0 = __shfl_down_sync(0xffffffffu, f0, j);
+                        const float v1 = __shfl_down_sync(0xffffffffu, f1, j);
+                        const float v2 = __shfl_down_sync(0xffffffffu, f2, j);
+                        const float v3 = __shfl_down_sync(0xffffffffu, f3, j);
+                        if (j <= nc) {
+                            a0 += v0;
+                            a1 += v1;
+                            a2 += v2;
+                            a3 += v3;
+                        }
+                    }
+                    if (nc) {
+                        Q[kl] = a0;
+                        Q[nsv + kl] = a1;
+                        Q[2 * nsv + kl] = a2;
+                        Q[3 * nsv + kl] = a3;
                     }
                 }
                 __syncthreads();
                 PHASE(5);
-                // pass 2: the owner of a cell that runs on into later ranges adds
-                // their partials in range order (a fixed order: deterministic)
-                if (wflags >> 1) {
-                    const int e1 = min(min(tid * R, nent) + R, nent);
-                    const unsigned kl = eidx[e1 - 1] >> 16;
-                    float a0 = Q[kl], a1 = Q[nsv + kl], a2 = Q[2 * nsv + kl], a3 = Q[3 * nsv + kl];
-                    const int t_end = tid + 1 + (wflags >> 1);
-                    for (int t2 = tid + 1; t2 < t_end; ++t2) {
-                        a0 += Sq[t2];
-                        a1 += Sq[bs + t2];
-                        a2 += Sq[2 * bs + t2];
-                        a3 += Sq[3 * bs + t2];
-                    }
-                    Q[kl] = a0;
-                    Q[nsv + kl] = a1;
-                    Q[2 * nsv + kl] = a2;
-                    Q[3 * nsv + kl] = a3;
-                }
-                __syncthreads();
-                PHASE(6);
-                // pass 3: per source pixel, the fixed-order sum of the corners it
-                // receives from its (up to) four occupied cells, plus sqrt(lam) H^T r_reg
+                // pass 3: per source pixel, (A p)_i = the fixed-order sum of the
+                // corners it receives from its (up to) four occupied cells plus
+                // lam (H^T H p)_i; then the CG updates of x, g and z = M^-1 g
                 float gsum = 0.f;
 #pragma unroll
                 for (int kk = 0; kk < NSP; ++kk) {
                     const int i = tid + kk * bs;
                     if (i < nsv) {
                         const unsigned m = msk >> (4 * kk);
-                        // empty or absent cells read the shared zero (no branches)
                         // empty or absent cells read the shared zero: no branches,
                         // four independent loads; adding +0 changes nothing
                         const int q0 = (m & 1u) ? i : zq;
@@ -925,9 +950,11 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_cgls_fast(const __grid_constant
                         acc += Q[q1];
                         acc += Q[q2];
                         acc += Q[q3];
-                        const float gr = acc + sl * hrow_fast(rreg, i, m >> 16, sxv, regv);
-                        s[kk] = minv[kk] * gr;  // preconditioned gradient z = M^-1 g
-                        gsum = fmaf(gr, s[kk], gsum);
+                        const float ap = fmaf(lamf, hth[kk], acc);
+                        x[kk] = fmaf(a, p[i], x[kk]);
+                        gv[kk] = fmaf(-a, ap, gv[kk]);
+                        z[kk] = minv[kk] * gv[kk];
+                        gsum = fmaf(gv[kk], z[kk], gsum);
                     }
                 }
                 PHASE(7);
@@ -957,7 +984,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_cgls_fast(const __grid_constant
 #pragma unroll
                 for (int kk = 0; kk < NSP; ++kk) {
                     const int i = tid + kk * bs;
-                    if (i < nsv) p[i] = fmaf(bt, p[i], s[kk]);
+                    if (i < nsv) p[i] = fmaf(bt, p[i], z[kk]);
                 }
                 __syncthreads();
                 PHASE(9);
@@ -973,7 +1000,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_cgls_fast(const __grid_constant
             }
             // the inner loop leaves u in P1 at mapped pixels (L p overwrites
             // every one of them) and the L^T planes in P2 (the frame is
-            // cleared again before the next B^T convolution)
+            // cleared again after the next B convolution)
             __syncthreads();
         }
 

@@ -1689,27 +1689,23 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_cgls(CglsArgs<T> A) {
             }
             prev_rel = rel64;  // the residuals accepted so far decrease: this is the best iterate
             for (int i = tid; i < g.ns; i += bs) w.xb[i] = w.x64[i];
-            // ---- inner CGLS on the correction, started from zero
+            // ---- inner solve of the correction equation A d = r: Jacobi-
+            // preconditioned CG on the normal equations, from d = 0.  r (the
+            // FP64 residual rounded to T) is the first gradient g (w.s); z =
+            // M^-1 g lives in qreg and H p in rreg (both at least ns long).
+            // Every vector of the recursion is of the size of the correction,
+            // so rounding stays relative to it (an image-space CGLS residual
+            // would carry the data misfit into every gradient).
             const double target = fmax(eta_min, 0.3 * A.tol / rel64);
             for (int i = tid; i < g.ns; i += bs) {
                 w.x[i] = 0;
-                w.p[i] = w.minv[i] * w.s[i];  // preconditioned gradient
-            }
-            for (int t = tid; t < g.ntiles; t += bs) {
-                const int ty = t / g.tiles_x, tx = t - ty * g.tiles_x;
-#pragma unroll
-                for (int r = 0; r < TILE; ++r) {
-                    const int pp = (ty * TILE + r + g.hk) * g.Wp + tx * TILE + g.xoff;
-                    const V4<T> rv = ld4(w.rimg + pp), sw = ld4(w.swp + pp);
-                    V4<T> o;
-#pragma unroll
-                    for (int cc = 0; cc < 4; ++cc) o.v[cc] = sw.v[cc] * rv.v[cc];
-                    st4(w.P2 + pp, o);
-                }
+                const T z = w.minv[i] * w.s[i];
+                w.qreg[i] = z;
+                w.p[i] = z;
             }
             {
                 T gs = 0;
-                for (int i = tid; i < g.ns; i += bs) gs = fma(w.s[i], w.p[i], gs);
+                for (int i = tid; i < g.ns; i += bs) gs = fma(w.s[i], w.qreg[i], gs);
                 const double gam = block_sum_to0<T>(gs, red);
                 if (tid == 0) {
                     ctl->gam = gam;
@@ -1724,27 +1720,28 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_cgls(CglsArgs<T> A) {
                 __syncthreads();
             }
             const int stag_window = max(4000, 2 * g.ns);
+            const T lamT = (T)lam;
             // per-cell L^T sums: bilinear and nearest only, when they fit in P2
             const bool cells_fit = g.interp != 2 && 4 * g.ncells <= g.plen;
             while (!ctl->stop) {
-                // q = A~ p: image part sqrt(W) B L p, regulariser part sqrt(lam) H p
+                // A p = L^T B^T W B L p + lam H^T H p: first L p and H p
                 apply_L<T, T, T, T>(g, w.E, w.inv, w.p, w.P1);
-                T dqr = 0;
+                T dh = 0;
                 for (int i = tid; i < g.nreg; i += bs) {
-                    const T q = sl * apply_H_row<T, T>(g, w.p, i);
-                    w.qreg[i] = q;
-                    dqr = fma(q, q, dqr);
+                    const T h = apply_H_row<T, T>(g, w.p, i);
+                    w.rreg[i] = h;
+                    dh = fma(h, h, dh);
                 }
                 __syncthreads();
+                // q = sqrt(W) B L p; delta = p^T A p = ||q||^2 + lam ||H p||^2
                 T cq;
                 if constexpr (K == 0 && BIG)
                     cq = w.fft ? conv_pass_fft<T>(&w.fft->t, w.P1, w.swp, w.qimg, g, CONV_Q)
                                : conv_pass<T, K, SH>(w.P1, w.taps, w.swp, w.qimg, g, CONV_Q);
                 else
                     cq = conv_pass<T, K, SH>(w.P1, w.taps, w.swp, w.qimg, g, CONV_Q);
-                const T dq = dqr + cq;
                 {
-                    const double delta = block_sum_to0<T>(dq, red);
+                    const double delta = block_sum_to0<T>(cq + lamT * dh, red);
                     if (tid == 0) {
                         if (!(delta > 0.0) || !isfinite(delta)) {
                             ctl->brk = 1;
@@ -1758,22 +1755,16 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_cgls(CglsArgs<T> A) {
                 }
                 if (ctl->brk) break;
                 const T a = sizeof(T) == 4 ? (T)ctl->a_f : (T)ctl->a_d;
-                for (int i = tid; i < g.ns; i += bs) w.x[i] = fma(a, w.p[i], w.x[i]);
-                for (int i = tid; i < g.nreg; i += bs) w.rreg[i] = fma(-a, w.qreg[i], w.rreg[i]);
+                // P2 = W B L p = sqrt(W) q
                 for (int t = tid; t < g.ntiles; t += bs) {
                     const int ty = t / g.tiles_x, tx = t - ty * g.tiles_x;
 #pragma unroll
                     for (int r = 0; r < TILE; ++r) {
                         const int pp = (ty * TILE + r + g.hk) * g.Wp + tx * TILE + g.xoff;
-                        V4<T> rv = ld4(w.rimg + pp);
                         const V4<T> qv = ld4(w.qimg + pp), sw = ld4(w.swp + pp);
                         V4<T> o;
 #pragma unroll
-                        for (int cc = 0; cc < 4; ++cc) {
-                            rv.v[cc] = fma(-a, qv.v[cc], rv.v[cc]);
-                            o.v[cc] = sw.v[cc] * rv.v[cc];
-                        }
-                        st4(w.rimg + pp, rv);
+                        for (int cc = 0; cc < 4; ++cc) o.v[cc] = sw.v[cc] * qv.v[cc];
                         st4(w.P2 + pp, o);
                     }
                 }
@@ -1787,11 +1778,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_cgls(CglsArgs<T> A) {
                     conv_pass<T, K, SH>(w.P2, w.taps + g.K * g.kp, nullptr, w.qimg, g, CONV_RAW);
                 }
                 __syncthreads();  // u complete
+                // (A p)_i = (L^T u)_i + lam (H^T H p)_i, then the CG updates of
+                // x, g (w.s) and z = M^-1 g (w.qreg)
                 T gs = 0;
                 if (cells_fit) {
                     // L^T u in two passes: per cell, the four corner sums of its
                     // rays (each ray read once) into P2's storage (free until the
-                    // next residual store); then per source pixel the fixed-order
+                    // next W B L p store); then per source pixel the fixed-order
                     // sum of the corners it receives from its (up to) four cells
                     T* cp = w.P2;
                     for (int cell = tid; cell < g.ncells; cell += bs) {
@@ -1819,19 +1812,25 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_cgls(CglsArgs<T> A) {
                         if (ib <= g.sy - 2 && ia >= 1) acc += cp[4 * (ib * g.ncx + ia - 1) + 1];
                         if (ib >= 1 && ia <= g.sx - 2) acc += cp[4 * ((ib - 1) * g.ncx + ia) + 2];
                         if (ib >= 1 && ia >= 1) acc += cp[4 * ((ib - 1) * g.ncx + ia - 1) + 3];
-                        const T v = acc * g.invNp + sl * apply_HT_at<T, T>(g, w.rreg, i, ia, ib);
-                        const T z = w.minv[i] * v;  // preconditioned gradient
-                        w.s[i] = z;
-                        gs = fma(v, z, gs);
+                        const T ap = acc * g.invNp + lamT * apply_HT_at<T, T>(g, w.rreg, i, ia, ib);
+                        w.x[i] = fma(a, w.p[i], w.x[i]);
+                        const T gv = fma(-a, ap, w.s[i]);
+                        const T z = w.minv[i] * gv;
+                        w.s[i] = gv;
+                        w.qreg[i] = z;
+                        gs = fma(gv, z, gs);
                     }
                 } else {
                     for (int i = tid; i < g.ns; i += bs) {
                         const int ib = i / g.sx, ia = i - ib * g.sx;
-                        const T v = apply_LT_at<T, T, T>(g, w.E, w.cst, w.qimg, ia, ib) +
-                                    sl * apply_HT_at<T, T>(g, w.rreg, i, ia, ib);
-                        const T z = w.minv[i] * v;  // preconditioned gradient
-                        w.s[i] = z;
-                        gs = fma(v, z, gs);
+                        const T ap = apply_LT_at<T, T, T>(g, w.E, w.cst, w.qimg, ia, ib) +
+                                     lamT * apply_HT_at<T, T>(g, w.rreg, i, ia, ib);
+                        w.x[i] = fma(a, w.p[i], w.x[i]);
+                        const T gv = fma(-a, ap, w.s[i]);
+                        const T z = w.minv[i] * gv;
+                        w.s[i] = gv;
+                        w.qreg[i] = z;
+                        gs = fma(gv, z, gs);
                     }
                 }
                 {
@@ -1861,7 +1860,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_cgls(CglsArgs<T> A) {
                 if (cells_fit)
                     for (int i = tid; i < 4 * g.ncells; i += bs) w.P2[i] = 0;
                 const T bt = sizeof(T) == 4 ? (T)ctl->b_f : (T)ctl->b_d;
-                for (int i = tid; i < g.ns; i += bs) w.p[i] = fma(bt, w.p[i], w.s[i]);
+                for (int i = tid; i < g.ns; i += bs) w.p[i] = fma(bt, w.p[i], w.qreg[i]);
                 __syncthreads();
             }
             total_it = ctl->total_it;

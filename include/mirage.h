@@ -157,12 +157,14 @@ int mirage_destroy(mirage_ctx_t* ctx);
  *  lam_start           nullable HOST array [n_cand]: a predicted corner index
  *                      per candidate (clamped to [0, n_lam-1]).  When given
  *                      (batched mode), each candidate's lambdas are solved as
- *                      two chains, lam_start down to 0 and lam_start+1 up to
- *                      n_lam-1, and every lambda after the first of its chain
- *                      starts from the solution of its neighbour nearer to
- *                      lam_start (a chain's first lambda starts from warm_x,
- *                      or zero).  Results agree with unchained calls to the
- *                      solver tolerance.  Ignored in plain mode.
+ *                      chains: lam_start down to 0 and lam_start+1 up to
+ *                      n_lam-1, each cut into segments whose estimated cost
+ *                      stays within one CTA slot's share of the call; every lambda
+ *                      after the first of its chain starts from the solution
+ *                      of its neighbour nearer to lam_start (a chain's first
+ *                      lambda starts from warm_x, or zero).  Results agree
+ *                      with unchained calls to the solver tolerance.  Ignored
+ *                      in plain mode.
  * Outputs ([n_cand*max_lam] unless noted; entries beyond n_lam untouched):
  *  chi2, reg           double: Eq. chi2 of the solution and ||H s||^2
  *  iters               int: CG iterations used
@@ -240,6 +242,12 @@ int mirage_lcurve(const double* chi2, const double* reg, const int* n_lam, int n
 int mirage_forward(mirage_ctx_t* ctx, const mirage_problem_t* prob, const double* lens,
                    const void* s, int n_src, void* model, double* chi2, int* status, void* stream);
 
+/* Leave `slots` CTA slots of the device free in this context's CGLS
+ * launches (the persistent kernels otherwise fill every SM), so that work on
+ * other streams, such as surrogate training, can run beside the solves.
+ * 0 (the default) uses the whole device.  The results do not depend on it. */
+int mirage_set_reserved_slots(mirage_ctx_t* ctx, int slots);
+
 /* Number of kernel launches the last eval/forward call of this context
  * issued (a replayed graph counts its kernels). */
 int mirage_last_launch_count(const mirage_ctx_t* ctx);
@@ -294,6 +302,16 @@ int mirage_mlp_grad(mirage_mlp_t* mlp, const float* x, const float* t, int n, fl
 /* One Adam step at learning rate lr on the batch (x, t). */
 int mirage_mlp_train_step(mirage_mlp_t* mlp, const float* x, const float* t, int n, float lr,
                           double* loss, float* y, void* stream);
+/* `steps` Adam steps at learning rate lr, each on `batch` rows drawn from
+ * the dataset (x [n x dims[0]], t [n x dims[L]], device FP32) on the
+ * device: step k takes row h(seed, k, j) mod n for slot j, with h a
+ * counter-based hash (splitmix64), so no host round trip happens between
+ * steps.  The launch sequence of one step is captured once per call as a
+ * CUDA graph on a private stream and replayed `steps` times on `stream`.
+ * Do not call while `stream` itself is being captured.  x and t must stay
+ * valid until the work on `stream` completes. */
+int mirage_mlp_train(mirage_mlp_t* mlp, const float* x, const float* t, int n, int steps, int batch,
+                     float lr, unsigned long long seed, void* stream);
 const char* mirage_mlp_last_error(void);
 
 /* Allocation-free forward model.  The paper has no counterpart: this entry

@@ -86,6 +86,8 @@ def load_library():
     lib.mirage_eval_iter.restype = ip
     lib.mirage_measure_ffma.argtypes = [i, vp, vp]
     lib.mirage_measure_ffma.restype = ip
+    lib.mirage_set_reserved_slots.argtypes = [vp, i]
+    lib.mirage_set_reserved_slots.restype = ip
     lib.mirage_last_launch_count.argtypes = [vp]
     lib.mirage_last_launch_count.restype = ip
     lib.mirage_last_phase_clocks.argtypes = [vp, vp]
@@ -117,6 +119,8 @@ def load_library():
     lib.mirage_mlp_grad.restype = ip
     lib.mirage_mlp_train_step.argtypes = [vp, vp, vp, i, ctypes.c_float, vp, vp, vp]
     lib.mirage_mlp_train_step.restype = ip
+    lib.mirage_mlp_train.argtypes = [vp, vp, vp, i, i, i, ctypes.c_float, ctypes.c_ulonglong, vp]
+    lib.mirage_mlp_train.restype = ip
     lib.mirage_mlp_last_error.argtypes = []
     lib.mirage_mlp_last_error.restype = ctypes.c_char_p
     _lib = lib
@@ -382,6 +386,15 @@ class MLP:
                   "mirage_mlp_grad")
         return g, loss, y
 
+    def train(self, x, t, steps, batch, lr, seed=0, stream=None):
+        """``steps`` Adam steps on minibatches of ``batch`` rows of (x, t)
+        drawn on the device (mirage_mlp_train)."""
+        x, t = x.contiguous(), t.contiguous()
+        self._chk(load_library().mirage_mlp_train(self.handle, _ptr(x), _ptr(t), int(x.shape[0]), int(steps),
+                                                  int(batch), float(lr), int(seed) & (2 ** 64 - 1),
+                                                  _stream_ptr(stream)), "mirage_mlp_train")
+        self._keep = (x, t)  # alive until the next call (the work is asynchronous)
+
     def train_step(self, x, t, lr, stream=None):
         loss = torch.zeros(1, dtype=torch.float64, device=x.device)
         y = torch.empty((x.shape[0], self.dims[-1]), dtype=torch.float32, device=x.device)
@@ -421,6 +434,10 @@ class Context:
 
     def forward(self, prob, lens, S, **kw):
         return mirage_forward(self.handle, prob, lens, S, **kw)
+
+    def reserve_slots(self, slots: int):
+        """Leave ``slots`` CTA slots free in the CGLS launches (mirage_set_reserved_slots)."""
+        _check(load_library().mirage_set_reserved_slots(self.handle, int(slots)), "mirage_set_reserved_slots")
 
     def launches(self) -> int:
         return mirage_last_launch_count(self.handle)

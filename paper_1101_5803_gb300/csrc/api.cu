@@ -110,6 +110,7 @@ struct mirage_ctx {
     int max_smem = 0;
     int max_smem_sm = 0;
     int last_launches = 0;
+    int reserved = 0;  // CTA slots the CGLS launches leave free (mirage_set_reserved_slots)
     // scratch
     DevBuf E, E64, Etmp, inv, cst, swp, dpad, nent, cstat, X, istat, slab, probs, cand_prob, items, counters;
     DevBuf stage;  // MIRAGE_MEM_HOST staging
@@ -132,6 +133,17 @@ struct mirage_ctx {
     int timed = 0;
     std::vector<void*> scratch_seen;     // scratch pointers the cached graphs were captured with
 };
+
+// CTAs of a persistent CGLS launch: per_sm on every SM, less the slots the
+// caller reserved for concurrent work on other streams (at least one)
+static long long cgls_slots(const mirage_ctx* ctx, int per_sm) {
+    return std::max<long long>(1, (long long)per_sm * ctx->sm_count - ctx->reserved);
+}
+
+// relative CG iteration count of lambda index k of an n-point grid (the
+// grids ascend): on the log-spaced grids of the workloads the count grows by
+// about 1.35x per step towards small lambda
+static double chain_weight(int n, int k) { return std::pow(1.35, (double)(n - 1 - k)); }
 
 namespace {
 void drop_graphs(mirage_ctx* ctx) {
@@ -614,6 +626,17 @@ int eval_impl(mirage_ctx* ctx, const mirage_problem_t* probs, int n_probs, const
         }
         return f;
     };
+    // chained calls: each CTA slot's share of the estimated cost of the call
+    double chain_budget = 0.0;
+    if (lam_start) {
+        double tw = 0.0;
+        for (int c = 0; c < n_cand; ++c) {
+            const Prob<T>& P = hp[prob_idx[c]];
+            const double work = (double)P.plen * P.K * P.K + 8.0 * P.nrays;
+            for (int k = 0; k < n_lam[c]; ++k) tw += work * chain_weight(n_lam[c], k);
+        }
+        chain_budget = tw / (double)cgls_slots(ctx, 2);
+    }
     for (int c = 0; c < n_cand; ++c) {
         const Prob<T>& P = hp[prob_idx[c]];
         const int place = pick_place<T>(ctx, P);
@@ -646,15 +669,43 @@ int eval_impl(mirage_ctx* ctx, const mirage_problem_t* probs, int n_probs, const
         // lambda grids ascend: smaller k = smaller lambda = more CG iterations
         auto cost_of = [&](int k) { return work * (double)(n_lam[c] - k + 4); };
         if (lam_start) {
-            // two chains from the predicted corner: down to the smallest
-            // lambda, and up from the next one
+            // chains from the predicted corner: down to the smallest lambda,
+            // and up from the next one.  A chain is cut into segments (each
+            // further segment starts cold) whose estimated cost stays within
+            // one CTA slot's share of the whole call, so that no work unit
+            // outlasts the persistent queue's balance.  Costs follow the
+            // iteration counts of log-spaced grids, which grow geometrically
+            // towards small lambda
             const int ks = std::min(std::max(lam_start[c], 0), n_lam[c] - 1);
-            double cd = 0.0, cu = 0.0;
-            for (int k = 0; k <= ks; ++k) cd += cost_of(k);
-            for (int k = ks + 1; k < n_lam[c]; ++k) cu += cost_of(k);
-            g.items.push_back({-cd, pack_chain(c, ks, 0)});
-            if (ks + 1 < n_lam[c]) g.items.push_back({-cu, pack_chain(c, ks + 1, n_lam[c] - 1)});
-            g.cost += cd + cu;
+            auto wk = [&](int k) { return work * chain_weight(n_lam[c], k); };
+            auto push_run = [&](int ka, int kb, double cd) {
+                g.items.push_back({-cd, pack_chain(c, ka, kb)});
+                g.cost += cd;
+            };
+            int ka = ks;
+            double cd = 0.0;
+            for (int k = ks; k >= 0; --k) {
+                if (k < ka && cd + wk(k) > chain_budget) {
+                    push_run(ka, k + 1, cd);
+                    ka = k;
+                    cd = 0.0;
+                }
+                cd += wk(k);
+            }
+            push_run(ka, 0, cd);
+            if (ks + 1 < n_lam[c]) {
+                ka = ks + 1;
+                cd = 0.0;
+                for (int k = ks + 1; k < n_lam[c]; ++k) {
+                    if (k > ka && cd + wk(k) > chain_budget) {
+                        push_run(ka, k - 1, cd);
+                        ka = k;
+                        cd = 0.0;
+                    }
+                    cd += wk(k);
+                }
+                push_run(ka, n_lam[c] - 1, cd);
+            }
         } else {
             for (int k = 0; k < n_lam[c]; ++k) {
                 g.items.push_back({-cost_of(k), pack_chain(c, k, k)});
@@ -722,7 +773,7 @@ int eval_impl(mirage_ctx* ctx, const mirage_problem_t* probs, int n_probs, const
         slab_stride = std::max(slab_stride, (g->slab + 255) / 256 * 256);
         // groups run concurrently: each owns its own CTA slots of the slab
         g_slab_off[gi] = slab_slots;
-        slab_slots += std::min<long long>((long long)g->per_sm * ctx->sm_count, (long long)g->items.size());
+        slab_slots += std::min<long long>(cgls_slots(ctx, g->per_sm), (long long)g->items.size());
     }
     if (o.mode == MIRAGE_MODE_PLAIN) slab_slots = std::max<long long>(slab_slots, max_lam);
     TRY(ctx->slab.ensure((size_t)slab_stride * std::max<long long>(slab_slots, 1)));
@@ -876,8 +927,7 @@ int eval_impl(mirage_ctx* ctx, const mirage_problem_t* probs, int n_probs, const
                 A.items = ditems + g_off[gi];
                 A.n_items = (int)g->items.size();
                 A.counter = dcnt + gi;
-                const int grid =
-                    (int)std::min<long long>((long long)g->per_sm * ctx->sm_count, (long long)g->items.size());
+                const int grid = (int)std::min<long long>(cgls_slots(ctx, g->per_sm), (long long)g->items.size());
                 if (g->fast) {
                     FastArgs fa;
                     std::memset(&fa, 0, sizeof(fa));
@@ -1291,6 +1341,16 @@ int mirage_eval_iter(mirage_ctx_t* ctx, const mirage_problem_t* probs, int n_pro
                                 dof, corner, kappa, s_out, status, st);
     return iter_impl<double>(ctx, probs, n_probs, lens, prob_idx, n_cand, n_iter, bhat, bhat_stride, chi2, reg, dof,
                              corner, kappa, s_out, status, st);
+}
+
+int mirage_set_reserved_slots(mirage_ctx_t* ctx, int slots) {
+    if (!ctx || slots < 0) {
+        set_error("set_reserved_slots: bad arguments");
+        return MIRAGE_ERR_ARG;
+    }
+    if (slots != ctx->reserved) drop_graphs(ctx);  // captured launches carry the old grid
+    ctx->reserved = slots;
+    return MIRAGE_OK;
 }
 
 int mirage_last_launch_count(const mirage_ctx_t* ctx) { return ctx ? ctx->last_launches : 0; }

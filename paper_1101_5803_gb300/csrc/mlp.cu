@@ -77,10 +77,13 @@ __device__ __forceinline__ float silu_g(float z) {
     return s * (1.f + z * (1.f - s));
 }
 
-// x (FP32) -> BF16 activations
-__global__ void k_to_bf16(const float* __restrict__ x, __nv_bfloat16* __restrict__ a, long n) {
+// x (FP32) -> BF16 activations; with idx, row j of the batch is row idx[j] of x
+__global__ void k_to_bf16(const float* __restrict__ x, const int* __restrict__ idx, int cols,
+                          __nv_bfloat16* __restrict__ a, long n) {
     const long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
-    if (i < n) a[i] = __float2bfloat16(x[i]);
+    if (i >= n) return;
+    const long src = idx ? (long)idx[i / cols] * cols + i % cols : i;
+    a[i] = __float2bfloat16(x[src]);
 }
 
 // Z += b (per column); hidden layers: A = bf16(silu(Z)); output layer: Y = Z
@@ -96,13 +99,16 @@ __global__ void k_bias_act(float* __restrict__ Z, const float* __restrict__ b, i
         Y[i] = z;
 }
 
-// dY = 2 (Y - T) / (n cols); loss partial sums
-__global__ void k_loss_grad(const float* __restrict__ Y, const float* __restrict__ T, long total,
-                            float* __restrict__ dZ, __nv_bfloat16* __restrict__ dZh, double* __restrict__ loss) {
+// dY = 2 (Y - T) / (n cols); loss partial sums.  With idx, row j of the
+// batch targets row idx[j] of T.
+__global__ void k_loss_grad(const float* __restrict__ Y, const float* __restrict__ T, const int* __restrict__ idx,
+                            int cols, long total, float* __restrict__ dZ, __nv_bfloat16* __restrict__ dZh,
+                            double* __restrict__ loss) {
     const long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
     double l = 0.0;
     if (i < total) {
-        const float d = Y[i] - T[i];
+        const long ti = idx ? (long)idx[i / cols] * cols + i % cols : i;
+        const float d = Y[i] - T[ti];
         dZ[i] = 2.f * d / (float)total;
         dZh[i] = __float2bfloat16(dZ[i]);
         l = (double)d * (double)d;
@@ -148,6 +154,44 @@ __global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float
     if (is_w[i]) ph[i] = __float2bfloat16(w);
 }
 
+// Adam whose bias corrections follow the device step counter (steps taken
+// so far, before this one), for the device-side training loop
+__global__ void k_adam_dev(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+                           float* __restrict__ v, long n, float lr, float b1, float b2, float eps,
+                           const long long* __restrict__ dstep, __nv_bfloat16* __restrict__ ph,
+                           const unsigned char* __restrict__ is_w) {
+    const long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float s = (float)(*dstep + 1);
+    const float c1 = 1.f - powf(b1, s), c2 = 1.f - powf(b2, s);
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float w = p[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    p[i] = w;
+    if (is_w[i]) ph[i] = __float2bfloat16(w);
+}
+
+// Minibatch rows of one training step: row slot j draws row
+// h(seed, step, j) mod n with h the splitmix64 finaliser (a counter-based
+// hash: the draw depends only on its three inputs)
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+__global__ void k_sample_rows(int* __restrict__ idx, int batch, int n, unsigned long long seed,
+                              const long long* __restrict__ dstep) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= batch) return;
+    const unsigned long long key =
+        seed * 0x9E3779B97F4A7C15ull + ((unsigned long long)*dstep << 24) + (unsigned long long)j;
+    idx[j] = (int)(mix64(key) % (unsigned long long)n);
+}
+__global__ void k_step_inc(long long* dstep) { *dstep += 1; }
+
 __global__ void k_params_bf16(const float* __restrict__ p, __nv_bfloat16* __restrict__ ph, long n) {
     const long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
     if (i < n) ph[i] = __float2bfloat16(p[i]);
@@ -186,6 +230,8 @@ struct mirage_mlp {
     float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
     Buf P, PH, M, V, G, ISW;   // params FP32, BF16 copy, Adam m, v, grads, weight mask
     Buf Z, A, DZ, DZH, DA, LOSS;  // per-batch work (grown on demand)
+    Buf IDX, DSTEP;            // device-side training loop: minibatch rows, step counter
+    cudaStream_t cap = nullptr;  // private stream on which the training step is captured
     long cap_rows = 0;
     std::vector<long> z_off, a_off;  // per layer offsets into Z / A (elements)
 };
@@ -226,15 +272,16 @@ int gemm(const __nv_bfloat16* A, long sam, long sak, const __nv_bfloat16* B, lon
     return MIRAGE_OK;
 }
 
-// forward pass storing Z (FP32) and A (BF16); Y (FP32) written to y
-int forward_pass(mirage_mlp* m, const float* x, int n, float* y, cudaStream_t st) {
+// forward pass storing Z (FP32) and A (BF16); Y (FP32) written to y.  With
+// idx, batch row j is row idx[j] of x.
+int forward_pass(mirage_mlp* m, const float* x, int n, float* y, cudaStream_t st, const int* idx = nullptr) {
     int r;
     if ((r = ensure_batch(m, n))) return r;
     float* Z = (float*)m->Z.p;
     __nv_bfloat16* A = (__nv_bfloat16*)m->A.p;
     const float* P = (const float*)m->P.p;
     const __nv_bfloat16* PH = (const __nv_bfloat16*)m->PH.p;
-    k_to_bf16<<<blocks((long)n * m->dims[0], 256), 256, 0, st>>>(x, A, (long)n * m->dims[0]);
+    k_to_bf16<<<blocks((long)n * m->dims[0], 256), 256, 0, st>>>(x, idx, m->dims[0], A, (long)n * m->dims[0]);
     for (int l = 1; l <= m->L; ++l) {
         const int in = m->dims[l - 1], out = m->dims[l];
         // Z_l = A_{l-1} W_l^T : A(m, k) = A[m in + k], B(k, j) = W[j in + k]
@@ -250,9 +297,9 @@ int forward_pass(mirage_mlp* m, const float* x, int n, float* y, cudaStream_t st
 
 // gradients of the MSE into m->G (and the loss into m->LOSS if wanted)
 int backward_pass(mirage_mlp* m, const float* x, const float* tgt, int n, float* yscratch, bool want_loss,
-                  cudaStream_t st) {
+                  cudaStream_t st, const int* idx = nullptr) {
     int r;
-    if ((r = forward_pass(m, x, n, yscratch, st))) return r;
+    if ((r = forward_pass(m, x, n, yscratch, st, idx))) return r;
     float* Z = (float*)m->Z.p;
     __nv_bfloat16* A = (__nv_bfloat16*)m->A.p;
     float* DZ = (float*)m->DZ.p;
@@ -263,7 +310,8 @@ int backward_pass(mirage_mlp* m, const float* x, const float* tgt, int n, float*
     double* loss = want_loss ? (double*)m->LOSS.p : nullptr;
     if (loss) MCK(cudaMemsetAsync(loss, 0, sizeof(double), st));
     const int outL = m->dims[m->L];
-    k_loss_grad<<<blocks((long)n * outL, 256), 256, 0, st>>>(yscratch, tgt, (long)n * outL, DZ, DZH, loss);
+    k_loss_grad<<<blocks((long)n * outL, 256), 256, 0, st>>>(yscratch, tgt, idx, outL, (long)n * outL, DZ, DZH,
+                                                             loss);
     MCK(cudaGetLastError());
     for (int l = m->L; l >= 1; --l) {
         const int in = m->dims[l - 1], out = m->dims[l];
@@ -345,8 +393,10 @@ int mirage_mlp_create(mirage_mlp_t** out, int device, int n_layers, const int* d
 int mirage_mlp_destroy(mirage_mlp_t* m) {
     if (!m) return MIRAGE_OK;
     cudaSetDevice(m->device);
-    Buf* bufs[] = {&m->P, &m->PH, &m->M, &m->V, &m->G, &m->ISW, &m->Z, &m->A, &m->DZ, &m->DZH, &m->DA, &m->LOSS};
+    Buf* bufs[] = {&m->P,  &m->PH,  &m->M,  &m->V,    &m->G,   &m->ISW,  &m->Z,
+                   &m->A,  &m->DZ,  &m->DZH, &m->DA,  &m->LOSS, &m->IDX, &m->DSTEP};
     for (Buf* b : bufs) b->release();
+    if (m->cap) cudaStreamDestroy(m->cap);
     delete m;
     return MIRAGE_OK;
 }
@@ -403,6 +453,57 @@ int mirage_mlp_train_step(mirage_mlp_t* m, const float* x, const float* t, int n
                                                      (float*)m->V.p, m->n_params, lr, m->b1, m->b2, m->eps, c1, c2,
                                                      (__nv_bfloat16*)m->PH.p, (const unsigned char*)m->ISW.p);
     MCK(cudaGetLastError());
+    return MIRAGE_OK;
+}
+
+int mirage_mlp_train(mirage_mlp_t* m, const float* x, const float* t, int n, int steps, int batch, float lr,
+                     unsigned long long seed, void* stream) {
+    if (!m || !x || !t || n < 1 || steps < 0 || batch < 1 || batch > (1 << 20))
+        return mlp_fail(MIRAGE_ERR_ARG, "mlp_train: bad arguments");
+    if (steps == 0) return MIRAGE_OK;
+    MCK(cudaSetDevice(m->device));
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    int r;
+    // every buffer the step touches exists before the capture (no allocation inside it)
+    if ((r = ensure_batch(m, batch)) || (r = m->IDX.ensure(sizeof(int) * (size_t)batch)) ||
+        (r = m->DSTEP.ensure(sizeof(long long))))
+        return r;
+    if (!m->cap) MCK(cudaStreamCreateWithFlags(&m->cap, cudaStreamNonBlocking));
+    long long* dstep = (long long*)m->DSTEP.p;
+    int* idx = (int*)m->IDX.p;
+    float* y = (float*)m->DA.p;  // the step's forward output (DA is free until the backward pass)
+    const long long s0 = m->step;
+    MCK(cudaMemcpyAsync(dstep, &s0, sizeof(long long), cudaMemcpyHostToDevice, st));
+
+    // one training step: draw rows, forward, MSE gradient, Adam; captured once
+    cudaGraph_t graph = nullptr;
+    MCK(cudaStreamBeginCapture(m->cap, cudaStreamCaptureModeThreadLocal));
+    k_sample_rows<<<blocks(batch, 256), 256, 0, m->cap>>>(idx, batch, n, seed, dstep);
+    r = backward_pass(m, x, t, batch, y, false, m->cap, idx);
+    if (!r) {
+        k_adam_dev<<<blocks(m->n_params, 256), 256, 0, m->cap>>>(
+            (float*)m->P.p, (const float*)m->G.p, (float*)m->M.p, (float*)m->V.p, m->n_params, lr, m->b1, m->b2,
+            m->eps, dstep, (__nv_bfloat16*)m->PH.p, (const unsigned char*)m->ISW.p);
+        k_step_inc<<<1, 1, 0, m->cap>>>(dstep);
+    }
+    const cudaError_t ec = cudaStreamEndCapture(m->cap, &graph);
+    if (r) {
+        if (graph) cudaGraphDestroy(graph);
+        return r;
+    }
+    if (ec != cudaSuccess || !graph)
+        return mlp_fail(MIRAGE_ERR_CUDA, std::string("mlp_train: capture failed: ") + cudaGetErrorString(ec));
+    cudaGraphExec_t exec = nullptr;
+    const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess)
+        return mlp_fail(MIRAGE_ERR_CUDA, std::string("mlp_train: instantiate failed: ") + cudaGetErrorString(ei));
+    cudaError_t el = cudaSuccess;
+    for (int k = 0; k < steps && el == cudaSuccess; ++k) el = cudaGraphLaunch(exec, st);
+    cudaGraphExecDestroy(exec);
+    if (el != cudaSuccess)
+        return mlp_fail(MIRAGE_ERR_CUDA, std::string("mlp_train: graph launch failed: ") + cudaGetErrorString(el));
+    m->step += steps;
     return MIRAGE_OK;
 }
 

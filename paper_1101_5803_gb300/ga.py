@@ -66,6 +66,8 @@ class GAConfig:
     batch: int = 256
     lr: float = 2e-3
     fallback_rho: float = 0.3
+    overlap_training: bool = True
+    reserved_slots: int = 8
     seed: int = 0
 
 
@@ -104,13 +106,13 @@ class Surrogate:
         return X, Y
 
     def train(self, steps: int, batch: int, lr: float, rng) -> None:
+        """``steps`` Adam steps on minibatches of the rows gathered so far,
+        drawn and run on the device in one library call."""
         X, Y = self._norm()
         xs = torch.as_tensor(((X - self.mu) / self.sd).astype(np.float32), device="cuda")
         ys = torch.as_tensor(((Y - self.ymu) / self.ysd).astype(np.float32), device="cuda")
         n = xs.shape[0]
-        for _ in range(steps):
-            idx = torch.as_tensor(rng.integers(0, n, min(batch, n)), device="cuda")
-            self.net.train_step(xs[idx], ys[idx], lr)
+        self.net.train(xs, ys, steps, min(batch, n), lr, seed=int(rng.integers(0, 2 ** 62)))
 
     def predict(self, lens: np.ndarray) -> np.ndarray:
         """Standardised predictions [n, 2] (log chi2*, log10 lambda*)."""
@@ -153,7 +155,14 @@ def _offspring(pop: np.ndarray, fit: np.ndarray, n: int, cfg: GAConfig, rng):
 
 
 def run_ga(ctx: Context, wl: Workload, cfg: GAConfig, log=None):
-    """Run the GA on one problem; returns (history, best lens, best chi2)."""
+    """Run the GA on one problem; returns (history, best lens, best chi2).
+
+    With the surrogate and ``overlap_training``, the network trains on a
+    side stream while each generation's exact solves run (the solve
+    launches leave ``reserved_slots`` CTA slots free for it), on the exact
+    results gathered up to the previous generation: the screen of
+    generation g uses a network trained on generations 0..g-2, and the
+    surrogate is off the solves' critical path."""
     rng = np.random.default_rng(cfg.seed)
     n_lam = int(wl.lambdas.shape[1])
     lam_row = wl.lambdas[0].cpu().numpy()
@@ -163,67 +172,106 @@ def run_ga(ctx: Context, wl: Workload, cfg: GAConfig, log=None):
     pidx = np.zeros(cfg.pop, np.int32)
     nl = np.full(cfg.pop, n_lam, np.int32)
     sur = Surrogate(cfg.hidden, cfg.seed) if cfg.surrogate else None
+    overlap = sur is not None and cfg.overlap_training
+    side = torch.cuda.Stream() if overlap else None
+    trained = [None]  # event recorded after the last training launch
 
-    def evaluate(lens, warm, lam_start=None):
-        out = ctx.eval_batch(probs, torch.as_tensor(lens, device="cuda"), pidx, lam_dev, nl, tol=cfg.tol,
-                             warm_x=warm, lam_start=lam_start, want_all_x=True)
+    def launch(lens, warm, lam_start=None):
+        return ctx.eval_batch(probs, torch.as_tensor(lens, device="cuda"), pidx, lam_dev, nl, tol=cfg.tol,
+                              warm_x=warm, lam_start=lam_start, want_all_x=cfg.warm_start)
+
+    def collect(lens, out):
         chi2 = out["chi2"].cpu().numpy()
         corner = out["corner"].cpu().numpy()
         fit = chi2[np.arange(len(lens)), corner]
         fit = np.where(np.isfinite(fit), fit, np.inf)
         return fit, lam_row[corner], out
 
-    t0 = time.perf_counter()
-    fit, lam_star, out = evaluate(pop, None)
-    X_pop = out["all_x"]
-    hist = [GenStats(0, float(fit.min()), cfg.pop, cfg.pop, int(out["iters"].sum().item()),
-                     time.perf_counter() - t0, None, None, False)]
-    if sur is not None:
-        sur.add(pop, fit, lam_star)
-        sur.train(cfg.train_steps * 3, cfg.batch, cfg.lr, rng)
-    screen = sur is not None
-    for gen in range(1, cfg.generations + 1):
+    def train(steps):
+        if not overlap:
+            sur.train(steps, cfg.batch, cfg.lr, rng)
+            return
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            sur.train(steps, cfg.batch, cfg.lr, rng)
+            ev = torch.cuda.Event()
+            ev.record(side)
+        trained[0] = ev
+
+    def predict(lens):
+        # the network's buffers are shared by training and inference
+        if trained[0] is not None:
+            torch.cuda.current_stream().wait_event(trained[0])
+        return sur.predict(lens)
+
+    if overlap:
+        ctx.reserve_slots(cfg.reserved_slots)
+    try:
         t0 = time.perf_counter()
-        n_draw = cfg.pop * (cfg.oversample if screen else 1)
-        kids, par = _offspring(pop, fit, n_draw, cfg, rng)
-        if screen:
-            pred = sur.predict(kids)[:, 0]
-            keep = np.argsort(pred)[:cfg.pop]
-            kids, par = kids[keep], par[keep]
-        warm = X_pop[par].contiguous() if cfg.warm_start else None
-        lam_start = None
-        if cfg.lam_chain and sur is not None:
-            # grid index nearest the predicted log10 lambda* of each child
-            l10 = sur.predict(kids)[:, 1] * sur.ysd[1] + sur.ymu[1]
-            lam_start = np.abs(np.log10(lam_row)[None, :] - l10[:, None]).argmin(axis=1).astype(np.int32)
-        kfit, klam, kout = evaluate(kids, warm, lam_start)
-        rm = rho = None
-        was_screened = screen
+        fit, lam_star, out = collect(pop, launch(pop, None))
+        X_pop = out["all_x"] if cfg.warm_start else None
+        hist = [GenStats(0, float(fit.min()), cfg.pop, cfg.pop, int(out["iters"].sum().item()),
+                         time.perf_counter() - t0, None, None, False)]
         if sur is not None:
-            rm = sur.rmse(kids, kfit, klam)
-            ok = np.isfinite(kfit)
-            rho = rank_corr(sur.predict(kids[ok])[:, 0], kfit[ok]) if ok.sum() > 2 else 0.0
-            screen = rho >= cfg.fallback_rho
-            sur.add(kids, kfit, klam)
-            sur.train(cfg.train_steps, cfg.batch, cfg.lr, rng)
-        # binary tournaments between offspring and parents (mu + lambda)
-        allp = np.concatenate([pop, kids])
-        allf = np.concatenate([fit, kfit])
-        allx = torch.cat([X_pop, kout["all_x"]])
-        a = rng.permutation(cfg.pop)
-        b = cfg.pop + rng.permutation(cfg.pop)
-        win = np.where(allf[a] <= allf[b], a, b)
-        # keep the best individual found so far
-        best = int(np.argmin(allf))
-        if best not in win:
-            win[np.argmax(allf[win])] = best
-        pop, fit = allp[win], allf[win]
-        X_pop = allx[torch.as_tensor(win, device="cuda")].contiguous()
-        st = GenStats(gen, float(fit.min()), cfg.pop, n_draw, int(kout["iters"].sum().item()),
-                      time.perf_counter() - t0, rm, rho, bool(was_screened))
-        hist.append(st)
-        if log:
-            log(st)
+            sur.add(pop, fit, lam_star)
+            train(cfg.train_steps * (1 if overlap else 3))
+        # with overlapped training the first network is still training beside
+        # generation 1's solves, so generation 1 is drawn unscreened
+        screen = sur is not None and not overlap
+        for gen in range(1, cfg.generations + 1):
+            t0 = time.perf_counter()
+            n_draw = cfg.pop * (cfg.oversample if screen else 1)
+            kids, par = _offspring(pop, fit, n_draw, cfg, rng)
+            if screen:
+                pred = predict(kids)[:, 0]
+                keep = np.argsort(pred)[:cfg.pop]
+                kids, par = kids[keep], par[keep]
+            warm = X_pop[par].contiguous() if cfg.warm_start else None
+            lam_start = None
+            if cfg.lam_chain and sur is not None and (screen or not overlap):
+                # grid index nearest the predicted log10 lambda* of each child
+                l10 = predict(kids)[:, 1] * sur.ysd[1] + sur.ymu[1]
+                lam_start = np.abs(np.log10(lam_row)[None, :] - l10[:, None]).argmin(axis=1).astype(np.int32)
+            if overlap and gen > 1:
+                # on generations 0..gen-1, queued before this generation's
+                # solves so that it runs beside them (the side stream waits
+                # only for the work queued so far: the screen's inference)
+                train(cfg.train_steps)
+            kfit, klam, kout = collect(kids, launch(kids, warm, lam_start))
+            rm = rho = None
+            was_screened = screen
+            if sur is not None:
+                ok = np.isfinite(kfit) & (kfit > 0)
+                p = predict(kids)
+                y = np.stack([np.log(kfit[ok]), np.log10(klam[ok])], axis=1)
+                rm = float(np.sqrt(np.mean(((y - sur.ymu) / sur.ysd - p[ok]) ** 2)))
+                rho = rank_corr(p[ok, 0], kfit[ok]) if ok.sum() > 2 else 0.0
+                screen = rho >= cfg.fallback_rho
+                sur.add(kids, kfit, klam)
+                if not overlap:
+                    train(cfg.train_steps)
+            # binary tournaments between offspring and parents (mu + lambda)
+            allp = np.concatenate([pop, kids])
+            allf = np.concatenate([fit, kfit])
+            allx = torch.cat([X_pop, kout["all_x"]]) if cfg.warm_start else None
+            a = rng.permutation(cfg.pop)
+            b = cfg.pop + rng.permutation(cfg.pop)
+            win = np.where(allf[a] <= allf[b], a, b)
+            # keep the best individual found so far
+            best = int(np.argmin(allf))
+            if best not in win:
+                win[np.argmax(allf[win])] = best
+            pop, fit = allp[win], allf[win]
+            X_pop = allx[torch.as_tensor(win, device="cuda")].contiguous() if cfg.warm_start else None
+            st = GenStats(gen, float(fit.min()), cfg.pop, n_draw, int(kout["iters"].sum().item()),
+                          time.perf_counter() - t0, rm, rho, bool(was_screened))
+            hist.append(st)
+            if log:
+                log(st)
+    finally:
+        if overlap:
+            torch.cuda.synchronize()
+            ctx.reserve_slots(0)
     b = int(np.argmin(fit))
     return hist, pop[b], float(fit[b])
 

@@ -100,3 +100,59 @@ def test_training_fits_a_smooth_map(binding):
     mse = float(np.mean((Y - T) ** 2))
     assert mse < 0.02 * first and mse < 5e-3, (first, mse)
     net.close()
+
+
+def _rows(seed, step, batch, n):
+    """The minibatch rows of mirage_mlp_train's step `step`: slot j takes
+    splitmix64-finaliser(seed * golden + (step << 24) + j) mod n, written
+    out here from the finaliser's published definition."""
+    M = (1 << 64) - 1
+    out = []
+    for j in range(batch):
+        z = (seed * 0x9E3779B97F4A7C15 + (step << 24) + j) & M
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & M
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & M
+        z ^= z >> 31
+        out.append(z % n)
+    return np.array(out)
+
+
+def test_device_training_loop_matches_host_steps(binding):
+    # mirage_mlp_train draws each step's rows on the device; with the same
+    # rows handed to train_step one at a time the parameters must agree
+    rng = np.random.default_rng(7)
+    X = rng.standard_normal((300, 7)).astype(np.float32)
+    T = rng.standard_normal((300, 2)).astype(np.float32)
+    xg, tg = torch.as_tensor(X, device="cuda"), torch.as_tensor(T, device="cuda")
+    a = binding.MLP([7, 64, 48, 2], seed=5)
+    b = binding.MLP([7, 64, 48, 2], seed=5)
+    a.train(xg, tg, steps=3, batch=96, lr=3e-3, seed=11)
+    for k in range(3):
+        idx = torch.as_tensor(_rows(11, k, 96, 300), device="cuda")
+        b.train_step(xg[idx], tg[idx], 3e-3)
+    torch.cuda.synchronize()
+    pa, pb = a.get_params(), b.get_params()
+    np.testing.assert_allclose(pa, pb, rtol=1e-5, atol=1e-6)
+    # a second call continues the step count (Adam's bias corrections)
+    a.train(xg, tg, steps=1, batch=96, lr=3e-3, seed=12)
+    idx = torch.as_tensor(_rows(12, 3, 96, 300), device="cuda")
+    b.train_step(xg[idx], tg[idx], 3e-3)
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(a.get_params(), b.get_params(), rtol=1e-5, atol=1e-6)
+    a.close()
+    b.close()
+
+
+def test_device_training_loop_fits_a_smooth_map(binding):
+    net = binding.MLP([7, 64, 64, 2], seed=3)
+    rng = np.random.default_rng(4)
+    X = rng.uniform(-1, 1, (2048, 7)).astype(np.float32)
+    T = np.stack([np.sin(X[:, 0] * 2) + X[:, 1] * X[:, 2], np.cos(X[:, 3]) - 0.5 * X[:, 4] ** 2], 1)
+    T = T.astype(np.float32)
+    xg, tg = torch.as_tensor(X, device="cuda"), torch.as_tensor(T, device="cuda")
+    first = float(np.mean((net.forward(xg).cpu().numpy() - T) ** 2))
+    net.train(xg, tg, steps=1500, batch=256, lr=3e-3, seed=1)
+    Y = net.forward(xg).cpu().numpy()
+    mse = float(np.mean((Y - T) ** 2))
+    assert mse < 0.02 * first and mse < 5e-3, (first, mse)
+    net.close()

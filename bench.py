@@ -34,6 +34,7 @@ if ROOT not in sys.path:
 METRIC = "lens-model evals/s at 64^2 image, CG rel-res 1e-6 (256 cand x 16 lambda)"
 UNIT = "evals/s"
 N_CAND, N_LAM, TOL = 256, 16, 1e-6
+TIGHT_TOL = 3e-8  # the tighter internal tolerance of the accuracy section
 CONFIG = {"workload": "ga64: 64x64 image 0.05\"/px, 32x32 source +-0.8\", 9x9 PSF sigma 1.5px, Laplacian H, "
                       "256 candidates x 16 lambdas 1e-4..1e2, CGLS rel-res 1e-6, L-curve corner",
           "global_batch": N_CAND, "n_lambda": N_LAM, "l2": "flushed between timed steps (512 MiB write)"}
@@ -319,6 +320,66 @@ def run_gpu(args):
             if line.startswith("traffic_bytes_per_item:"):
                 traffic = float(line.split(":")[1]) * float(iters.size)
 
+    def _accuracy_section():
+        # per-result error against the FP64 oracle on a sample of the measured
+        # population: 8 candidates x 16 lambdas, the same problem arrays, at
+        # the benchmark's tolerance and at the tighter internal tolerance
+        from oracle.solve import Problem as OracleProblem, eval_candidate
+        n_acc = 8
+        idx = np.arange(0, N_CAND, N_CAND // n_acc)[:n_acc]
+        g = wl.geom
+        f64 = lambda t: t.double().cpu().numpy().reshape(g.ny, g.nx)
+        oprob = OracleProblem(g, f64(wl.problem.d), f64(wl.problem.sigma),
+                              wl.problem.mask.cpu().numpy().reshape(g.ny, g.nx),
+                              wl.problem.psf.double().cpu().numpy().reshape(g.kpsf, g.kpsf))
+        lams = wl.lambdas[0].cpu().numpy()
+        lens_h = wl.lens.cpu().numpy()
+        t0 = time.perf_counter()
+        refs = [eval_candidate(oprob, lens_h[c], lams) for c in idx]
+        t_oracle = time.perf_counter() - t0
+        sel = torch.as_tensor(idx, device="cuda")
+        acc = {"sample": f"{n_acc} candidates x {N_LAM} lambdas of the timed population (FP64 dense-Cholesky oracle)",
+               "oracle_s": t_oracle}
+        for name, tol in (("tol_1e-6", TOL), ("tol_3e-8", TIGHT_TOL)):
+            sub = ctx.eval_batch(probs, wl.lens[sel].contiguous(), wl.prob_idx[idx], wl.lambdas[sel].contiguous(),
+                                 wl.n_lam[idx], tol=tol, maxit=100000, want_all_x=True)
+            X = sub["all_x"].double().cpu().numpy()
+            chi = sub["chi2"].cpu().numpy()
+            ist = sub["item_status"].cpu().numpy()
+            ce, se = [], []
+            for j, r in enumerate(refs):
+                ce += list(np.abs(chi[j] - r.chi2) / r.chi2)
+                se += [np.linalg.norm(X[j, k, :g.ns] - r.s[k]) / np.linalg.norm(r.s[k]) for k in range(N_LAM)]
+            ce, se = np.array(ce), np.array(se)
+            acc[name] = {"chi2_rel_err_max": float(ce.max()), "chi2_rel_err_median": float(np.median(ce)),
+                         "items_chi2_over_1e-5": int((ce > 1e-5).sum()),
+                         "s_rel_err_max": float(se.max()), "s_rel_err_median": float(np.median(se)),
+                         "items_s_over_1e-4": int((se > 1e-4).sum()), "items": int(ce.size),
+                         "items_flagged": int(((ist & 7) != 0).sum())}
+            if tol == TOL:
+                # the sampled candidates' results are those of the timed step
+                acc[name]["identical_to_timed_step"] = bool(np.array_equal(chi, out["chi2"][sel].cpu().numpy()))
+        return acc
+
+    acc_res = _guarded("accuracy", _accuracy_section)
+
+    def _tight_section():
+        # the whole population at the tighter internal tolerance, where every
+        # sampled result meets |ds|/|s| <= 1e-4 and |dchi2|/chi2 <= 1e-5
+        tout = ctx.eval_batch(probs, wl.lens, wl.prob_idx, wl.lambdas, wl.n_lam, tol=TIGHT_TOL, maxit=100000)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        tout = ctx.eval_batch(probs, wl.lens, wl.prob_idx, wl.lambdas, wl.n_lam, tol=TIGHT_TOL, maxit=100000,
+                              out=tout)
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        return {"tol": TIGHT_TOL, "evals_per_s": N_CAND / (ms / 1e3), "ms": ms,
+                "cg_iters_mean_per_item": float(tout["iters"].float().mean().item()),
+                "items_flagged": int(((tout["item_status"] & 7) != 0).sum().item())}
+
+    tight_res = _guarded("tight_tolerance", _tight_section)
+
     def _iter_section():
         # the paper's own fitness: 40 CGLS iterations per candidate, L-curve over
         # the iterations, Monte Carlo degrees of freedom (FP64 arithmetic)
@@ -398,22 +459,25 @@ def run_gpu(args):
 
     wide = _guarded("wide_psf", _wide_section)
 
-    n_gen = int(os.environ.get("MIRAGE_GA_GENERATIONS", "4"))
+    n_gen = int(os.environ.get("MIRAGE_GA_GENERATIONS", "8"))
 
     def _ga_section():
-        # GA generations on the same problem: surrogate screen vs none
+        # GA generations on the same problem: the surrogate screen (4x
+        # oversampled offspring, network trained beside the solves, lambda
+        # chains from its predicted corner) against no screen
         from paper_1101_5803_gb300.ga import GAConfig, run_ga
         ga_res = {}
-        for name, sur_on, chain in (("with_surrogate", True, False), ("with_surrogate_lambda_chains", True, True),
-                                    ("without", False, False)):
-            cfg = GAConfig(pop=N_CAND, generations=n_gen, surrogate=sur_on, lam_chain=chain, seed=7)
+        for name, sur_on in (("with_surrogate", True), ("without", False)):
+            cfg = GAConfig(pop=N_CAND, generations=n_gen, surrogate=sur_on, lam_chain=sur_on, seed=7)
             hist, _, bchi = run_ga(ctx, wl, cfg)
             gens = hist[1:]
             t_gen = sum(h.seconds for h in gens)
-            ga_res[name] = {"exact_evals_per_s": sum(h.exact_evals for h in gens) / t_gen,
+            ex = sum(h.exact_evals for h in gens)
+            ga_res[name] = {"exact_evals_per_s": ex / t_gen,
                             "decisions_per_s": sum(h.decisions for h in gens) / t_gen,
-                            "cg_iters_per_exact_eval": sum(h.cg_iters for h in gens) / max(1, sum(h.exact_evals for h in gens)),
+                            "cg_iters_per_exact_eval": sum(h.cg_iters for h in gens) / max(1, ex),
                             "best_chi2_by_gen": [round(h.best_chi2, 2) for h in hist],
+                            "seconds_by_gen": [round(h.seconds, 4) for h in hist],
                             "screened_gens": int(sum(h.screened for h in gens)),
                             "rank_corr_by_gen": [None if h.surrogate_rho is None else round(h.surrogate_rho, 3)
                                                  for h in gens],
@@ -422,6 +486,8 @@ def run_gpu(args):
                             "fallback_rate": (1.0 - sum(h.screened for h in gens) / max(1, len(gens))) if sur_on else None}
         ga_res["generations"] = n_gen
         ga_res["oversample"] = 4
+        ga_res["note"] = ("decisions = offspring ranked per second (surrogate screen, then the exact solve of the "
+                          "pop best); every survivor's fitness comes from the exact solve")
         return ga_res
 
     ga_res = _guarded("ga_surrogate", _ga_section)
@@ -472,6 +538,16 @@ def run_gpu(args):
                    "items_converged_frac": float(((item_status & 7) == 0).mean()),
                    "status_bits_any": int(np.bitwise_or.reduce(status))},
             "phase_ms": {"raytrace": phase[0], "cgls": phase[1], "finalize": phase[2]},
+            "batched_surrogate": (None if "with_surrogate" not in ga_res else {
+                "decisions_per_s": ga_res["with_surrogate"]["decisions_per_s"],
+                "exact_evals_per_s": ga_res["with_surrogate"]["exact_evals_per_s"],
+                "speedup_vs_plain": ga_res["with_surrogate"]["decisions_per_s"] / plain,
+                "exact_speedup_vs_plain": ga_res["with_surrogate"]["exact_evals_per_s"] / plain,
+                "exact_evals_per_s_without_surrogate": ga_res["without"]["exact_evals_per_s"],
+                "workload": f"GA on the same problem, population {N_CAND}, {n_gen} generations, 4x oversampled "
+                            f"offspring"}),
+            "accuracy": acc_res,
+            "tight_tolerance": tight_res,
             "ga_surrogate": ga_res,
             "pso": pso_res,
             "iter_lcurve": iter_res,
@@ -546,6 +622,199 @@ def run_profile_forward() -> int:
     return 0
 
 
+def _oracle_problem(prob, geom):
+    """The oracle's view of a device problem: the same arrays in float64."""
+    from oracle.solve import Problem as OracleProblem
+    f64 = lambda t: t.double().cpu().numpy().reshape(geom.ny, geom.nx)
+    return OracleProblem(geom, f64(prob.d), f64(prob.sigma), prob.mask.cpu().numpy().reshape(geom.ny, geom.nx),
+                         prob.psf.double().cpu().numpy().reshape(geom.kpsf, geom.kpsf))
+
+
+def _errs(chi, X, ns, ref, n):
+    """Per-lambda |dchi2|/chi2 and |ds|/|s| of one candidate against an oracle result."""
+    ce = np.abs(chi[:n] - ref.chi2[:n]) / ref.chi2[:n]
+    se = np.array([np.linalg.norm(X[k, :ns] - ref.s[k]) / np.linalg.norm(ref.s[k]) for k in range(n)])
+    return ce, se
+
+
+def _summ(ce, se):
+    ce, se = np.concatenate(ce), np.concatenate(se)
+    return {"items": int(ce.size), "chi2_rel_err_max": float(ce.max()), "chi2_rel_err_median": float(np.median(ce)),
+            "items_chi2_over_1e-5": int((ce > 1e-5).sum()), "s_rel_err_max": float(se.max()),
+            "s_rel_err_median": float(np.median(se)), "items_s_over_1e-4": int((se > 1e-4).sum())}
+
+
+def _timed_call(fn):
+    import torch
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    out = fn()
+    e1.record(st)
+    torch.cuda.synchronize()
+    return out, e0.elapsed_time(e1)
+
+
+def run_workload(name: str, args) -> int:
+    """One of the other stated workloads at full size, with a sampled oracle
+    check; prints one JSON line (not the default benchmark line)."""
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from oracle.solve import eval_candidate
+    from paper_1101_5803_gb300 import binding
+    from paper_1101_5803_gb300 import problems as P
+
+    ctx = binding.Context(0, binding.MIRAGE_FP32)
+    res = {"workload": name}
+    if name == "uneven1024":
+        # 1024 candidates, each with its own observation: images {48..128}^2 with
+        # annular masks, sources {16..48}^2, PSFs {7,11,15}, 8..32 lambdas
+        mw = P.uneven_workload(ctx, 1024, seed=1)
+        call = lambda **kw: ctx.eval_batch(mw.problems, mw.lens, mw.prob_idx, mw.lambdas, mw.n_lam, tol=TOL, **kw)
+        call()  # warm-up (kernel attributes, scratch)
+        out, ms = _timed_call(lambda: call(want_all_x=True))
+        ist = out["item_status"].cpu().numpy()
+        valid = np.arange(ist.shape[1])[None, :] < mw.n_lam[:, None]
+        res.update({"config": "1024 candidates, images {48,64,96,128}^2 (6.4\"), annular masks 0.3-0.6\" / "
+                              "1.5-2.5\", sources {16,24,32,48}^2 over +-0.8\", PSFs {7,11,15} px, 8-32 lambdas "
+                              "1e-4..1e2, tol 1e-6, one call",
+                    "ms": ms, "evals_per_s": 1024 / (ms / 1e3), "items": int(valid.sum()),
+                    "cg_iterations": int(out["iters"].cpu().numpy()[valid].sum()),
+                    "items_converged_frac": float(((ist & 7) == 0)[valid].mean()),
+                    "status_bits_any": int(np.bitwise_or.reduce(out["status"].cpu().numpy()))})
+        # oracle on 16 sampled candidates (every image size, their own lambda grids)
+        rng = np.random.default_rng(3)
+        pick = np.sort(rng.choice(1024, 16, replace=False))
+        X = out["all_x"].double().cpu().numpy()
+        chi = out["chi2"].cpu().numpy()
+        lens_h = mw.lens.cpu().numpy()
+        lam_h = mw.lambdas.cpu().numpy()
+        ce, se = [], []
+        t0 = time.perf_counter()
+        refs = {}
+        for c in pick:
+            pr = mw.problems[c]
+            r = refs[c] = eval_candidate(_oracle_problem(pr, pr.geom), lens_h[c], lam_h[c, :mw.n_lam[c]])
+            a, b = _errs(chi[c], X[c], pr.geom.ns, r, mw.n_lam[c])
+            ce.append(a)
+            se.append(b)
+        res["oracle_sample"] = dict(_summ(ce, se), candidates=[int(c) for c in pick],
+                                    oracle_s=time.perf_counter() - t0)
+        # the same candidates at the tighter internal tolerance
+        sel = torch.as_tensor(pick, device="cuda")
+        tout = ctx.eval_batch([mw.problems[c] for c in pick], mw.lens[sel].contiguous(),
+                              np.arange(len(pick), dtype=np.int32), mw.lambdas[sel].contiguous(), mw.n_lam[pick],
+                              tol=TIGHT_TOL, maxit=200000, want_all_x=True)
+        Xt = tout["all_x"].double().cpu().numpy()
+        ct = tout["chi2"].cpu().numpy()
+        ce, se = [], []
+        for j, c in enumerate(pick):
+            a, b = _errs(ct[j], Xt[j], mw.problems[c].geom.ns, refs[c], mw.n_lam[c])
+            ce.append(a)
+            se.append(b)
+        res["oracle_sample_tol_3e-8"] = dict(_summ(ce, se), items_flagged=int(
+            ((tout["item_status"].cpu().numpy() & 7) != 0)[np.arange(tout["item_status"].shape[1])[None, :]
+                                                             < mw.n_lam[pick][:, None]].sum()))
+    elif name == "ga128":
+        # the end-to-end GA: 128x128 image at 0.03", 48x48 source, 11x11 PSF,
+        # population 512 x G generations, 4x oversampled surrogate screen
+        from paper_1101_5803_gb300.ga import GAConfig, run_ga
+        gens = args.generations
+        wl = P.e2e128_workload(ctx, n_cand=512, seed=0)
+        cfg = GAConfig(pop=512, generations=gens, surrogate=True, lam_chain=True, seed=0)
+        hist, best, bchi = run_ga(ctx, wl, cfg)
+        g = hist[1:]
+        tg = sum(h.seconds for h in g)
+        rms = [h.surrogate_rmse for h in g if h.surrogate_rmse is not None]
+        res.update({"config": f"128x128 image 0.03\"/px, 48x48 source +-0.8\", 11x11 PSF sigma 1.5 px, Laplacian, "
+                              f"16 lambdas 1e-4..1e2, population 512 x {gens} generations, 4x oversampled screen",
+                    "seconds": tg, "exact_evals_per_s": sum(h.exact_evals for h in g) / tg,
+                    "decisions_per_s": sum(h.decisions for h in g) / tg,
+                    "fallback_rate": 1.0 - sum(h.screened for h in g) / max(1, len(g)),
+                    "surrogate_rmse_first_last_median": [rms[0], rms[-1], float(np.median(rms))] if rms else None,
+                    "surrogate_rmse_by_gen": [None if h.surrogate_rmse is None else round(h.surrogate_rmse, 4) for h in g],
+                    "rank_corr_by_gen": [None if h.surrogate_rho is None else round(h.surrogate_rho, 3) for h in g],
+                    "best_chi2_by_gen": [round(h.best_chi2, 2) for h in hist],
+                    "best_lens": [float(v) for v in best], "best_chi2": bchi,
+                    "true_lens": [float(v) for v in __import__("synth").TRUE_LENS]})
+        # oracle on the best lens: the exact solve's corner chi^2 and every lambda
+        lams = wl.lambdas[0].cpu().numpy()
+        out = ctx.eval_batch([wl.problem], torch.as_tensor(best[None, :], device="cuda"), [0], wl.lambdas[:1],
+                             wl.n_lam[:1], tol=TOL, want_all_x=True)
+        t0 = time.perf_counter()
+        r = eval_candidate(_oracle_problem(wl.problem, wl.geom), best, lams)
+        a, b = _errs(out["chi2"][0].cpu().numpy(), out["all_x"][0].double().cpu().numpy(), wl.geom.ns, r, len(lams))
+        res["oracle_best_lens"] = dict(_summ([a], [b]), corner_gpu=int(out["corner"][0].item()), corner_oracle=r.corner,
+                                       oracle_s=time.perf_counter() - t0)
+    elif name == "large256":
+        # 64 candidates x 32 lambdas at 256x256 (128x128 source, 21x21 PSF),
+        # CG to 1e-6, with and without the surrogate's predicted lambda*
+        # starting each candidate's chains
+        from oracle.cg import chi2_reg, cgls_solve, sparse_operators
+        from paper_1101_5803_gb300.ga import Surrogate
+        n_c, n_l = 64, 32
+        wl = P.large_workload(ctx, n_cand=n_c + 16, n_lam=n_l, seed=3)
+        lams = wl.lambdas[0].cpu().numpy()
+        # the surrogate learns (log chi2*, log10 lambda*) from 16 other candidates
+        tr = slice(n_c, n_c + 16)
+        tout = ctx.eval_batch([wl.problem], wl.lens[tr].contiguous(), wl.prob_idx[tr], wl.lambdas[tr].contiguous(),
+                              wl.n_lam[tr], tol=TOL)
+        tc = tout["corner"].cpu().numpy()
+        tchi = tout["chi2"].cpu().numpy()[np.arange(16), tc]
+        sur = Surrogate(256, 0)
+        sur.add(wl.lens[tr].cpu().numpy(), tchi, lams[tc])
+        sur.train(600, 16, 2e-3, np.random.default_rng(0))
+        lens_m = wl.lens[:n_c].contiguous()
+        l10 = sur.predict(lens_m.cpu().numpy())[:, 1] * sur.ysd[1] + sur.ymu[1]
+        ks = np.abs(np.log10(lams)[None, :] - l10[:, None]).argmin(axis=1).astype(np.int32)
+        runs = {}
+        for key, kw in (("cold", {}), ("surrogate_lambda_start", {"lam_start": ks})):
+            o, ms = _timed_call(lambda: ctx.eval_batch([wl.problem], lens_m, wl.prob_idx[:n_c],
+                                                       wl.lambdas[:n_c].contiguous(), wl.n_lam[:n_c], tol=TOL,
+                                                       want_all_x=(key == "cold"), **kw))
+            it = o["iters"].cpu().numpy()
+            runs[key] = {"ms": ms, "evals_per_s": n_c / (ms / 1e3), "cg_iterations": int(it.sum()),
+                         "cg_iterations_max_item": int(it.max()),
+                         "items_converged_frac": float(((o["item_status"].cpu().numpy() & 7) == 0).mean()),
+                         "out": o}
+        cold = runs["cold"].pop("out")
+        warm = runs["surrogate_lambda_start"].pop("out")
+        npix = wl.geom.nx * wl.geom.ny
+        f_it = 4 * 21 * 21 * npix + 16 * npix + 32 * wl.geom.ns
+        for key in runs:
+            runs[key]["tflops"] = runs[key]["cg_iterations"] * f_it / (runs[key]["ms"] / 1e3) / 1e12
+        res.update({"config": "256x256 image 0.02\"/px, 128x128 source +-1.2\", 21x21 PSF sigma 3 px, Laplacian, "
+                              "64 candidates x 32 lambdas 1e-4..1e2, tol 1e-6",
+                    "runs": runs,
+                    "chi2_agree_cold_vs_warm_max_rel": float(np.max(np.abs(warm["chi2"].cpu().numpy() -
+                                                                          cold["chi2"].cpu().numpy()) /
+                                                                   cold["chi2"].cpu().numpy()))})
+        # matrix-free FP64 oracle (dense F does not fit) on 2 candidates x the 2
+        # largest lambdas (the oracle's CGLS needs far fewer iterations there)
+        op = _oracle_problem(wl.problem, wl.geom)
+        X = cold["all_x"].double().cpu().numpy()
+        chi = cold["chi2"].cpu().numpy()
+        ce, se = [], []
+        t0 = time.perf_counter()
+        for c in (0, 1):
+            ops = sparse_operators(op, wl.lens[c].cpu().numpy())
+            for k in (n_l - 2, n_l - 1):
+                s_ref, _, _ = cgls_solve(ops, float(lams[k]), tol=1e-12)
+                c_ref, _ = chi2_reg(ops, s_ref)
+                ce.append(np.array([abs(chi[c, k] - c_ref) / c_ref]))
+                se.append(np.array([np.linalg.norm(X[c, k, :wl.geom.ns] - s_ref) / np.linalg.norm(s_ref)]))
+        res["oracle_sample"] = dict(_summ(ce, se), sample="candidates 0-1 x the two largest lambdas, matrix-free "
+                                                          "FP64 CGLS oracle at tol 1e-12",
+                                    oracle_s=time.perf_counter() - t0)
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    print(json.dumps(res), flush=True)
+    ctx.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -560,7 +829,13 @@ def main():
                     help="candidates of the --profile-case run (x 16 lambdas)")
     ap.add_argument("--profile-forward", action="store_true",
                     help="run only the forward-batch case of the ncu captures (256x256, 1024 sources) and exit")
+    ap.add_argument("--workload", default=None, choices=["uneven1024", "ga128", "large256"],
+                    help="run one of the other stated workloads at full size with a sampled oracle check and "
+                         "print its own JSON line")
+    ap.add_argument("--generations", type=int, default=200, help="generations of --workload ga128")
     args = ap.parse_args()
+    if args.workload:
+        return run_workload(args.workload, args)
     if args.profile_forward:
         return run_profile_forward()
     if args.profile_case is not None:

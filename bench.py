@@ -220,12 +220,13 @@ def run_gpu(args):
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     st = torch.cuda.current_stream()
 
-    from paper_1101_5803_gb300.autotune import tune
-    variant = tune(ctx, probs, wl.lens, wl.prob_idx, wl.lambdas, wl.n_lam, tol=TOL)
+    from paper_1101_5803_gb300.autotune import tune_config
+    tcfg = tune_config(ctx, probs, wl.lens, wl.prob_idx, wl.lambdas, wl.n_lam, tol=TOL)
+    variant = tcfg["variant"]
 
     def step(out=None, graph=True, timing=False):
         return ctx.eval_batch(probs, wl.lens, wl.prob_idx, wl.lambdas, wl.n_lam, tol=TOL, use_graph=graph,
-                              out=out, want_kappa=True, phase_timing=timing, variant=variant)
+                              out=out, want_kappa=True, phase_timing=timing, **tcfg)
 
     # untimed: one phase-timed call for the kernel roofline, then graph warm-up
     out = step(graph=False, timing=True)
@@ -263,12 +264,12 @@ def run_gpu(args):
                          wl.problem.mask.cpu().pin_memory(), wl.problem.psf.cpu().pin_memory())
     hl = wl.lens.cpu().pin_memory()
     hlam = wl.lambdas.cpu().pin_memory()
-    hout = ctx.eval_batch([hp], hl, wl.prob_idx, hlam, wl.n_lam, tol=TOL)
+    hout = ctx.eval_batch([hp], hl, wl.prob_idx, hlam, wl.n_lam, tol=TOL, **tcfg)
     e2e_steps = max(1, min(args.steps, 3))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        hout = ctx.eval_batch([hp], hl, wl.prob_idx, hlam, wl.n_lam, tol=TOL, out=hout)
+        hout = ctx.eval_batch([hp], hl, wl.prob_idx, hlam, wl.n_lam, tol=TOL, out=hout, **tcfg)
     t_e2e = (time.perf_counter() - t0) / e2e_steps
     h2d = sum(t.numel() * t.element_size() for t in (hp.d, hp.sigma, hp.mask, hp.psf, hl, hlam))
     d2h = sum(t.numel() * t.element_size() for t in hout.values())
@@ -280,7 +281,7 @@ def run_gpu(args):
 
     def plain_call(n):
         return ctx.eval_batch(probs, wl.lens[:n].contiguous(), wl.prob_idx[:n], wl.lambdas[:n].contiguous(),
-                              wl.n_lam[:n], tol=TOL, mode=binding.MIRAGE_MODE_PLAIN)
+                              wl.n_lam[:n], tol=TOL, mode=binding.MIRAGE_MODE_PLAIN, **tcfg)
 
     plain_call(2)
     torch.cuda.synchronize()
@@ -517,7 +518,7 @@ def run_gpu(args):
             "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32 (f64 reductions)", "data": "synthetic",
             "config": dict(CONFIG, parallelism=f"replicas{world}" if world > 1 else "single",
-                           kernel_variant=variant),
+                           kernel_variant=variant, tuned=tcfg),
             "e2e": {"value": N_CAND / t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
@@ -671,10 +672,19 @@ def run_workload(name: str, args) -> int:
     if name == "uneven1024":
         # 1024 candidates, each with its own observation: images {48..128}^2 with
         # annular masks, sources {16..48}^2, PSFs {7,11,15}, 8..32 lambdas
+        from paper_1101_5803_gb300.autotune import tune_config
         mw = P.uneven_workload(ctx, 1024, seed=1)
         call = lambda **kw: ctx.eval_batch(mw.problems, mw.lens, mw.prob_idx, mw.lambdas, mw.n_lam, tol=TOL, **kw)
         call()  # warm-up (kernel attributes, scratch)
-        out, ms = _timed_call(lambda: call(want_all_x=True))
+        _, ms_default = _timed_call(call)
+        # the autotuner's configuration for this shape class (probe: the first
+        # 64 candidates' grids), then the timed full batch with it
+        tcfg = tune_config(ctx, mw.problems, mw.lens, mw.prob_idx, mw.lambdas, mw.n_lam, tol=TOL)
+        call(**tcfg)
+        _, ms = _timed_call(lambda: call(**tcfg))
+        out = call(want_all_x=True, **tcfg)  # the same results, with every lambda's source for the oracle check
+        res["autotune"] = {"config": tcfg, "ms_default": ms_default, "ms_tuned": ms,
+                           "gain": ms_default / ms}
         ist = out["item_status"].cpu().numpy()
         valid = np.arange(ist.shape[1])[None, :] < mw.n_lam[:, None]
         res.update({"config": "1024 candidates, images {48,64,96,128}^2 (6.4\"), annular masks 0.3-0.6\" / "
@@ -815,6 +825,29 @@ def run_workload(name: str, args) -> int:
     return 0
 
 
+def run_profile_large() -> int:
+    """The case the ncu captures of the general CGLS kernel at 256x256 run
+    (GLOBAL placement: the work vectors live in an L2-resident slab): 152
+    candidates x lambda = 10 (one item per SM), two evaluations."""
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1101_5803_gb300 import binding
+    from paper_1101_5803_gb300.problems import large_workload
+    ctx = binding.Context(0, binding.MIRAGE_FP32)
+    wl = large_workload(ctx, n_cand=152, n_lam=1, seed=3)
+    lam = torch.full((152, 1), 10.0, dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        out = ctx.eval_batch([wl.problem], wl.lens, wl.prob_idx, lam, wl.n_lam, tol=TOL)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_large": True, "items": 152, "cg_iterations": int(out["iters"].sum().item()),
+                      "iters_max": int(out["iters"].max().item()),
+                      "converged": bool(((out["item_status"] & 7) == 0).all().item())}), flush=True)
+    ctx.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -829,6 +862,8 @@ def main():
                     help="candidates of the --profile-case run (x 16 lambdas)")
     ap.add_argument("--profile-forward", action="store_true",
                     help="run only the forward-batch case of the ncu captures (256x256, 1024 sources) and exit")
+    ap.add_argument("--profile-large", action="store_true",
+                    help="run only the 256x256 case of the ncu captures of the general CGLS kernel and exit")
     ap.add_argument("--workload", default=None, choices=["uneven1024", "ga128", "large256"],
                     help="run one of the other stated workloads at full size with a sampled oracle check and "
                          "print its own JSON line")
@@ -836,6 +871,8 @@ def main():
     args = ap.parse_args()
     if args.workload:
         return run_workload(args.workload, args)
+    if args.profile_large:
+        return run_profile_large()
     if args.profile_forward:
         return run_profile_forward()
     if args.profile_case is not None:

@@ -127,6 +127,19 @@ typedef struct {
                           choice: FFT for PSFs of 23 x 23 and wider, direct below.
                           Forced choices fall back to the general kernel where
                           they do not apply.  Other values: MIRAGE_ERR_ARG. */
+    double inner_eta;  /* FP32 contexts: the relative residual reduction each inner
+                          solve of the refinement aims for (each solve stops at
+                          max(inner_eta, 0.3 tol / current residual)); 0 = the
+                          default 0.03; otherwise 1e-4 <= inner_eta <= 0.5, else
+                          MIRAGE_ERR_ARG.  Changes the iteration path, not the
+                          solution (to tol).  FP64 contexts ignore it. */
+    int place;         /* work-buffer placement of the general kernel: 0 = automatic
+                          (the most on-chip placement that fits), 1 = all in shared
+                          memory, 2 = convolution inputs and source vectors in
+                          shared memory, the rest in an L2-resident slab, 3 = all in
+                          the slab; a placement that does not fit, or a problem on
+                          the FFT path (always 3), keeps the automatic one.  Other
+                          values: MIRAGE_ERR_ARG. */
 } mirage_opts_t;
 
 typedef struct mirage_ctx mirage_ctx_t;

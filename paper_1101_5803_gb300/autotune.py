@@ -1,13 +1,28 @@
-"""Autotuner for the CGLS kernel variant of a shape class.
+"""Autotuner of the CGLS launch configuration of a shape class.
 
-The library offers several implementations of the same item computation
-(mirage_opts_t.variant): the two-CTA-per-SM kernel with PSF taps in shared
-memory (1), as kernel parameters with FFMA (2) or packed FFMA2 (3), and the
-general kernel (4).  All give results within the parity tolerances (1-3
-bitwise identical).  For a shape class (image, source grid, PSF, sub-pixels,
-regulariser, precision, one or several PSFs per launch) the tuner times each
-variant on a short probe batch with CUDA events and caches the fastest in a
-JSON file; later calls read the cache.
+Three choices are tuned, each by timing a short probe batch with CUDA events
+and keeping the fastest of a few runs:
+
+* the kernel variant (mirage_opts_t.variant): the library's automatic
+  choice (0), the two-CTA-per-SM kernel with PSF taps in shared memory (1),
+  as kernel parameters with FFMA (2) or packed FFMA2 (3), and the general
+  kernel (4), timed on the probe
+  candidates at two lambdas from the middle of their grids (items of
+  typical length);
+* the reduction each inner solve of the refinement aims for
+  (mirage_opts_t.inner_eta; FP32 contexts): a smaller target means fewer
+  FP64 residual passes but longer inner solves, timed on the probe
+  candidates' whole lambda grids, since the trade-off moves with lambda;
+* the work-buffer placement of the problems that run on the general kernel
+  (mirage_opts_t.place): all in shared memory, the convolution inputs in
+  shared memory and the rest in an L2-resident slab, or all in the slab.
+
+A choice replaces the default only when it is more than MARGIN faster on the
+probe.  All choices solve the same systems to the same tolerance (variants
+1-3 and the placements bitwise alike).  A shape class is the set of (image, source
+grid, PSF, sub-pixels, regulariser) of the problems, the precision and
+whether a launch mixes PSFs; its choice is cached in a JSON file and later
+calls read the cache.
 """
 from __future__ import annotations
 
@@ -19,7 +34,10 @@ import torch
 
 from .binding import MIRAGE_FP32
 
-VARIANTS = (1, 2, 3, 4)
+VARIANTS = (0, 1, 2, 3, 4)  # 0: the library's automatic choice
+ETAS = (0.03, 0.01, 0.1)     # the first is the default
+PLACES = (1, 2, 3)
+MARGIN = 0.03                # a choice must beat the default by this much to replace it
 
 
 def cache_path() -> str:
@@ -51,36 +69,81 @@ def _save(d):
     os.replace(tmp, p)
 
 
-def tune(ctx, probs, lens, prob_idx, lambdas, n_lam, *, tol=1e-6, n_probe=64, reps=3, retune=False) -> int:
-    """Fastest variant for this shape class (best of ``reps`` timed runs), timed
-    on the first n_probe candidates at two lambdas from the middle of their grids (items of
-    typical length: the largest lambdas converge in a few dozen iterations
-    and would time mostly the fixed per-item work)."""
+def _time(ctx, probs, lens, prob_idx, lam, nl, reps, **kw) -> float:
+    """Fastest of ``reps`` timed calls (after one warm-up), in ms."""
+    ctx.eval_batch(probs, lens, prob_idx, lam, nl, **kw)
+    best = float("inf")
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ctx.eval_batch(probs, lens, prob_idx, lam, nl, **kw)
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    return best
+
+
+def _pick(times: dict, default):
+    """The fastest choice, unless it beats the default by less than MARGIN
+    (timing noise must not move a configuration)."""
+    best = min(times, key=times.get)
+    return best if times[best] < (1.0 - MARGIN) * times[default] else default
+
+
+def tune_config(ctx, probs, lens, prob_idx, lambdas, n_lam, *, tol=1e-6, n_probe=None, reps=3,
+                retune=False) -> dict:
+    """The fastest launch configuration for this shape class, as keyword
+    arguments of ``Context.eval_batch`` (variant, inner_eta, place).  The
+    probe is the first n_probe candidates (default 64, or 256 for classes of
+    several problems, whose items vary more: a probe of a few items per CTA
+    slot times the launch's tail, not its steady state)."""
     key = shape_key(ctx, probs)
     db = _load()
-    if key in db and not retune:
-        return int(db[key]["variant"])
+    if key in db and not retune and "inner_eta" in db[key]:
+        e = db[key]
+        return {"variant": int(e["variant"]), "inner_eta": float(e["inner_eta"]), "place": int(e["place"])}
+    if n_probe is None:
+        n_probe = 256 if len(probs) > 1 else 64
     n = min(n_probe, int(lens.shape[0]))
     m = int(lambdas.shape[1])
+    pl = lens[:n].contiguous()
+    pidx = prob_idx[:n]
+    fp32 = ctx.precision == MIRAGE_FP32
+    base = dict(tol=tol, want_s=False, want_kappa=False)
+    # 1: the kernel variant, at two lambdas from the middle of the grids
     cols = [m // 2, min(m - 1, m // 2 + 1)] if m >= 2 else [0]
-    lam = lambdas[:n, cols].contiguous()
-    nl = np.minimum(np.asarray(n_lam[:n]), lam.shape[1]).astype(np.int32)
-    times = {}
+    lam2 = lambdas[:n, cols].contiguous()
+    nl2 = np.minimum(np.asarray(n_lam[:n]), lam2.shape[1]).astype(np.int32)
+    t_var = {}
     for v in VARIANTS:
-        if v in (1, 2, 3) and ctx.precision != MIRAGE_FP32:
+        if v in (1, 2, 3) and not fp32:
             continue
-        kw = dict(tol=tol, variant=v, want_s=False, want_kappa=False)
-        ctx.eval_batch(probs, lens[:n].contiguous(), prob_idx[:n], lam, nl, **kw)  # warm-up
-        best = float("inf")
-        for _ in range(reps):  # the fastest of a few runs: variants can be within a few percent
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record()
-            ctx.eval_batch(probs, lens[:n].contiguous(), prob_idx[:n], lam, nl, **kw)
-            e1.record()
-            torch.cuda.synchronize()
-            best = min(best, e0.elapsed_time(e1))
-        times[v] = best
-    best = min(times, key=times.get)
-    db[key] = {"variant": int(best), "ms": {str(k): round(t, 4) for k, t in times.items()}}
+        t_var[v] = _time(ctx, probs, pl, pidx, lam2, nl2, reps, variant=v, **base)
+    variant = _pick(t_var, 0)
+    # 2 and 3: on the probe candidates' whole grids
+    lam = lambdas[:n].contiguous()
+    nl = np.asarray(n_lam[:n]).astype(np.int32)
+    t_eta = {}
+    eta = 0.0
+    if fp32:
+        for e in ETAS:
+            t_eta[e] = _time(ctx, probs, pl, pidx, lam, nl, max(1, reps - 1), variant=variant, inner_eta=e, **base)
+        eta = _pick(t_eta, ETAS[0])
+    # (the two-CTA kernel has one layout: the placement only moves the
+    # problems that run on the general kernel)
+    t_place = {}
+    for p in (0,) + PLACES:
+        t_place[p] = _time(ctx, probs, pl, pidx, lam, nl, max(1, reps - 1), variant=variant, inner_eta=eta,
+                           place=p, **base)
+    place = _pick(t_place, 0)
+    db[key] = {"variant": int(variant), "inner_eta": float(eta), "place": int(place),
+               "ms": {"variant": {str(k): round(t, 4) for k, t in t_var.items()},
+                      "inner_eta": {str(k): round(t, 4) for k, t in t_eta.items()},
+                      "place": {str(k): round(t, 4) for k, t in t_place.items()}}}
     _save(db)
-    return int(best)
+    return {"variant": int(variant), "inner_eta": float(eta), "place": int(place)}
+
+
+def tune(ctx, probs, lens, prob_idx, lambdas, n_lam, **kw) -> int:
+    """The tuned kernel variant alone (see tune_config)."""
+    return tune_config(ctx, probs, lens, prob_idx, lambdas, n_lam, **kw)["variant"]

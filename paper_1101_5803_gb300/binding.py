@@ -53,7 +53,8 @@ class mirage_problem_t(ctypes.Structure):
 class mirage_opts_t(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("maxit", ctypes.c_int), ("mode", ctypes.c_int),
                 ("mem", ctypes.c_int), ("use_graph", ctypes.c_int), ("threads", ctypes.c_int),
-                ("replace_every", ctypes.c_int), ("variant", ctypes.c_int)]
+                ("replace_every", ctypes.c_int), ("variant", ctypes.c_int), ("inner_eta", ctypes.c_double),
+                ("place", ctypes.c_int)]
 
 
 _lib = None
@@ -189,7 +190,7 @@ def mirage_last_launch_count(ctx) -> int:
 def mirage_eval_batch(ctx, probs, lens, prob_idx, lambdas, n_lam, *, tol=1e-6, maxit=0,
                       mode=MIRAGE_MODE_BATCHED, use_graph=False, replace_every=0, warm_x=None, lam_start=None,
                       want_s=True, want_all_x=False, want_kappa=True, out=None, stream=None, real=torch.float32,
-                      phase_timing=False, phase_clocks=False, variant=0):
+                      phase_timing=False, phase_clocks=False, variant=0, inner_eta=0.0, place=0):
     """Evaluate candidates; returns a dict of output tensors (see mirage.h).
 
     ``lens`` [n,7] float64 and ``lambdas`` [n,max_lam] float64 are device
@@ -225,7 +226,7 @@ def mirage_eval_batch(ctx, probs, lens, prob_idx, lambdas, n_lam, *, tol=1e-6, m
     arr = (mirage_problem_t * len(probs))(*[p.c_struct() for p in probs])
     opts = mirage_opts_t(float(tol), int(maxit), int(mode), MIRAGE_MEM_HOST if host else MIRAGE_MEM_DEVICE,
                          int(bool(use_graph)), -2 if phase_clocks else (-1 if phase_timing else 0),
-                         int(replace_every), int(variant))
+                         int(replace_every), int(variant), float(inner_eta), int(place))
     rc = lib.mirage_eval_batch(
         ctx, arr, len(probs), _ptr(lens.contiguous()), pidx.ctypes.data_as(ctypes.c_void_p), n,
         _ptr(lambdas.contiguous()), nl.ctypes.data_as(ctypes.c_void_p), max_lam, ctypes.byref(opts),

@@ -669,7 +669,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_cgls_fast(const __grid_constant
         int status = 0, total_it = 0, slow = 0;
         double chi2 = 0, reg2 = 0, g64 = 0, rel64 = 0, prev_rel = 1e300;
         constexpr int MAX_OUTER = 16;
-        const double eta_min = 0.03;
+        const double eta_min = A.eta;
         const int nsv = g.ns, sxv = g.sx, regv = g.reg;
         float* Q = P2;  // L^T corner planes: Q[q * ns + base], q = 00, 10, 01, 11
         // signed offset of the shared zero from Q (both in the one shared

@@ -86,6 +86,7 @@ struct CglsArgs {
     int n_items;
     int* counter;           // queue head
     double tol;
+    double eta;             // FP32 contexts: inner-solve reduction target of the refinement
     int maxit;              // <= 0: 10 * ns
     int replace_every;
     int max_lam, max_ns;
@@ -1653,7 +1654,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_cgls(CglsArgs<T> A) {
         constexpr int MAX_OUTER = 16;
         // inner target: a 30x reduction per FP32 inner solve keeps each inner
         // solve short (FP32 loses orthogonality on long ones) at few FP64 passes
-        const double eta_min = sizeof(T) == 4 ? 0.03 : 0.3 * A.tol;
+        const double eta_min = sizeof(T) == 4 ? A.eta : 0.3 * A.tol;
         bool reverted = false;
         for (int outer = 0;; ++outer) {
             chi2 = residual64<T>(w, g, lam, red, which, reg2, g64, conv_ref);

@@ -11,13 +11,14 @@ chi^2 of its L-curve corner solution (Section 2.6).
 
 With a surrogate, each generation draws ``oversample`` times more
 offspring than it can afford exact solves for, ranks them by the
-surrogate's predicted corner chi^2, evaluates only the best ``pop`` exactly
-(every survivor is judged by the exact solve), and trains the network on
-the new exact results.  The screen ranks, so its quality is judged by the rank
-correlation between predicted and exact corner chi^2 on the latest exact
-results: below ``fallback_rho`` the screen is switched off for the next
-generation (offspring drawn without ranking), and back on when it
-recovers.  Warm-starting the children's CG from their parents' solutions
+surrogate's predicted corner chi^2, evaluates the best ``pop`` exactly
+(every survivor is judged by the exact solve) except for a control set of
+``control * pop`` offspring drawn at random from the rest, and trains the
+network on the new exact results.  The screen ranks, so its quality is
+judged by the rank correlation between predicted and exact corner chi^2 on
+the control set (the screened offspring alone span too narrow a range):
+below ``fallback_rho`` the screen is switched off for the next generation
+(offspring drawn without ranking), and back on when it recovers.  Warm-starting the children's CG from their parents' solutions
 is available but off by default: a parent's source is a poor start for a
 different lens and measured more CG iterations, not fewer.
 
@@ -66,6 +67,7 @@ class GAConfig:
     batch: int = 256
     lr: float = 2e-3
     fallback_rho: float = 0.3
+    control: float = 0.125
     overlap_training: bool = True
     reserved_slots: int = 8
     seed: int = 0
@@ -222,9 +224,18 @@ def run_ga(ctx: Context, wl: Workload, cfg: GAConfig, log=None):
             t0 = time.perf_counter()
             n_draw = cfg.pop * (cfg.oversample if screen else 1)
             kids, par = _offspring(pop, fit, n_draw, cfg, rng)
+            n_ctrl = 0
             if screen:
+                # the pop - n_ctrl best-ranked offspring, plus n_ctrl drawn at
+                # random from the rest: the control set on which the screen's
+                # rank correlation and RMSE are measured without the range
+                # restriction of its own selection
                 pred = predict(kids)[:, 0]
-                keep = np.argsort(pred)[:cfg.pop]
+                order = np.argsort(pred)
+                n_ctrl = int(round(cfg.control * cfg.pop))
+                top = order[:cfg.pop - n_ctrl]
+                ctrl = rng.choice(order[cfg.pop - n_ctrl:], n_ctrl, replace=False)
+                keep = np.concatenate([top, ctrl])
                 kids, par = kids[keep], par[keep]
             warm = X_pop[par].contiguous() if cfg.warm_start else None
             lam_start = None
@@ -242,6 +253,8 @@ def run_ga(ctx: Context, wl: Workload, cfg: GAConfig, log=None):
             was_screened = screen
             if sur is not None:
                 ok = np.isfinite(kfit) & (kfit > 0)
+                if n_ctrl > 2:
+                    ok[:cfg.pop - n_ctrl] = False  # judge the screen on its control set
                 p = predict(kids)
                 y = np.stack([np.log(kfit[ok]), np.log10(klam[ok])], axis=1)
                 rm = float(np.sqrt(np.mean(((y - sur.ymu) / sur.ysd - p[ok]) ** 2)))

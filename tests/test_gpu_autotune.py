@@ -42,3 +42,52 @@ def test_ffma_microbenchmark():
     tf, fc = binding.mirage_measure_ffma(0)
     assert 0.3 * 256 < fc < 1.05 * 256, fc
     assert tf > 0
+
+
+def test_tune_config_caches_and_agrees(tmp_path, monkeypatch):
+    # the tuned (variant, inner target, placement) solves the same systems:
+    # chi2 within the solver tolerance of the default configuration, and
+    # the cached choice is returned on the next call
+    monkeypatch.setenv("MIRAGE_TUNE_CACHE", str(tmp_path / "tune.json"))
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1101_5803_gb300 import autotune, binding
+    from paper_1101_5803_gb300.problems import ga64_workload
+
+    ctx = binding.Context(0, binding.MIRAGE_FP32)
+    wl = ga64_workload(ctx, 16, 6, seed=9)
+    cfg = autotune.tune_config(ctx, [wl.problem], wl.lens, wl.prob_idx, wl.lambdas, wl.n_lam, n_probe=8, reps=1)
+    assert cfg["variant"] in autotune.VARIANTS and cfg["inner_eta"] in autotune.ETAS
+    assert cfg["place"] in (0,) + autotune.PLACES
+    assert autotune.tune_config(ctx, [wl.problem], wl.lens, wl.prob_idx, wl.lambdas, wl.n_lam) == cfg
+    a = ctx.eval_batch([wl.problem], wl.lens, wl.prob_idx, wl.lambdas, wl.n_lam, tol=1e-6, **cfg)
+    b = ctx.eval_batch([wl.problem], wl.lens, wl.prob_idx, wl.lambdas, wl.n_lam, tol=1e-6)
+    assert ((a["item_status"] & 7) == 0).all() and ((b["item_status"] & 7) == 0).all()
+    c1, c2 = a["chi2"].cpu().numpy(), b["chi2"].cpu().numpy()
+    assert np.abs(c1 / c2 - 1).max() < 1e-4
+    ctx.close()
+
+
+def test_general_kernel_placements_agree_bitwise():
+    # the general kernel's work buffers in shared memory, split, or all in
+    # the L2-resident slab: the same arithmetic in the same order
+    import __graft_entry__
+    __graft_entry__.build()
+    import synth
+    from paper_1101_5803_gb300 import binding
+    from paper_1101_5803_gb300.problems import observe_on_device
+
+    ctx = binding.Context(0, binding.MIRAGE_FP32)
+    g = synth.Geometry(48, 48, 6.4 / 48, 16, 16, -0.8, 0.8, -0.8, 0.8, 7, 1, synth.REG_LAPLACIAN)
+    rng = np.random.default_rng(2)
+    prob = observe_on_device(ctx, g, synth.gaussian_psf(7, 7 / 6), synth.drawn_source(rng), synth.TRUE_LENS, rng)
+    lens = torch.as_tensor(synth.lens_population(rng, 6), device="cuda")
+    lams = torch.as_tensor(np.tile(synth.lambda_grid(5), (6, 1)), device="cuda")
+    outs = [ctx.eval_batch([prob], lens, [0] * 6, lams, [5] * 6, tol=1e-6, variant=4, place=p, want_all_x=True)
+            for p in (1, 2, 3)]
+    for o in outs[1:]:
+        for key in ("chi2", "reg", "iters", "all_x"):
+            assert torch.equal(o[key], outs[0][key]), key
+    with pytest.raises(binding.MirageError):
+        ctx.eval_batch([prob], lens, [0] * 6, lams, [5] * 6, place=7)
+    ctx.close()

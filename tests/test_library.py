@@ -33,11 +33,31 @@ def test_binding_loads(lib):
     assert l2.mirage_eval_batch is not None
 
 
-def test_struct_layouts_match_header():
-    # mirage_geom_t: 2 ints, 3 doubles, 2 ints, 4 doubles, 4 ints (natural alignment, no padding)
-    assert ctypes.sizeof(binding.mirage_geom_t) == 88
-    assert ctypes.sizeof(binding.mirage_opts_t) == 40  # double + 8 ints
-    assert ctypes.sizeof(binding.mirage_problem_t) == 88 + 32
+def test_struct_layouts_match_header(tmp_path):
+    # the binding's ctypes structures against the header as a C compiler lays
+    # it out: every struct's size and every field's offset
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = [binding.mirage_geom_t, binding.mirage_opts_t, binding.mirage_problem_t]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "mirage.h"', "int main(void) {"]
+    for st in structs:
+        lines.append(f'  printf("%zu\\n", sizeof({st.__name__}));')
+        for f in st._fields_:
+            lines.append(f'  printf("%zu\\n", offsetof({st.__name__}, {f[0]}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.dirname(binding.HEADER), str(src), "-o", str(exe)], check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
+    want = []
+    for st in structs:
+        want.append(ctypes.sizeof(st))
+        want += [getattr(st, f[0]).offset for f in st._fields_]
+    assert got == want
 
 
 def test_header_constants_match_binding():

@@ -130,7 +130,7 @@ typedef struct {
     double inner_eta;  /* FP32 contexts: the relative residual reduction each inner
                           solve of the refinement aims for (each solve stops at
                           max(inner_eta, 0.3 tol / current residual)); 0 = the
-                          default 0.03; otherwise 1e-4 <= inner_eta <= 0.5, else
+                          default 0.01; otherwise 1e-4 <= inner_eta <= 0.5, else
                           MIRAGE_ERR_ARG.  Changes the iteration path, not the
                           solution (to tol).  FP64 contexts ignore it. */
     int place;         /* work-buffer placement of the general kernel: 0 = automatic

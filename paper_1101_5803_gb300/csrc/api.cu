@@ -859,7 +859,7 @@ int eval_impl(mirage_ctx* ctx, const mirage_problem_t* probs, int n_probs, const
     A.lens = d_lens;
     A.lambdas = d_lambdas;
     A.tol = o.tol;
-    A.eta = o.inner_eta > 0.0 ? o.inner_eta : 0.03;
+    A.eta = o.inner_eta > 0.0 ? o.inner_eta : 0.01;
     A.maxit = o.maxit;
     A.replace_every = o.replace_every;
     A.max_lam = max_lam;

@@ -446,7 +446,10 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_cgls_fast(const __grid_constant
         const bool own = tid < g.ntiles;
         const int ty = own ? tid / g.tiles_x : 0, tx = own ? tid - (tid / g.tiles_x) * g.tiles_x : 0;
         const int pp0 = (ty * TILE + g.hk) * g.Wp + tx * TILE + g.xoff;
-        const float* P1t = P1 + (ty * TILE) * g.Wp + tx * TILE;
+        // the tile holding this tile's pixels in the reversed image (L p is
+        // stored reversed: pixel (Y, X) at (ny-1-Y, nx-1-X))
+        const float* P1r = P1 + ((g.ntiles / g.tiles_x - 1 - ty) * TILE) * g.Wp + (g.tiles_x - 1 - tx) * TILE;
+        const int crev = (P.ny - 1 + 2 * g.hk) * g.Wp + P.nx - 1 + 2 * g.xoff;  // ppos -> reversed ppos
         const float* P2t = P2 + (ty * TILE) * g.Wp + tx * TILE;
         float sw[16];
         unsigned mbits = 0;
@@ -747,7 +750,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_cgls_fast(const __grid_constant
             }
             const int stag_window = max(4000, 2 * nsv);
             while (!stop) {
-                // P1 <- L p at the mapped pixels, four rays at a time (all
+                // P1 <- L p at the mapped pixels, reversed, four rays at a time (all
                 // loads first, so their latencies overlap); q_reg = sqrt(lam) H p
                 for (int e = tid; e < nent; e += 4 * bs) {
                     unsigned id[4];
@@ -767,7 +770,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_cgls_fast(const __grid_constant
                     }
 #pragma unroll
                     for (int j = 0; j < 4; ++j)
-                        if (e + j * bs < nent) P1[id[j] & 0xffffu] = val[j];
+                        if (e + j * bs < nent) P1[crev - (int)(id[j] & 0xffffu)] = val[j];
                 }
                 // H p of the owned source pixels into hbuf, and lam ||H p||^2
                 float dh = 0.f;
@@ -783,67 +786,80 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_cgls_fast(const __grid_constant
                 __syncthreads();
                 PHASE(0);
                 // q = B P1 on the owned tile: delta += ||sqrt(W) q||^2, P2 <- W q
+                // B and B^T run one copy of the convolution code (one unrolled
+                // K x K tile loop in the instruction cache instead of two).  L p
+                // is stored reversed; B L p at a pixel is the PSF correlation of
+                // the reversed image at the reversed pixel, so it is read from
+                // the reversed tile in reversed order.  B^T is the PSF
+                // correlation itself
                 float dl_part = lamf * dh;
-                if (own) {
+                float a = 0.f;
+#pragma unroll 1
+                for (int dir = 0; dir < 2; ++dir) {
                     float o16[16];
-                    conv_tile_fast<K, MODE>(P1t, g.Wp, taps2, FA.ptap[0], o16);
+                    if (own) conv_tile_fast<K, MODE>(dir == 0 ? P1r : P2t, g.Wp, taps2 + K * K, FA.ptap[1], o16);
+                    if (dir == 0) {
+                        // q = sqrt(W) B L p on the owned tile: delta += ||q||^2, P2 <- W B L p
+                        if (own) {
 #pragma unroll
-                    for (int r = 0; r < TILE; ++r) {
-                        V4<float> o;
+                            for (int r = 0; r < TILE; ++r) {
+                                V4<float> o;
 #pragma unroll
-                        for (int cc = 0; cc < 4; ++cc) {
-                            const float t = sw[r * 4 + cc] * o16[r * 4 + cc];
-                            dl_part = fmaf(t, t, dl_part);
-                            o.v[cc] = sw[r * 4 + cc] * t;
+                                for (int cc = 0; cc < 4; ++cc) {
+                                    const float t = sw[r * 4 + cc] * o16[(TILE - 1 - r) * 4 + (3 - cc)];
+                                    dl_part = fmaf(t, t, dl_part);
+                                    o.v[cc] = sw[r * 4 + cc] * t;
+                                }
+                                st4(P2 + pp0 + r * g.Wp, o);
+                            }
                         }
-                        st4(P2 + pp0 + r * g.Wp, o);
-                    }
-                }
-                // the previous L^T planes overwrote part of P2's zero frame
-                {
-                    const int nfz = fi->nfz, top = fi->top;
-                    for (int f = tid; f < nfz; f += bs) {
-                        int q4 = f;
-                        if (f >= top) {
-                            const int f2 = f - top, mfr = fi->mfr, xl = fi->xl;
-                            const int r = (int)(((float)f2 + 0.5f) * fi->inv_mfr);
-                            const int j = f2 - r * mfr;
-                            q4 = (g.hk + r) * fi->W4 + (j < xl ? j : j + g.tiles_x);
+                    // the previous L^T planes overwrote part of P2's zero frame
+                    {
+                        const int nfz = fi->nfz, top = fi->top;
+                        for (int f = tid; f < nfz; f += bs) {
+                            int q4 = f;
+                            if (f >= top) {
+                                const int f2 = f - top, mfr = fi->mfr, xl = fi->xl;
+                                const int r = (int)(((float)f2 + 0.5f) * fi->inv_mfr);
+                                const int j = f2 - r * mfr;
+                                q4 = (g.hk + r) * fi->W4 + (j < xl ? j : j + g.tiles_x);
+                            }
+                            reinterpret_cast<float4*>(P2)[q4] = make_float4(0.f, 0.f, 0.f, 0.f);
                         }
-                        reinterpret_cast<float4*>(P2)[q4] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    }
+                    // H^T (H p) of the owned source pixels (neighbours' H p from hbuf)
+    #pragma unroll
+                    for (int kk = 0; kk < NSP; ++kk) {
+                        const int i = tid + kk * bs;
+                        hth[kk] = i < nsv ? hrow_fast(hbuf, i, msk >> (16 + 4 * kk), sxv, regv) : 0.f;
+                    }
+                        PHASE(1);
+                        // delta = p^T A p; the reduction's barrier also completes P2
+                        const float2 dl = block_pair_tree(dl_part, pbuf, half);
+                        half ^= 1;
+                        const float delta = dl.x + dl.y;
+                        PHASE(2);
+                        if (!(delta > 0.f) || !isfinite(delta)) {
+                            brk = 1;
+                            break;
+                        }
+                        a = gam / delta;
+                    } else {
+                        // u = B^T P2 on the owned tile, stored into P1 at mapped pixels
+                        if (own) {
+#pragma unroll
+                            for (int r = 0; r < TILE; ++r) {
+                                float* dst = P1 + pp0 + r * g.Wp;
+#pragma unroll
+                                for (int cc = 0; cc < 4; ++cc)
+                                    if (mbits & (1u << (r * 4 + cc))) dst[cc] = o16[r * 4 + cc];
+                            }
+                        }
+                        __syncthreads();  // u complete
+                        PHASE(4);
                     }
                 }
-                // H^T (H p) of the owned source pixels (neighbours' H p from hbuf)
-#pragma unroll
-                for (int kk = 0; kk < NSP; ++kk) {
-                    const int i = tid + kk * bs;
-                    hth[kk] = i < nsv ? hrow_fast(hbuf, i, msk >> (16 + 4 * kk), sxv, regv) : 0.f;
-                }
-                PHASE(1);
-                // delta = p^T A p; the reduction's barrier also completes P2
-                const float2 dl = block_pair_tree(dl_part, pbuf, half);
-                half ^= 1;
-                const float delta = dl.x + dl.y;
-                PHASE(2);
-                if (!(delta > 0.f) || !isfinite(delta)) {
-                    brk = 1;
-                    break;
-                }
-                const float a = gam / delta;
-                // u = B^T P2 on the owned tile, stored into P1 at mapped pixels
-                if (own) {
-                    float o16[16];
-                    conv_tile_fast<K, MODE>(P2t, g.Wp, taps2 + K * K, FA.ptap[1], o16);
-#pragma unroll
-                    for (int r = 0; r < TILE; ++r) {
-                        float* dst = P1 + pp0 + r * g.Wp;
-#pragma unroll
-                        for (int cc = 0; cc < 4; ++cc)
-                            if (mbits & (1u << (r * 4 + cc))) dst[cc] = o16[r * 4 + cc];
-                    }
-                }
-                __syncthreads();  // u complete
-                PHASE(4);
+                if (brk) break;
                 // L^T u: each lane walks its run of consecutive rays (sorted by
                 // cell) and sums, per cell, the four corner weights times u; a
                 // cell's total goes to the planes (indexed by the cell's base
@@ -930,6 +946,12 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_cgls_fast(const __grid_constant
                 }
                 __syncthreads();
                 PHASE(5);
+                // u has been read: clear the owned tile of P1 (the reversed L p
+                // of the next iteration writes only mapped pixels)
+                if (own) {
+#pragma unroll
+                    for (int r = 0; r < TILE; ++r) st4(P1 + pp0 + r * g.Wp, V4<float>{{0.f, 0.f, 0.f, 0.f}});
+                }
                 // pass 3: per source pixel, (A p)_i = the fixed-order sum of the
                 // corners it receives from its (up to) four occupied cells plus
                 // lam (H^T H p)_i; then the CG updates of x, g and z = M^-1 g
@@ -1024,8 +1046,11 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_cgls_fast(const __grid_constant
 // one image tile per thread, 16-bit ray/pixel/cell indices, and room for the
 // four L^T corner planes (4 ns floats) in P2 above its last interior row
 __host__ inline size_t fast_smem_bytes(const Prob<float>& P) {
+    // (image sides in whole tiles: L p is stored reversed, and the reversed
+    // image must fall on the same tile grid)
     if (P.Np != 1 || P.ntiles > NTHREADS || P.plen >= 65536 || P.nrays >= 65536 || P.ns > 4 * NTHREADS ||
-        P.nreg != P.ns || 4 * P.ncells > P.plen || 4 * P.ns > (P.hk + TILE * P.tiles_y) * P.Wp)
+        P.nreg != P.ns || 4 * P.ncells > P.plen || 4 * P.ns > (P.hk + TILE * P.tiles_y) * P.Wp ||
+        P.nx % TILE != 0 || P.ny % TILE != 0)
         return 0;
     size_t o = FAST_HDR;
     o += align_up<float>(sizeof(float2) * 2 * P.K * P.K, 16);

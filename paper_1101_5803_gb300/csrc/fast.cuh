@@ -868,7 +868,11 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_cgls_fast(const __grid_constant
                 // one is used, and the sums are stored at the last ray of each
                 // cell run (known from the next ray's cell)
                 if (e0 < e1) {
+                    // the ray index is loaded two rays ahead, so that the next
+                    // ray's u load does not wait on an index loaded in the same
+                    // iteration
                     unsigned id = eidx[e0];
+                    unsigned idn = eidx[min(e0 + 1, e1 - 1)];
                     unsigned cur = id >> 16;
                     float* dst = (wflags & 1) ? Sq + tid : Q + cur;
                     int ps = (wflags & 1) ? bs : nsv;
@@ -877,7 +881,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_cgls_fast(const __grid_constant
                     float c00 = 0.f, c10 = 0.f, c01 = 0.f, c11 = 0.f;
                     for (int e = e0; e < e1; ++e) {
                         const int en = min(e + 1, e1 - 1);
-                        const unsigned idn = eidx[en];
+                        const unsigned idnn = eidx[min(e + 2, e1 - 1)];
                         const float2 uvn = euv[en];
                         const float Un = P1[idn & 0xffffu];
                         const unsigned key = id >> 16;
@@ -899,6 +903,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_cgls_fast(const __grid_constant
                             dst[3 * ps] = c11;
                         }
                         id = idn;
+                        idn = idnn;
                         uv = uvn;
                         U = Un;
                     }

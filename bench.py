@@ -381,6 +381,26 @@ def run_gpu(args):
 
     tight_res = _guarded("tight_tolerance", _tight_section)
 
+    def _tf32_section():
+        # the inner solves' convolutions at TF32 precision (variant 7: both
+        # factors of every product rounded to 10-bit mantissas, FP32 sums):
+        # what a single-pass TF32 tensor-core B/B^T would cost in CG
+        # iterations inside the exact FP64 refinement
+        res = {"note": "FFMA kernel with TF32-rounded factors (a precision experiment, not a tensor-core kernel)"}
+        for name, var in (("fp32", variant), ("tf32_factors", 7)):
+            o = ctx.eval_batch(probs, wl.lens, wl.prob_idx, wl.lambdas, wl.n_lam, tol=TOL, variant=var)
+            o, ms = _timed_call(lambda: ctx.eval_batch(probs, wl.lens, wl.prob_idx, wl.lambdas, wl.n_lam,
+                                                       tol=TOL, variant=var))
+            it = o["iters"].float()
+            res[name] = {"ms": ms, "cg_iters_mean_per_item": float(it.mean().item()),
+                         "cg_iters_max": int(it.max().item()),
+                         "items_flagged": int(((o["item_status"] & 7) != 0).sum().item()),
+                         "relres_max": float(o["relres"].max().item())}
+        res["iteration_ratio"] = res["tf32_factors"]["cg_iters_mean_per_item"] / res["fp32"]["cg_iters_mean_per_item"]
+        return res
+
+    tf32_res = _guarded("tf32_precision", _tf32_section)
+
     def _iter_section():
         # the paper's own fitness: 40 CGLS iterations per candidate, L-curve over
         # the iterations, Monte Carlo degrees of freedom (FP64 arithmetic)
@@ -549,6 +569,7 @@ def run_gpu(args):
                             f"offspring"}),
             "accuracy": acc_res,
             "tight_tolerance": tight_res,
+            "tf32_precision": tf32_res,
             "ga_surrogate": ga_res,
             "pso": pso_res,
             "iter_lcurve": iter_res,

@@ -123,7 +123,12 @@ typedef struct {
                           parameters (FFMA); 3 = the same with packed FFMA2; 4 = the
                           general one-CTA kernel; 5 = the general kernel with every
                           convolution by FFT (Section 2.2); 6 = the general kernel
-                          with direct convolution at any PSF width.  Automatic
+                          with direct convolution at any PSF width; 7 = the
+                          two-CTA kernel with the inner solves' convolution
+                          factors rounded to TF32 (the arithmetic of a TF32
+                          tensor-core B/B^T; 9x9 PSFs, one PSF per call; an
+                          experiment on the inner solves' precision, the
+                          refinement's residual stays exact).  Automatic
                           choice: FFT for PSFs of 23 x 23 and wider, direct below.
                           Forced choices fall back to the general kernel where
                           they do not apply.  Other values: MIRAGE_ERR_ARG. */

@@ -140,6 +140,19 @@ static long long cgls_slots(const mirage_ctx* ctx, int per_sm) {
     return std::max<long long>(1, (long long)per_sm * ctx->sm_count - ctx->reserved);
 }
 
+// a PSF tap as the fast kernel's parameter: as is, or rounded to TF32
+// (nearest, ties away from zero: the cvt.rna.tf32 rule) for the TF32
+// precision variant
+static float tap_value(float t, bool tf32) {
+    if (!tf32) return t;
+    unsigned u;
+    std::memcpy(&u, &t, sizeof(u));
+    if ((u & 0x7f800000u) != 0x7f800000u) u = (u + 0x1000u) & ~0x1fffu;
+    float r;
+    std::memcpy(&r, &u, sizeof(r));
+    return r;
+}
+
 // relative CG iteration count of lambda index k of an n-point ascending
 // grid: measured counts scale like lambda^-0.37, and the grids span about six
 // decades log-spaced, so the count grows by 10^(2.2 / (n - 1)) per step
@@ -462,7 +475,7 @@ int eval_impl(mirage_ctx* ctx, const mirage_problem_t* probs, int n_probs, const
         return MIRAGE_ERR_ARG;
     }
     const mirage_opts_t o = *opts;
-    if (!(o.tol >= 0) || o.mode < 0 || o.mode > 1 || o.mem < 0 || o.mem > 1 || o.variant < 0 || o.variant > 6 ||
+    if (!(o.tol >= 0) || o.mode < 0 || o.mode > 1 || o.mem < 0 || o.mem > 1 || o.variant < 0 || o.variant > 7 ||
         !(o.inner_eta == 0.0 || (o.inner_eta >= 1e-4 && o.inner_eta <= 0.5)) || o.place < 0 || o.place > 3) {
         set_error("eval_batch: bad options");
         return MIRAGE_ERR_ARG;
@@ -623,6 +636,7 @@ int eval_impl(mirage_ctx* ctx, const mirage_problem_t* probs, int n_probs, const
         if (want == 1) m = 0;
         if (want == 2) m = 1;
         if (want == 3) m = 2;
+        if (want == 7) m = 3;
         if (m > 0 && (n_used > 1 || P.K * P.K > MAX_PTAP)) m = 0;
         const void* f = pick_fast<T>(ctx, P, m);
         if (!f && m == 1 && want == 0) {  // FFMA parameter taps are compiled for K = 9 only
@@ -772,8 +786,8 @@ int eval_impl(mirage_ctx* ctx, const mirage_problem_t* probs, int n_probs, const
         tp.assign(2 * MAX_PTAP, 0.f);
         for (int a = 0; a < K; ++a)
             for (int b = 0; b < K; ++b) {
-                tp[a * K + b] = (float)psf[(K - 1 - a) * K + (K - 1 - b)];
-                tp[MAX_PTAP + a * K + b] = (float)psf[a * K + b];
+                tp[a * K + b] = tap_value((float)psf[(K - 1 - a) * K + (K - 1 - b)], o.variant == 7);
+                tp[MAX_PTAP + a * K + b] = tap_value((float)psf[a * K + b], o.variant == 7);
             }
     }
     // per-CTA global slab (bytes): FP64 refinement buffers, plus all work
@@ -1013,8 +1027,9 @@ int eval_impl(mirage_ctx* ctx, const mirage_problem_t* probs, int n_probs, const
                         CK(cudaMemcpy(psf.data(), P.psf, sizeof(T) * P.K * P.K, cudaMemcpyDefault));
                         for (int a = 0; a < P.K; ++a)
                             for (int b = 0; b < P.K; ++b) {
-                                fa.ptap[0][a * P.K + b] = (float)psf[(P.K - 1 - a) * P.K + (P.K - 1 - b)];
-                                fa.ptap[1][a * P.K + b] = (float)psf[a * P.K + b];
+                                fa.ptap[0][a * P.K + b] =
+                                    tap_value((float)psf[(P.K - 1 - a) * P.K + (P.K - 1 - b)], pmode == 3);
+                                fa.ptap[1][a * P.K + b] = tap_value((float)psf[a * P.K + b], pmode == 3);
                             }
                     }
                     void* a2[] = {&fa};

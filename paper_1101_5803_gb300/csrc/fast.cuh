@@ -73,8 +73,19 @@ struct FastArgs {
     float ptap[2][MAX_PTAP];  // [0] flipped PSF (B), [1] PSF (B^T), row-major K x K
 };
 
-// tap source of the fast convolution
-enum : int { TAPS_SMEM_X2 = 0, TAPS_PARAM = 1, TAPS_PARAM_X2 = 2 };
+// tap source of the fast convolution; TAPS_PARAM_TF32 is TAPS_PARAM with
+// both factors of every product rounded to TF32 (10-bit mantissa, the taps
+// on the host, the image values here) and FP32 accumulation: the arithmetic
+// of a TF32 tensor-core convolution, to measure its effect on the inner
+// solves (the refinement's residual stays exact)
+enum : int { TAPS_SMEM_X2 = 0, TAPS_PARAM = 1, TAPS_PARAM_X2 = 2, TAPS_PARAM_TF32 = 3 };
+
+// round to TF32 (nearest, ties away from zero), returned as a float
+__device__ __forceinline__ float tf32_round(float x) {
+    unsigned r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
 
 template <int K, int MODE>
 __device__ __forceinline__ void conv_tile_fast(const float* __restrict__ Pb, int Wp, const float2* __restrict__ taps2,
@@ -108,6 +119,10 @@ __device__ __forceinline__ void conv_tile_fast(const float* __restrict__ Pb, int
             float in[NVW];
 #pragma unroll
             for (int v = 0; v < NVW; v += 4) lds_vec(src_a + (unsigned)((i * Wp + v) * sizeof(float)), in + v);
+            if constexpr (MODE == TAPS_PARAM_TF32) {
+#pragma unroll
+                for (int v = 0; v < NVW; ++v) in[v] = tf32_round(in[v]);
+            }
 #pragma unroll
             for (int b = 0; b < K; ++b) {
                 const int o = b + SHF;
@@ -116,7 +131,7 @@ __device__ __forceinline__ void conv_tile_fast(const float* __restrict__ Pb, int
                     const int a = i - r;
                     if (a >= 0 && a < K) {
                         const float t = pt[a * K + b];
-                        if constexpr (MODE == TAPS_PARAM) {
+                        if constexpr (MODE == TAPS_PARAM || MODE == TAPS_PARAM_TF32) {
 #pragma unroll
                             for (int c = 0; c < TILE; ++c) acc[r][c] = fmaf(t, in[o + c], acc[r][c]);
                         } else {
@@ -130,7 +145,7 @@ __device__ __forceinline__ void conv_tile_fast(const float* __restrict__ Pb, int
         }
 #pragma unroll
         for (int r = 0; r < TILE; ++r) {
-            if constexpr (MODE == TAPS_PARAM) {
+            if constexpr (MODE == TAPS_PARAM || MODE == TAPS_PARAM_TF32) {
 #pragma unroll
                 for (int c = 0; c < TILE; ++c) out[r * 4 + c] = acc[r][c];
             } else {

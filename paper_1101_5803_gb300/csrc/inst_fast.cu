@@ -13,6 +13,7 @@ void fill_fast(KernelTable& t) {
     t.fast[11][0][0] = (const void*)k_cgls_fast<11, 4, TAPS_SMEM_X2>;
     t.fast[9][0][1] = (const void*)k_cgls_fast<9, 4, TAPS_PARAM>;
     t.fast[9][0][2] = (const void*)k_cgls_fast<9, 4, TAPS_PARAM_X2>;
+    t.fast[9][0][3] = (const void*)k_cgls_fast<9, 4, TAPS_PARAM_TF32>;
     t.fast[5][0][2] = (const void*)k_cgls_fast<5, 4, TAPS_PARAM_X2>;
     t.fast[7][0][2] = (const void*)k_cgls_fast<7, 4, TAPS_PARAM_X2>;
     t.fast[11][0][2] = (const void*)k_cgls_fast<11, 4, TAPS_PARAM_X2>;

@@ -18,8 +18,9 @@ struct KernelTable {
     const void* rt_sortcells[2];
     const void* finalize[2];
     // fast[K][v][mode]: two-CTA-per-SM FP32 kernel, v = 0 for ns <= 1024,
-    // 1 for ns <= 2304; mode = tap source (0 shared, 1 params FFMA, 2 params FFMA2)
-    const void* fast[MAX_K][2][3];
+    // 1 for ns <= 2304; mode = tap source (0 shared, 1 params FFMA, 2 params
+    // FFMA2, 3 params FFMA with TF32-rounded factors)
+    const void* fast[MAX_K][2][4];
     // iter[prec][K]: fixed-iteration CGLS with the iteration L-curve
     const void* iter[2][MAX_K];
     // fwdb[K]: banded FP32 forward batch (one ray per pixel)

@@ -1,6 +1,7 @@
 // Surrogate network: a multilayer perceptron with SiLU hidden layers and a
 // linear output layer, trained with mean-squared error and Adam.  Matrix
-// products run on BF16 tensor cores (mma.sync m16n8k16, FP32 accumulate);
+// products run on the BF16 tcgen05 tensor cores (FP32 accumulate in tensor
+// memory);
 // master weights, Adam moments, bias, activation and loss stay in FP32.
 //
 // It predicts, from the encoded lens vector, the standardised
@@ -15,6 +16,7 @@
 #include <vector>
 
 #include "../../include/mirage.h"
+#include "tc05.cuh"
 
 namespace {
 
@@ -31,44 +33,105 @@ int mlp_fail(int code, const std::string& msg) {
         if (e_ != cudaSuccess) return mlp_fail(MIRAGE_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
     } while (0)
 
-__device__ __forceinline__ unsigned pack_bf16(__nv_bfloat16 lo, __nv_bfloat16 hi) {
-    return (unsigned)__bfloat16_as_ushort(lo) | ((unsigned)__bfloat16_as_ushort(hi) << 16);
-}
-
 // C[M x N] (FP32, row-major, ldc) = sum_k A(m, k) B(k, n) with
 //   A(m, k) = A[m * sam + k * sak],  B(k, n) = B[k * sbk + n * sbn]  (BF16)
-// One warp per 16 x 8 output tile, K in steps of 16; edges are zero-filled.
-__global__ void k_gemm_bf16(const __nv_bfloat16* __restrict__ A, long sam, long sak, const __nv_bfloat16* __restrict__ B,
-                            long sbk, long sbn, float* __restrict__ C, int ldc, int M, int N, int K) {
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    const int tiles_n = (N + 7) / 8;
-    const int tm = warp / tiles_n, tn = warp - (warp / tiles_n) * tiles_n;
-    if (tm * 16 >= M) return;
-    const int g = lane >> 2, t = lane & 3;
-    const int m0 = tm * 16, n0 = tn * 8;
+// on the fifth-generation tensor cores: one CTA of four warps per 128 x BN
+// output tile, accumulator in tensor memory (BN FP32 columns), K in chunks
+// of 64 staged by the CTA into shared memory as K-major core matrices
+// (8 rows x 8 BF16), four tcgen05.mma of K = 16 per chunk issued by one
+// thread, completion through an mbarrier.  Edges are zero-filled.  Should a
+// completion wait run out (about a second), the tile is written as NaN.
+constexpr int TC_BM = 128, TC_BK = 64;
+
+template <int BN>
+constexpr int tc_smem_bytes() {
+    return (TC_BM + BN) * TC_BK * 2 + 16;
+}
+
+__device__ __forceinline__ void tc_stage(__nv_bfloat16* dst, int rows, const __nv_bfloat16* __restrict__ src,
+                                         long s_row, long s_k, int r0, int R, int k0, int K) {
+    // element (r, k) of the tile -> core matrix (r / 8, k / 8), k-chunks
+    // innermost: byte ((r / 8) * 8 + k / 8) * 128 + (r % 8) * 16 + (k % 8) * 2
     const __nv_bfloat16 z = __float2bfloat16(0.f);
-    auto a_at = [&](int m, int k) { return (m < M && k < K) ? A[m * sam + k * sak] : z; };
-    auto b_at = [&](int k, int n) { return (k < K && n < N) ? B[k * sbk + n * sbn] : z; };
-    float c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f;
-    for (int k0 = 0; k0 < K; k0 += 16) {
-        const unsigned a0 = pack_bf16(a_at(m0 + g, k0 + 2 * t), a_at(m0 + g, k0 + 2 * t + 1));
-        const unsigned a1 = pack_bf16(a_at(m0 + g + 8, k0 + 2 * t), a_at(m0 + g + 8, k0 + 2 * t + 1));
-        const unsigned a2 = pack_bf16(a_at(m0 + g, k0 + 2 * t + 8), a_at(m0 + g, k0 + 2 * t + 9));
-        const unsigned a3 = pack_bf16(a_at(m0 + g + 8, k0 + 2 * t + 8), a_at(m0 + g + 8, k0 + 2 * t + 9));
-        const unsigned b0 = pack_bf16(b_at(k0 + 2 * t, n0 + g), b_at(k0 + 2 * t + 1, n0 + g));
-        const unsigned b1 = pack_bf16(b_at(k0 + 2 * t + 8, n0 + g), b_at(k0 + 2 * t + 9, n0 + g));
-        asm volatile(
-            "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-            "{%0,%1,%2,%3};"
-            : "+f"(c0), "+f"(c1), "+f"(c2), "+f"(c3)
-            : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+    const int n = rows * TC_BK;
+    if (s_k == 1) {  // consecutive threads along k
+        for (int e = threadIdx.x; e < n; e += blockDim.x) {
+            const int r = e / TC_BK, k = e - r * TC_BK;
+            const int gr = r0 + r, gk = k0 + k;
+            dst[((r >> 3) * 8 + (k >> 3)) * 64 + (r & 7) * 8 + (k & 7)] =
+                (gr < R && gk < K) ? src[(long)gr * s_row + gk] : z;
+        }
+    } else {  // consecutive threads along the rows
+        for (int e = threadIdx.x; e < n; e += blockDim.x) {
+            const int k = e / rows, r = e - k * rows;
+            const int gr = r0 + r, gk = k0 + k;
+            dst[((r >> 3) * 8 + (k >> 3)) * 64 + (r & 7) * 8 + (k & 7)] =
+                (gr < R && gk < K) ? src[(long)gr * s_row + (long)gk * s_k] : z;
+        }
     }
-    const int r0 = m0 + g, r1 = m0 + g + 8, cA = n0 + 2 * t, cB = n0 + 2 * t + 1;
-    if (r0 < M && cA < N) C[(long)r0 * ldc + cA] = c0;
-    if (r0 < M && cB < N) C[(long)r0 * ldc + cB] = c1;
-    if (r1 < M && cA < N) C[(long)r1 * ldc + cA] = c2;
-    if (r1 < M && cB < N) C[(long)r1 * ldc + cB] = c3;
+}
+
+template <int BN>
+__global__ void __launch_bounds__(128) k_gemm_tc(const __nv_bfloat16* __restrict__ A, long sam, long sak,
+                                                 const __nv_bfloat16* __restrict__ B, long sbk, long sbn,
+                                                 float* __restrict__ C, int ldc, int M, int N, int K) {
+    using namespace mirage::tc05;
+    constexpr int TCOLS = BN < 32 ? 32 : BN;  // a power of two >= 32
+    constexpr uint32_t ID = idesc(FMT_BF16, TC_BM, BN);
+    extern __shared__ __align__(128) unsigned char tc_sm[];
+    __nv_bfloat16* sA = reinterpret_cast<__nv_bfloat16*>(tc_sm);
+    __nv_bfloat16* sB = sA + TC_BM * TC_BK;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(sB + BN * TC_BK);
+    uint32_t* slot = reinterpret_cast<uint32_t*>(bar + 1);
+    const int m0 = blockIdx.x * TC_BM, n0 = blockIdx.y * BN;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp == 0) tmem_alloc(slot, TCOLS);
+    if (threadIdx.x == 0) bar_init(bar, 1);
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tmem = *slot;
+    bool ok = true;
+    uint32_t phase = 0;
+    for (int k0 = 0; k0 < K && ok; k0 += TC_BK) {
+        tc_stage(sA, TC_BM, A, sam, sak, m0, M, k0, K);
+        // B(k, n) as rows n: row stride sbn, k stride sbk
+        tc_stage(sB, BN, B, sbn, sbk, n0, N, k0, K);
+        fence_async_smem();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            fence_after_sync();
+#pragma unroll
+            for (int s = 0; s < TC_BK / 16; ++s) {
+                // K step s: core-matrix columns 2s and 2s + 1 (128 B apart),
+                // 8-row groups 8 * 128 B apart
+                const uint64_t da = sdesc(saddr(sA) + s * 256, 128, 1024);
+                const uint64_t db = sdesc(saddr(sB) + s * 256, 128, 1024);
+                mma_bf16(tmem, da, db, ID, (k0 > 0 || s > 0) ? 1u : 0u);
+            }
+            commit(bar);
+        }
+        ok = __syncthreads_and(bar_wait(bar, phase)) != 0;  // one decision for the whole CTA
+        phase ^= 1;
+        fence_after_sync();
+    }
+    if (!ok) bar_wait(bar, phase ^ 1);  // (bounded) for the MMAs still in flight
+    const int row = m0 + warp * 32 + lane;
+#pragma unroll 1
+    for (int c0 = 0; c0 < BN; c0 += 16) {
+        float v[16];
+        ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+        if (row < M) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int col = n0 + c0 + j;
+                if (col < N) C[(long)row * ldc + col] = (ok && K > 0) ? v[j] : (K > 0 ? __int_as_float(0x7fc00000) : 0.f);
+            }
+        }
+    }
+    fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tmem_free(tmem, TCOLS);
 }
 
 __device__ __forceinline__ float silu_f(float z) { return z / (1.f + __expf(-z)); }
@@ -264,12 +327,33 @@ int ensure_batch(mirage_mlp* m, int n) {
     return MIRAGE_OK;
 }
 
-int gemm(const __nv_bfloat16* A, long sam, long sak, const __nv_bfloat16* B, long sbk, long sbn, float* C, int ldc,
-         int M, int N, int K, cudaStream_t st) {
-    const long warps = (long)((M + 15) / 16) * ((N + 7) / 8);
-    k_gemm_bf16<<<blocks(warps * 32, 128), 128, 0, st>>>(A, sam, sak, B, sbk, sbn, C, ldc, M, N, K);
+template <int BN>
+int gemm_tc(const __nv_bfloat16* A, long sam, long sak, const __nv_bfloat16* B, long sbk, long sbn, float* C, int ldc,
+            int M, int N, int K, cudaStream_t st) {
+    constexpr int smem = tc_smem_bytes<BN>();
+    static unsigned long long attr_set = 0;  // devices on which the kernel's shared-memory limit is raised
+    int dev = 0;
+    MCK(cudaGetDevice(&dev));
+    if (dev >= 64 || !(attr_set >> dev & 1ull)) {
+        MCK(cudaFuncSetAttribute(k_gemm_tc<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        if (dev < 64) attr_set |= 1ull << dev;
+    }
+    const dim3 grid((unsigned)((M + TC_BM - 1) / TC_BM), (unsigned)((N + BN - 1) / BN));
+    k_gemm_tc<BN><<<grid, 128, smem, st>>>(A, sam, sak, B, sbk, sbn, C, ldc, M, N, K);
     MCK(cudaGetLastError());
     return MIRAGE_OK;
+}
+
+// the N tile: the smallest of 16, 32, 64, 128, 256 that covers N (N > 256
+// runs in several 256-column tiles)
+int gemm(const __nv_bfloat16* A, long sam, long sak, const __nv_bfloat16* B, long sbk, long sbn, float* C, int ldc,
+         int M, int N, int K, cudaStream_t st) {
+    if (M <= 0 || N <= 0) return MIRAGE_OK;
+    if (N <= 16) return gemm_tc<16>(A, sam, sak, B, sbk, sbn, C, ldc, M, N, K, st);
+    if (N <= 32) return gemm_tc<32>(A, sam, sak, B, sbk, sbn, C, ldc, M, N, K, st);
+    if (N <= 64) return gemm_tc<64>(A, sam, sak, B, sbk, sbn, C, ldc, M, N, K, st);
+    if (N <= 128) return gemm_tc<128>(A, sam, sak, B, sbk, sbn, C, ldc, M, N, K, st);
+    return gemm_tc<256>(A, sam, sak, B, sbk, sbn, C, ldc, M, N, K, st);
 }
 
 // forward pass storing Z (FP32) and A (BF16); Y (FP32) written to y.  With

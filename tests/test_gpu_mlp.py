@@ -56,6 +56,28 @@ def test_forward_and_gradients(binding, dims):
     net.close()
 
 
+@pytest.mark.parametrize("rows,k,n", [(1, 7, 2), (127, 64, 16), (128, 65, 17), (300, 256, 256),
+                                       (1000, 300, 300), (257, 33, 200)])
+def test_tensor_core_product_per_element(binding, rows, k, n):
+    """A one-layer network is the product itself: Y = bf16(X) bf16(W)^T + b.
+    Every element is checked against FP64 on the same BF16 operands, with the
+    FP32 accumulation bound (K + 8) 2^-22 sum|terms|: ragged M, N and K
+    tiles, N above one 256-column tile, and K above one 64-wide chunk."""
+    net = binding.MLP([k, n], seed=5)
+    rng = np.random.default_rng(rows + k + n)
+    flat = rng.standard_normal(net.n_params).astype(np.float32)
+    net.set_params(flat)
+    X = rng.standard_normal((rows, k)).astype(np.float32)
+    (W, b), = net.layers(flat)
+    Xr, Wr = bf16_round(X), bf16_round(W).reshape(W.shape)
+    ref = Xr @ Wr.T + b
+    bound = (k + 8) * 2.0 ** -22 * (np.abs(Xr) @ np.abs(Wr).T + np.abs(b)) + 1e-30
+    Y = net.forward(torch.as_tensor(X, device="cuda")).cpu().numpy().astype(np.float64)
+    assert Y.shape == (rows, n)
+    assert np.all(np.abs(Y - ref) <= bound), np.max(np.abs(Y - ref) / bound)
+    net.close()
+
+
 def test_adam_step_matches_oracle(binding):
     net = binding.MLP([7, 32, 2], seed=2)
     rng = np.random.default_rng(1)

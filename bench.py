@@ -400,6 +400,7 @@ def run_gpu(args):
         return res
 
     tf32_res = _guarded("tf32_precision", _tf32_section)
+    tcblur_res = _guarded("tc_blur", blur_engine_compare) if rank == 0 else None
 
     def _iter_section():
         # the paper's own fitness: 40 CGLS iterations per candidate, L-curve over
@@ -505,6 +506,15 @@ def run_gpu(args):
                             "surrogate_rmse_by_gen": [None if h.surrogate_rmse is None else round(h.surrogate_rmse, 4)
                                                       for h in gens],
                             "fallback_rate": (1.0 - sum(h.screened for h in gens) / max(1, len(gens))) if sur_on else None}
+        # best chi^2 of each run at the wall time at which the faster run ended
+        # (generation 0, the shared initial population, excluded from the clock)
+        def best_at(r, t):
+            cum = np.cumsum(r["seconds_by_gen"][1:])
+            k = int(np.searchsorted(cum, t * (1 + 1e-9), side="right"))
+            return r["best_chi2_by_gen"][k]
+        t_eq = min(sum(ga_res[k]["seconds_by_gen"][1:]) for k in ("with_surrogate", "without"))
+        ga_res["best_chi2_at_equal_time"] = {"seconds": round(t_eq, 3),
+                                             **{k: best_at(ga_res[k], t_eq) for k in ("with_surrogate", "without")}}
         ga_res["generations"] = n_gen
         ga_res["oversample"] = 4
         ga_res["note"] = ("decisions = offspring ranked per second (surrogate screen, then the exact solve of the "
@@ -570,6 +580,7 @@ def run_gpu(args):
             "accuracy": acc_res,
             "tight_tolerance": tight_res,
             "tf32_precision": tf32_res,
+            "tc_blur": tcblur_res,
             "ga_surrogate": ga_res,
             "pso": pso_res,
             "iter_lcurve": iter_res,
@@ -613,6 +624,64 @@ def run_profile_case(variant: int, n_cand: int = 160) -> int:
                       "phase_clk_per_iteration": {n: round(c / max(its, 1.0), 1) for n, c in zip(names, clk)}}),
           flush=True)
     ctx.close()
+    return 0
+
+
+def blur_engine_compare(n: int = 4096, reps: int = 64, repeats: int = 3) -> dict:
+    """The blur B of the inner solves (64 x 64 images, the workload's 9 x 9
+    Gaussian PSF) on the CG kernel's FFMA register tiles and as TF32
+    block-Toeplitz products on the tcgen05 tensor cores (mirage_psf_blur):
+    n images, B applied `reps` times to each while it stays in shared
+    memory, the fastest of `repeats` timed calls after a warm-up call."""
+    import torch
+
+    import synth
+    from paper_1101_5803_gb300 import binding
+    g = synth.geom_ga64()
+    K = g.kpsf
+    psf = synth.gaussian_psf(K, synth.PSF_SIGMA["ga64"]).astype(np.float32)
+    imgs = torch.as_tensor(np.random.default_rng(11).standard_normal((n, g.ny, g.nx)).astype(np.float32),
+                           device="cuda")
+    out = torch.empty_like(imgs)
+    flop = 2.0 * K * K * g.nx * g.ny
+    # the products the tensor cores execute: 16-column strips, 128-row tiles
+    # of the stacked strips, a 24-wide Toeplitz window per PSF row
+    tiles = -(-(g.nx // 16) * (g.ny + K - 1) // 128)
+    tc_flop = 2.0 * tiles * 128 * 16 * ((16 + K - 1 + 7) // 8 * 8) * K
+    peaks, basis = measured_peaks()
+    tf32_peak = peaks["bf16_tflops"] / 2.0
+    res = {"images": n, "reps": reps, "image": [g.ny, g.nx], "kpsf": K, "algorithmic_flop_per_blur": flop,
+           "tensor_flop_per_blur": tc_flop,
+           "tf32_peak_tflops": tf32_peak, "tf32_peak_basis": f"{basis} bf16 x 1/2 (nominal TF32/BF16 ratio)"}
+    one = {}
+    for name, eng in (("ffma", binding.MIRAGE_BLUR_FFMA), ("tc_tf32", binding.MIRAGE_BLUR_TC_TF32)):
+        binding.mirage_psf_blur(eng, imgs, psf, reps, out=out)
+        best = float("inf")
+        for _ in range(repeats):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            binding.mirage_psf_blur(eng, imgs, psf, reps, out=out)
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        nb = n * reps
+        r = {"ms": best, "ns_per_blur": best * 1e6 / nb, "tflops_algorithmic": flop * nb / (best * 1e-3) / 1e12}
+        if eng == binding.MIRAGE_BLUR_TC_TF32:
+            r["tflops_tensor"] = tc_flop * nb / (best * 1e-3) / 1e12
+            r["frac_of_tf32_peak"] = r["tflops_tensor"] / tf32_peak
+        res[name] = r
+        one[name] = binding.mirage_psf_blur(eng, imgs[:256], psf, 1).double()
+    res["tc_max_rel_diff_one_blur"] = float(((one["tc_tf32"] - one["ffma"]).abs().max() /
+                                             one["ffma"].abs().max()).item())
+    res["speedup_tc_over_ffma"] = res["ffma"]["ms"] / res["tc_tf32"]["ms"]
+    return res
+
+
+def run_blur_engines(n: int, reps: int) -> int:
+    """The blur-engine comparison alone (also the case of its ncu captures)."""
+    import __graft_entry__
+    __graft_entry__.build()
+    print(json.dumps({"blur_engines": blur_engine_compare(n, reps)}), flush=True)
     return 0
 
 
@@ -848,8 +917,8 @@ def run_workload(name: str, args) -> int:
 
 def run_profile_large() -> int:
     """The case the ncu captures of the general CGLS kernel at 256x256 run
-    (GLOBAL placement: the work vectors live in an L2-resident slab): 152
-    candidates x lambda = 10 (one item per SM), two evaluations."""
+    (all work vectors in the CTA's global slab, two CTAs per SM): 304
+    candidates x lambda = 10 (one item per CTA slot), two evaluations."""
     import torch
 
     import __graft_entry__
@@ -857,12 +926,13 @@ def run_profile_large() -> int:
     from paper_1101_5803_gb300 import binding
     from paper_1101_5803_gb300.problems import large_workload
     ctx = binding.Context(0, binding.MIRAGE_FP32)
-    wl = large_workload(ctx, n_cand=152, n_lam=1, seed=3)
-    lam = torch.full((152, 1), 10.0, dtype=torch.float64, device="cuda")
+    n = 304
+    wl = large_workload(ctx, n_cand=n, n_lam=1, seed=3)
+    lam = torch.full((n, 1), 10.0, dtype=torch.float64, device="cuda")
     for _ in range(2):
         out = ctx.eval_batch([wl.problem], wl.lens, wl.prob_idx, lam, wl.n_lam, tol=TOL)
     torch.cuda.synchronize()
-    print(json.dumps({"profile_large": True, "items": 152, "cg_iterations": int(out["iters"].sum().item()),
+    print(json.dumps({"profile_large": True, "items": n, "cg_iterations": int(out["iters"].sum().item()),
                       "iters_max": int(out["iters"].max().item()),
                       "converged": bool(((out["item_status"] & 7) == 0).all().item())}), flush=True)
     ctx.close()
@@ -889,7 +959,13 @@ def main():
                     help="run one of the other stated workloads at full size with a sampled oracle check and "
                          "print its own JSON line")
     ap.add_argument("--generations", type=int, default=200, help="generations of --workload ga128")
+    ap.add_argument("--blur-engines", action="store_true",
+                    help="run only the blur-engine comparison (FFMA tiles against tcgen05 TF32) and exit")
+    ap.add_argument("--blur-images", type=int, default=4096, help="images of --blur-engines")
+    ap.add_argument("--blur-reps", type=int, default=64, help="applications of B per image in --blur-engines")
     args = ap.parse_args()
+    if args.blur_engines:
+        return run_blur_engines(args.blur_images, args.blur_reps)
     if args.workload:
         return run_workload(args.workload, args)
     if args.profile_large:

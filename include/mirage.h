@@ -139,10 +139,14 @@ typedef struct {
                           MIRAGE_ERR_ARG.  Changes the iteration path, not the
                           solution (to tol).  FP64 contexts ignore it. */
     int place;         /* work-buffer placement of the general kernel: 0 = automatic
-                          (the most on-chip placement that fits), 1 = all in shared
+                          (the most on-chip placement that fits; all in the slab
+                          means 4 where that kernel is compiled for the PSF width),
+                          1 = all in shared
                           memory, 2 = convolution inputs and source vectors in
                           shared memory, the rest in an L2-resident slab, 3 = all in
-                          the slab; a placement that does not fit, or a problem on
+                          the slab, 4 = all in the slab with two CTAs per SM (the
+                          kernel held to 128 registers a thread; FP32 contexts,
+                          else 3); a placement that does not fit, or a problem on
                           the FFT path (always 3), keeps the automatic one.  Other
                           values: MIRAGE_ERR_ARG. */
 } mirage_opts_t;
@@ -293,8 +297,10 @@ const char* mirage_last_error(void);
  * Surrogate network (the learned screen in front of the exact solves).
  * A multilayer perceptron dims[0] -> dims[1] -> ... -> dims[n_layers]: SiLU
  * after every hidden layer, linear output, mean-squared-error loss, Adam
- * (b1 0.9, b2 0.999, eps 1e-8).  Products run on BF16 tensor cores with
- * FP32 accumulation; master weights, moments and activations' gradients
+ * (b1 0.9, b2 0.999, eps 1e-8).  Products run on the tcgen05 tensor cores
+ * (BF16 operands, FP32 accumulation in tensor memory; if a product's
+ * completion wait runs out, about a second, its output tile is NaN); master
+ * weights, moments and activations' gradients
  * are FP32.  Parameters are ordered W_1 [dims[1] x dims[0]] (row-major),
  * b_1 [dims[1]], W_2, b_2, ...  Device arrays unless noted; the network
  * object owns its weights and work buffers.  The paper's optimisers use no
@@ -363,6 +369,35 @@ const char* mirage_noalloc_last_error(void);
 
 /* Size in bytes of the fixed scratch array of mirage_forward_noalloc. */
 size_t mirage_noalloc_capacity(void);
+
+/* Repeated PSF blur of a batch of images on one of two engines.  A
+ * measurement entry point, not a step of the solve path: it times the blur
+ * B of the linear system (Section 2.2; the paper applies it by FFT) as the
+ * FP32 inner solves apply it, against a tensor-core form of it.
+ *  engine  MIRAGE_BLUR_FFMA: the CG kernel's FP32 FFMA register tiles (4 x 4
+ *          outputs per thread, taps as kernel parameters);
+ *          MIRAGE_BLUR_TC_TF32: block-Toeplitz products on the tcgen05
+ *          tensor cores (strips of 16 output columns, M = 128 stacked rows,
+ *          a 24 x 16 Toeplitz matrix per PSF row), both factors rounded to
+ *          TF32 (nearest), FP32 accumulation in tensor memory.
+ *  img     device, n images of ny x nx FP32, row-major, back to back;
+ *          16-byte aligned
+ *  out     device, same layout (may not alias img): B applied `reps` times
+ *          to each image, (B x)(y, x) = sum_ij psf(i, j) x(y - i + h,
+ *          x - j + h) with h = (K - 1) / 2 and x zero outside the image,
+ *          the oracle's blur operator
+ *  psf     HOST, K x K FP32, row-major
+ *  reps    >= 1; each image stays in shared memory between applications
+ * Limits: K = 9; nx a positive multiple of 16; the image must fit shared
+ * memory (64 x 64 fits both engines).  Returns MIRAGE_ERR_ARG or
+ * MIRAGE_ERR_UNSUPPORTED otherwise (text in mirage_blur_last_error).  If a
+ * tensor-core completion wait runs out (about a second), the affected
+ * images are written as NaN.  Asynchronous on `stream`. */
+#define MIRAGE_BLUR_FFMA 0
+#define MIRAGE_BLUR_TC_TF32 1
+int mirage_psf_blur(int engine, const float* img, float* out, int n, int nx, int ny, const float* psf, int K,
+                    int reps, void* stream);
+const char* mirage_blur_last_error(void);
 
 /* FP32 FMA-pipe microbenchmark on `device`: sixteen independent FMA chains
  * per thread on every SM, timed with CUDA events after a warm-up launch.

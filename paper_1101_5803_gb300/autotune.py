@@ -13,9 +13,10 @@ and keeping the fastest of a few runs:
   (mirage_opts_t.inner_eta; FP32 contexts): a smaller target means fewer
   FP64 residual passes but longer inner solves, timed on the probe
   candidates' whole lambda grids, since the trade-off moves with lambda;
-* the work-buffer placement of the problems that run on the general kernel
-  (mirage_opts_t.place): all in shared memory, the convolution inputs in
-  shared memory and the rest in an L2-resident slab, or all in the slab.
+* the work-buffer placement and occupancy of the problems that run on the
+  general kernel (mirage_opts_t.place): all in shared memory, the
+  convolution inputs in shared memory and the rest in an L2-resident slab,
+  or all in the slab with one or two CTAs per SM.
 
 A choice replaces the default only when it is more than MARGIN faster on the
 probe.  All choices solve the same systems to the same tolerance (variants
@@ -36,7 +37,7 @@ from .binding import MIRAGE_FP32
 
 VARIANTS = (0, 1, 2, 3, 4)  # 0: the library's automatic choice
 ETAS = (0.01, 0.03, 0.1)     # the first is the library's default
-PLACES = (1, 2, 3)
+PLACES = (1, 2, 3, 4)
 MARGIN = 0.03                # a choice must beat the default by this much to replace it
 MARGIN_PLACE = 0.05          # (a placement only moves the problems on the general kernel)
 

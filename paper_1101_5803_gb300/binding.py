@@ -27,6 +27,7 @@ MIRAGE_MEM_DEVICE, MIRAGE_MEM_HOST = 0, 1
 MIRAGE_MODE_BATCHED, MIRAGE_MODE_PLAIN = 0, 1
 MIRAGE_INTERP_BILINEAR, MIRAGE_INTERP_NEAREST, MIRAGE_INTERP_BICUBIC = 0, 1, 2
 MIRAGE_REG_IDENTITY, MIRAGE_REG_GRADIENT, MIRAGE_REG_LAPLACIAN = 0, 1, 2
+MIRAGE_BLUR_FFMA, MIRAGE_BLUR_TC_TF32 = 0, 1
 ST_MAXIT, ST_STAGNATION, ST_BREAKDOWN, ST_BAD_PARAM, ST_EMPTY_MAP, ST_LCURVE_FLAT = 1, 2, 4, 8, 16, 32
 MAX_LAM = 64
 MAX_KPSF = 65  # MIRAGE_MAX_KPSF
@@ -101,6 +102,10 @@ def load_library():
     lib.mirage_forward_noalloc.restype = ip
     lib.mirage_noalloc_last_error.argtypes = []
     lib.mirage_noalloc_last_error.restype = ctypes.c_char_p
+    lib.mirage_psf_blur.argtypes = [i, vp, vp, i, i, i, vp, i, i, vp]
+    lib.mirage_psf_blur.restype = ip
+    lib.mirage_blur_last_error.argtypes = []
+    lib.mirage_blur_last_error.restype = ctypes.c_char_p
     lib.mirage_noalloc_capacity.argtypes = []
     lib.mirage_noalloc_capacity.restype = ctypes.c_size_t
     ll = ctypes.c_long
@@ -329,6 +334,23 @@ def mirage_forward_noalloc(precision, prob, lens, S, *, want_model=True, stream=
         raise MirageError(f"mirage_forward_noalloc failed ({rc}): "
                           f"{lib.mirage_noalloc_last_error().decode(errors='replace')}")
     return model, chi2, status
+
+
+def mirage_psf_blur(engine, img, psf, reps=1, *, out=None, stream=None):
+    """B applied ``reps`` times to each image of ``img`` [n, ny, nx] (FP32,
+    device) with the K x K ``psf`` (host array) on the FFMA or the
+    tensor-core engine (see mirage.h).  Returns the output tensor."""
+    lib = load_library()
+    img = img.contiguous()
+    n, ny, nx = (int(d) for d in img.shape)
+    psf = np.ascontiguousarray(np.asarray(psf, dtype=np.float32))
+    if out is None:
+        out = torch.empty_like(img)
+    rc = lib.mirage_psf_blur(int(engine), _ptr(img), _ptr(out), n, nx, ny, psf.ctypes.data_as(ctypes.c_void_p),
+                             int(psf.shape[0]), int(reps), _stream_ptr(stream))
+    if rc != MIRAGE_OK:
+        raise MirageError(f"mirage_psf_blur failed ({rc}): {lib.mirage_blur_last_error().decode(errors='replace')}")
+    return out
 
 
 class MLP:

@@ -269,12 +269,26 @@ const void* pick_cgls(int prec, int place, int K) {
 template <typename T>
 int pick_place(const mirage_ctx* ctx, const Prob<T>& P, int want = 0) {
     if (P.fft_m) return PLACE_GLOBAL;  // the FFT path lives in the runtime-K global-memory kernel
-    // a requested placement (mirage_opts_t.place: 1 SMEM, 2 MID, 3 GLOBAL) where it fits
+    // a requested placement (mirage_opts_t.place: 1 SMEM, 2 MID, 3 GLOBAL,
+    // 4 GLOBAL with two CTAs per SM) where it fits
     if (want == 1 && smem_bytes<T>(P, PLACE_SMEM) <= (size_t)ctx->max_smem) return PLACE_SMEM;
     if (want == 2 && sizeof(T) == 4 && smem_bytes<T>(P, PLACE_MID) <= (size_t)ctx->max_smem) return PLACE_MID;
     if (want == 3) return PLACE_GLOBAL;
+    if (want == 4) {
+        const KernelTable& t = table();
+        if (sizeof(T) == 4 && (t.cgls[0][PLACE_GLOBAL2][P.K < MAX_K ? P.K : 0] || t.cgls[0][PLACE_GLOBAL2][0]) &&
+            2 * (long long)smem_bytes<T>(P, PLACE_GLOBAL) <= ctx->max_smem_sm - 2048)
+            return PLACE_GLOBAL2;
+        return PLACE_GLOBAL;
+    }
     if (smem_bytes<T>(P, PLACE_SMEM) <= (size_t)ctx->max_smem) return PLACE_SMEM;
     if (sizeof(T) == 4 && smem_bytes<T>(P, PLACE_MID) <= (size_t)ctx->max_smem) return PLACE_MID;
+    // all in the slab: two CTAs per SM where that kernel is compiled for the
+    // problem's PSF width (FP32; 1.47x faster at 256 x 256 with a 21 x 21 PSF,
+    // where one 253-register CTA per SM could not hide the slab's latency)
+    if (sizeof(T) == 4 && P.K < MAX_K && table().cgls[0][PLACE_GLOBAL2][P.K] &&
+        2 * (long long)smem_bytes<T>(P, PLACE_GLOBAL) <= ctx->max_smem_sm - 2048)
+        return PLACE_GLOBAL2;
     return PLACE_GLOBAL;
 }
 
@@ -476,7 +490,7 @@ int eval_impl(mirage_ctx* ctx, const mirage_problem_t* probs, int n_probs, const
     }
     const mirage_opts_t o = *opts;
     if (!(o.tol >= 0) || o.mode < 0 || o.mode > 1 || o.mem < 0 || o.mem > 1 || o.variant < 0 || o.variant > 7 ||
-        !(o.inner_eta == 0.0 || (o.inner_eta >= 1e-4 && o.inner_eta <= 0.5)) || o.place < 0 || o.place > 3) {
+        !(o.inner_eta == 0.0 || (o.inner_eta >= 1e-4 && o.inner_eta <= 0.5)) || o.place < 0 || o.place > 4) {
         set_error("eval_batch: bad options");
         return MIRAGE_ERR_ARG;
     }
@@ -669,9 +683,9 @@ int eval_impl(mirage_ctx* ctx, const mirage_problem_t* probs, int n_probs, const
         const int place = pick_place<T>(ctx, P, o.place);
         const bool big = place != PLACE_SMEM;
         const void* fn = pick_cgls(prec, place, P.fft_m ? 0 : P.K);
-        size_t item_smem = smem_bytes<T>(P, place);
-        long long item_slab = (long long)slab_bytes<T>(P, place);
-        int per_sm = 1, mode = 0;
+        size_t item_smem = smem_bytes<T>(P, layout_of(place));
+        long long item_slab = (long long)slab_bytes<T>(P, layout_of(place));
+        int per_sm = place == PLACE_GLOBAL2 ? 2 : 1, mode = 0;
         bool fast = false;
         if (const void* ff = choose(P, mode, fast)) {
             fn = ff;
@@ -1004,7 +1018,7 @@ int eval_impl(mirage_ctx* ctx, const mirage_problem_t* probs, int n_probs, const
                 const Prob<T>& P = hp[prob_idx[c]];
                 const int place = pick_place<T>(ctx, P, o.place);
                 const void* fn = pick_cgls(prec, place, P.fft_m ? 0 : P.K);
-                size_t item_smem = smem_bytes<T>(P, place);
+                size_t item_smem = smem_bytes<T>(P, layout_of(place));
                 int pmode = 0;
                 bool pfast = false;
                 if (const void* ff = choose(P, pmode, pfast)) {

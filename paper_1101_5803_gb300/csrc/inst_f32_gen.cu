@@ -6,6 +6,7 @@ namespace mirage {
 void fill_f32_gen(KernelTable& t) {
     t.cgls[0][0][0] = (const void*)k_cgls<float, 0, PLACE_SMEM>;
     t.cgls[0][1][0] = (const void*)k_cgls<float, 0, PLACE_GLOBAL>;
+    t.cgls[0][PLACE_GLOBAL2][0] = (const void*)k_cgls<float, 0, PLACE_GLOBAL, 2>;
     t.cgls[0][2][0] = (const void*)k_cgls<float, 0, PLACE_MID>;
     t.fwd[0][0] = (const void*)k_forward<float, 0>;
     t.fwd[0][9] = (const void*)k_forward<float, 9>;

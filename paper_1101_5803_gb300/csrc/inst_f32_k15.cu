@@ -6,6 +6,7 @@ namespace mirage {
 void fill_f32_k15(KernelTable& t) {
     t.cgls[0][0][15] = (const void*)k_cgls<float, 15, PLACE_SMEM>;
     t.cgls[0][1][15] = (const void*)k_cgls<float, 15, PLACE_GLOBAL>;
+    t.cgls[0][PLACE_GLOBAL2][15] = (const void*)k_cgls<float, 15, PLACE_GLOBAL, 2>;
     t.cgls[0][2][15] = (const void*)k_cgls<float, 15, PLACE_MID>;
 
 }

@@ -6,6 +6,7 @@ namespace mirage {
 void fill_f32_k9(KernelTable& t) {
     t.cgls[0][0][9] = (const void*)k_cgls<float, 9, PLACE_SMEM>;
     t.cgls[0][1][9] = (const void*)k_cgls<float, 9, PLACE_GLOBAL>;
+    t.cgls[0][PLACE_GLOBAL2][9] = (const void*)k_cgls<float, 9, PLACE_GLOBAL, 2>;
     t.cgls[0][2][9] = (const void*)k_cgls<float, 9, PLACE_MID>;
 }
 }  // namespace mirage

@@ -1301,6 +1301,10 @@ __host__ __device__ inline size_t align_up(size_t v, size_t a) {
 //   PLACE_MID    the two convolution inputs and the source vectors in
 //                shared memory, the rest in the slab (mid-size images)
 enum : int { PLACE_SMEM = 0, PLACE_GLOBAL = 1, PLACE_MID = 2 };
+// kernel-table index of the global-slab kernel compiled for two CTAs per SM
+// (its buffers are laid out as PLACE_GLOBAL)
+constexpr int PLACE_GLOBAL2 = 3;
+__host__ __device__ constexpr int layout_of(int place) { return place == PLACE_GLOBAL2 ? PLACE_GLOBAL : place; }
 
 template <typename T>
 __host__ __device__ inline size_t smem_bytes(const Prob<T>& P, int place) {
@@ -1361,8 +1365,11 @@ struct ChainPos {
     }
 };
 
-template <typename T, int K, int PLACE>
-__global__ void __launch_bounds__(NTHREADS, 1) k_cgls(CglsArgs<T> A) {
+// MINB: resident CTAs per SM the register allocation is held to (2 caps
+// it at 128 registers a thread, so that two latency-bound global-slab CTAs
+// share an SM)
+template <typename T, int K, int PLACE, int MINB = 1>
+__global__ void __launch_bounds__(NTHREADS, MINB) k_cgls(CglsArgs<T> A) {
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr bool BIG = PLACE == PLACE_GLOBAL;
     constexpr bool MID = PLACE == PLACE_MID;

@@ -48,28 +48,81 @@ constexpr int tc_smem_bytes() {
     return (TC_BM + BN) * TC_BK * 2 + 16;
 }
 
-__device__ __forceinline__ void tc_stage(__nv_bfloat16* dst, int rows, const __nv_bfloat16* __restrict__ src,
-                                         long s_row, long s_k, int r0, int R, int k0, int K) {
-    // element (r, k) of the tile -> core matrix (r / 8, k / 8), k-chunks
-    // innermost: byte ((r / 8) * 8 + k / 8) * 128 + (r % 8) * 16 + (k % 8) * 2
-    const __nv_bfloat16 z = __float2bfloat16(0.f);
-    const int n = rows * TC_BK;
-    if (s_k == 1) {  // consecutive threads along k
-        for (int e = threadIdx.x; e < n; e += blockDim.x) {
-            const int r = e / TC_BK, k = e - r * TC_BK;
-            const int gr = r0 + r, gk = k0 + k;
-            dst[((r >> 3) * 8 + (k >> 3)) * 64 + (r & 7) * 8 + (k & 7)] =
-                (gr < R && gk < K) ? src[(long)gr * s_row + gk] : z;
-        }
-    } else {  // consecutive threads along the rows
-        for (int e = threadIdx.x; e < n; e += blockDim.x) {
-            const int k = e / rows, r = e - k * rows;
-            const int gr = r0 + r, gk = k0 + k;
-            dst[((r >> 3) * 8 + (k >> 3)) * 64 + (r & 7) * 8 + (k & 7)] =
-                (gr < R && gk < K) ? src[(long)gr * s_row + (long)gk * s_k] : z;
+// element (r, k) of a staged tile -> core matrix (r / 8, k / 8), k-chunks
+// innermost: BF16 index ((r / 8) * 8 + k / 8) * 64 + (r % 8) * 8 + k % 8, so
+// one 16-byte row of a core matrix holds 8 consecutive k of one row r
+__device__ __forceinline__ int tc_at(int r, int k) { return ((r >> 3) * 8 + (k >> 3)) * 64 + (r & 7) * 8 + (k & 7); }
+
+// How an operand view is staged: rows contiguous along k (16-byte rows of
+// 8 k), a transposed view (8 rows contiguous at one k), or element by element
+enum : int { ST_KROW = 0, ST_KCOL = 1, ST_SCALAR = 2 };
+
+__device__ __forceinline__ int stage_mode(const __nv_bfloat16* src, long s_row, long s_k) {
+    const bool al = ((uintptr_t)src & 15) == 0;
+    if (s_k == 1 && (s_row & 7) == 0 && al) return ST_KROW;
+    if (s_row == 1 && (s_k & 7) == 0 && al) return ST_KCOL;
+    return ST_SCALAR;
+}
+
+// One K chunk of a ROWS x 64 operand tile: the loads into registers (NV
+// 16-byte vectors a thread, all issued before any is used, so their
+// latencies overlap one another and the previous chunk's products) ...
+template <int ROWS>
+struct TcStage {
+    static constexpr int NV = ROWS * (TC_BK / 8) / 128;
+    uint4 v[NV];
+
+    __device__ __forceinline__ void load(int mode, const __nv_bfloat16* __restrict__ src, long s_row, long s_k,
+                                         int r0, int R, int k0, int K) {
+        const __nv_bfloat16 z = __float2bfloat16(0.f);
+#pragma unroll
+        for (int i = 0; i < NV; ++i) {
+            const int e = threadIdx.x + 128 * i;
+            v[i] = make_uint4(0u, 0u, 0u, 0u);
+            __nv_bfloat16* t = reinterpret_cast<__nv_bfloat16*>(&v[i]);
+            if (mode == ST_KROW) {  // row r, k-octet kc
+                const int r = e >> 3, gr = r0 + r, gk = k0 + 8 * (e & 7);
+                if (gr < R && gk + 8 <= K)
+                    v[i] = *reinterpret_cast<const uint4*>(src + (long)gr * s_row + gk);
+                else if (gr < R)
+                    for (int j = 0; j < 8; ++j) t[j] = gk + j < K ? src[(long)gr * s_row + gk + j] : z;
+            } else if (mode == ST_KCOL) {  // rows 8 g .. 8 g + 7 at one k
+                const int g = e / TC_BK, gr = r0 + 8 * g, gk = k0 + (e - g * TC_BK);
+                if (gk < K && gr + 8 <= R)
+                    v[i] = *reinterpret_cast<const uint4*>(src + (long)gk * s_k + gr);
+                else if (gk < K)
+                    for (int j = 0; j < 8; ++j) t[j] = gr + j < R ? src[(long)gk * s_k + gr + j] : z;
+            }
         }
     }
-}
+
+    // ... then the stores into the K-major core-matrix layout (the element
+    // by element mode loads and stores here)
+    __device__ __forceinline__ void store(int mode, __nv_bfloat16* dst, const __nv_bfloat16* __restrict__ src,
+                                          long s_row, long s_k, int r0, int R, int k0, int K) const {
+        if (mode == ST_SCALAR) {
+            const __nv_bfloat16 z = __float2bfloat16(0.f);
+            for (int e = threadIdx.x; e < ROWS * TC_BK; e += 128) {
+                const int r = e / TC_BK, k = e - r * TC_BK;
+                const int gr = r0 + r, gk = k0 + k;
+                dst[tc_at(r, k)] = (gr < R && gk < K) ? src[(long)gr * s_row + (long)gk * s_k] : z;
+            }
+            return;
+        }
+#pragma unroll
+        for (int i = 0; i < NV; ++i) {
+            const int e = threadIdx.x + 128 * i;
+            if (mode == ST_KROW) {
+                *reinterpret_cast<uint4*>(dst + tc_at(e >> 3, 8 * (e & 7))) = v[i];
+            } else {
+                const int g = e / TC_BK, k = e - g * TC_BK;
+                const __nv_bfloat16* t = reinterpret_cast<const __nv_bfloat16*>(&v[i]);
+#pragma unroll
+                for (int j = 0; j < 8; ++j) dst[tc_at(8 * g + j, k)] = t[j];
+            }
+        }
+    }
+};
 
 template <int BN>
 __global__ void __launch_bounds__(128) k_gemm_tc(const __nv_bfloat16* __restrict__ A, long sam, long sak,
@@ -85,6 +138,12 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const __nv_bfloat16* __restrict
     uint32_t* slot = reinterpret_cast<uint32_t*>(bar + 1);
     const int m0 = blockIdx.x * TC_BM, n0 = blockIdx.y * BN;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // B(k, n) is staged as rows n: row stride sbn, k stride sbk
+    const int ma = stage_mode(A, sam, sak), mb = stage_mode(B, sbn, sbk);
+    TcStage<TC_BM> ra;
+    TcStage<BN> rb;
+    ra.load(ma, A, sam, sak, m0, M, 0, K);
+    rb.load(mb, B, sbn, sbk, n0, N, 0, K);
     if (warp == 0) tmem_alloc(slot, TCOLS);
     if (threadIdx.x == 0) bar_init(bar, 1);
     fence_before_sync();
@@ -94,9 +153,8 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const __nv_bfloat16* __restrict
     bool ok = true;
     uint32_t phase = 0;
     for (int k0 = 0; k0 < K && ok; k0 += TC_BK) {
-        tc_stage(sA, TC_BM, A, sam, sak, m0, M, k0, K);
-        // B(k, n) as rows n: row stride sbn, k stride sbk
-        tc_stage(sB, BN, B, sbn, sbk, n0, N, k0, K);
+        ra.store(ma, sA, A, sam, sak, m0, M, k0, K);
+        rb.store(mb, sB, B, sbn, sbk, n0, N, k0, K);
         fence_async_smem();
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -110,6 +168,10 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const __nv_bfloat16* __restrict
                 mma_bf16(tmem, da, db, ID, (k0 > 0 || s > 0) ? 1u : 0u);
             }
             commit(bar);
+        }
+        if (k0 + TC_BK < K) {  // the next chunk's loads overlap these products
+            ra.load(ma, A, sam, sak, m0, M, k0 + TC_BK, K);
+            rb.load(mb, B, sbn, sbk, n0, N, k0 + TC_BK, K);
         }
         ok = __syncthreads_and(bar_wait(bar, phase)) != 0;  // one decision for the whole CTA
         phase ^= 1;
@@ -331,29 +393,30 @@ template <int BN>
 int gemm_tc(const __nv_bfloat16* A, long sam, long sak, const __nv_bfloat16* B, long sbk, long sbn, float* C, int ldc,
             int M, int N, int K, cudaStream_t st) {
     constexpr int smem = tc_smem_bytes<BN>();
-    static unsigned long long attr_set = 0;  // devices on which the kernel's shared-memory limit is raised
-    int dev = 0;
-    MCK(cudaGetDevice(&dev));
-    if (dev >= 64 || !(attr_set >> dev & 1ull)) {
-        MCK(cudaFuncSetAttribute(k_gemm_tc<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-        if (dev < 64) attr_set |= 1ull << dev;
-    }
     const dim3 grid((unsigned)((M + TC_BM - 1) / TC_BM), (unsigned)((N + BN - 1) / BN));
     k_gemm_tc<BN><<<grid, 128, smem, st>>>(A, sam, sak, B, sbk, sbn, C, ldc, M, N, K);
     MCK(cudaGetLastError());
     return MIRAGE_OK;
 }
 
-// the N tile: the smallest of 16, 32, 64, 128, 256 that covers N (N > 256
-// runs in several 256-column tiles)
+// raises the product kernels' shared-memory limit on the current device
+// (once per network, outside any stream capture)
+int gemm_setup() {
+    MCK(cudaFuncSetAttribute(k_gemm_tc<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem_bytes<16>()));
+    MCK(cudaFuncSetAttribute(k_gemm_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem_bytes<32>()));
+    MCK(cudaFuncSetAttribute(k_gemm_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem_bytes<64>()));
+    return MIRAGE_OK;
+}
+
+// the N tile: 16 or 32 for the narrow output layer, else 64 columns (the
+// 256-wide layers run in four tiles: more CTAs, each with a shorter
+// staging pass)
 int gemm(const __nv_bfloat16* A, long sam, long sak, const __nv_bfloat16* B, long sbk, long sbn, float* C, int ldc,
          int M, int N, int K, cudaStream_t st) {
     if (M <= 0 || N <= 0) return MIRAGE_OK;
     if (N <= 16) return gemm_tc<16>(A, sam, sak, B, sbk, sbn, C, ldc, M, N, K, st);
     if (N <= 32) return gemm_tc<32>(A, sam, sak, B, sbk, sbn, C, ldc, M, N, K, st);
-    if (N <= 64) return gemm_tc<64>(A, sam, sak, B, sbk, sbn, C, ldc, M, N, K, st);
-    if (N <= 128) return gemm_tc<128>(A, sam, sak, B, sbk, sbn, C, ldc, M, N, K, st);
-    return gemm_tc<256>(A, sam, sak, B, sbk, sbn, C, ldc, M, N, K, st);
+    return gemm_tc<64>(A, sam, sak, B, sbk, sbn, C, ldc, M, N, K, st);
 }
 
 // forward pass storing Z (FP32) and A (BF16); Y (FP32) written to y.  With
@@ -436,6 +499,7 @@ int mirage_mlp_create(mirage_mlp_t** out, int device, int n_layers, const int* d
     for (int l = 0; l <= n_layers; ++l)
         if (dims[l] < 1 || dims[l] > 4096) return mlp_fail(MIRAGE_ERR_ARG, "mlp_create: layer width out of range");
     MCK(cudaSetDevice(device));
+    if (const int rs = gemm_setup()) return rs;
     mirage_mlp* m = new mirage_mlp();
     m->device = device;
     m->L = n_layers;

@@ -37,8 +37,8 @@ int mlp_fail(int code, const std::string& msg) {
 //   A(m, k) = A[m * sam + k * sak],  B(k, n) = B[k * sbk + n * sbn]  (BF16)
 // on the fifth-generation tensor cores: one CTA of four warps per 128 x BN
 // output tile, accumulator in tensor memory (BN FP32 columns), K in chunks
-// of 64 staged by the CTA into shared memory as K-major core matrices
-// (8 rows x 8 BF16), four tcgen05.mma of K = 16 per chunk issued by one
+// of TC_BK staged by the CTA into shared memory as K-major core matrices
+// (8 rows x 8 BF16), TC_BK / 16 tcgen05.mma of K = 16 per chunk issued by one
 // thread, completion through an mbarrier.  Edges are zero-filled.  Should a
 // completion wait run out (about a second), the tile is written as NaN.
 constexpr int TC_BM = 128, TC_BK = 64;
@@ -49,9 +49,10 @@ constexpr int tc_smem_bytes() {
 }
 
 // element (r, k) of a staged tile -> core matrix (r / 8, k / 8), k-chunks
-// innermost: BF16 index ((r / 8) * 8 + k / 8) * 64 + (r % 8) * 8 + k % 8, so
+// innermost: BF16 index ((r / 8) * TC_KO + k / 8) * 64 + (r % 8) * 8 + k % 8, so
 // one 16-byte row of a core matrix holds 8 consecutive k of one row r
-__device__ __forceinline__ int tc_at(int r, int k) { return ((r >> 3) * 8 + (k >> 3)) * 64 + (r & 7) * 8 + (k & 7); }
+constexpr int TC_KO = TC_BK / 8;  // k-octets (core-matrix columns) per staged row group
+__device__ __forceinline__ int tc_at(int r, int k) { return ((r >> 3) * TC_KO + (k >> 3)) * 64 + (r & 7) * 8 + (k & 7); }
 
 // How an operand view is staged: rows contiguous along k (16-byte rows of
 // 8 k), a transposed view (8 rows contiguous at one k), or element by element
@@ -64,7 +65,7 @@ __device__ __forceinline__ int stage_mode(const __nv_bfloat16* src, long s_row, 
     return ST_SCALAR;
 }
 
-// One K chunk of a ROWS x 64 operand tile: the loads into registers (NV
+// One K chunk of a ROWS x TC_BK operand tile: the loads into registers (NV
 // 16-byte vectors a thread, all issued before any is used, so their
 // latencies overlap one another and the previous chunk's products) ...
 template <int ROWS>
@@ -81,7 +82,7 @@ struct TcStage {
             v[i] = make_uint4(0u, 0u, 0u, 0u);
             __nv_bfloat16* t = reinterpret_cast<__nv_bfloat16*>(&v[i]);
             if (mode == ST_KROW) {  // row r, k-octet kc
-                const int r = e >> 3, gr = r0 + r, gk = k0 + 8 * (e & 7);
+                const int r = e / TC_KO, gr = r0 + r, gk = k0 + 8 * (e % TC_KO);
                 if (gr < R && gk + 8 <= K)
                     v[i] = *reinterpret_cast<const uint4*>(src + (long)gr * s_row + gk);
                 else if (gr < R)
@@ -113,7 +114,7 @@ struct TcStage {
         for (int i = 0; i < NV; ++i) {
             const int e = threadIdx.x + 128 * i;
             if (mode == ST_KROW) {
-                *reinterpret_cast<uint4*>(dst + tc_at(e >> 3, 8 * (e & 7))) = v[i];
+                *reinterpret_cast<uint4*>(dst + tc_at(e / TC_KO, 8 * (e % TC_KO))) = v[i];
             } else {
                 const int g = e / TC_BK, k = e - g * TC_BK;
                 const __nv_bfloat16* t = reinterpret_cast<const __nv_bfloat16*>(&v[i]);
@@ -162,9 +163,9 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const __nv_bfloat16* __restrict
 #pragma unroll
             for (int s = 0; s < TC_BK / 16; ++s) {
                 // K step s: core-matrix columns 2s and 2s + 1 (128 B apart),
-                // 8-row groups 8 * 128 B apart
-                const uint64_t da = sdesc(saddr(sA) + s * 256, 128, 1024);
-                const uint64_t db = sdesc(saddr(sB) + s * 256, 128, 1024);
+                // 8-row groups TC_KO * 128 B apart
+                const uint64_t da = sdesc(saddr(sA) + s * 256, 128, TC_KO * 128);
+                const uint64_t db = sdesc(saddr(sB) + s * 256, 128, TC_KO * 128);
                 mma_bf16(tmem, da, db, ID, (k0 > 0 || s > 0) ? 1u : 0u);
             }
             commit(bar);

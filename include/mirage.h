@@ -146,7 +146,9 @@ typedef struct {
                           shared memory, the rest in an L2-resident slab, 3 = all in
                           the slab, 4 = all in the slab with two CTAs per SM (the
                           kernel held to 128 registers a thread; FP32 contexts,
-                          else 3); a placement that does not fit, or a problem on
+                          else 3), 5 = as 2 with two CTAs per SM (FP32, where two
+                          CTAs' shared memory fits an SM, else automatic); a
+                          placement that does not fit, or a problem on
                           the FFT path (always 3), keeps the automatic one.  Other
                           values: MIRAGE_ERR_ARG. */
 } mirage_opts_t;

@@ -15,11 +15,12 @@ and keeping the fastest of a few runs:
   candidates' whole lambda grids, since the trade-off moves with lambda;
 * the work-buffer placement and occupancy of the problems that run on the
   general kernel (mirage_opts_t.place): all in shared memory, the
-  convolution inputs in shared memory and the rest in an L2-resident slab,
-  or all in the slab with one or two CTAs per SM.
+  convolution inputs in shared memory and the rest in an L2-resident slab
+  (one or two CTAs per SM), or all in the slab (one or two CTAs per SM).
 
 A choice replaces the default only when it is more than MARGIN faster on the
-probe.  All choices solve the same systems to the same tolerance (variants
+probe (the placement: on the whole batch, where one evaluation of it is
+cheap).  All choices solve the same systems to the same tolerance (variants
 1-3 and the placements bitwise alike).  A shape class is the set of (image, source
 grid, PSF, sub-pixels, regulariser) of the problems, the precision and
 whether a launch mixes PSFs; its choice is cached in a JSON file and later
@@ -37,9 +38,10 @@ from .binding import MIRAGE_FP32
 
 VARIANTS = (0, 1, 2, 3, 4)  # 0: the library's automatic choice
 ETAS = (0.01, 0.03, 0.1)     # the first is the library's default
-PLACES = (1, 2, 3, 4)
+PLACES = (1, 2, 3, 4, 5)
 MARGIN = 0.03                # a choice must beat the default by this much to replace it
 MARGIN_PLACE = 0.05          # (a placement only moves the problems on the general kernel)
+FULL_BATCH_MS = 5000.0       # placements are re-timed on whole batches up to this cost
 
 
 def cache_path() -> str:
@@ -93,12 +95,16 @@ def _pick(times: dict, default, margin=MARGIN):
 
 
 def tune_config(ctx, probs, lens, prob_idx, lambdas, n_lam, *, tol=1e-6, n_probe=None, reps=3,
-                retune=False) -> dict:
+                retune=False, full_batch_ms=None) -> dict:
     """The fastest launch configuration for this shape class, as keyword
     arguments of ``Context.eval_batch`` (variant, inner_eta, place).  The
     probe is the first n_probe candidates (default 64, or 256 for classes of
     several problems, whose items vary more: a probe of a few items per CTA
-    slot times the launch's tail, not its steady state)."""
+    slot times the launch's tail, not its steady state).  The placement is
+    then re-timed on the whole batch when one evaluation of it takes at most
+    ``full_batch_ms`` (default FULL_BATCH_MS; 0: never)."""
+    if full_batch_ms is None:
+        full_batch_ms = FULL_BATCH_MS
     key = shape_key(ctx, probs)
     db = _load()
     if key in db and not retune and "inner_eta" in db[key]:
@@ -141,10 +147,26 @@ def tune_config(ctx, probs, lens, prob_idx, lambdas, n_lam, *, tol=1e-6, n_probe
     for p in (0,) + PLACES:
         t_place[p] = _time(ctx, probs, pl, pidx, lam, nl, reps, variant=variant, inner_eta=eta, place=p, **base)
     place = _pick(t_place, 0, MARGIN_PLACE)
+    # the placements again on the whole batch when that is cheap: how the
+    # kernel groups of a mixed batch share the SMs (one or two CTAs per SM,
+    # which groups overlap) depends on the batch's size, which a probe of a
+    # few hundred candidates does not reproduce
+    t_full = {}
+    n_all = int(lens.shape[0])
+    if n_all > n and full_batch_ms > 0:
+        nl_all = np.asarray(n_lam).astype(np.int32)
+        full = lambda p: _time(ctx, probs, lens, prob_idx, lambdas, nl_all, 1, variant=variant, inner_eta=eta,
+                               place=p, **base)
+        t_full[0] = full(0)
+        if t_full[0] <= full_batch_ms:
+            for p in PLACES:
+                t_full[p] = full(p)
+            place = _pick(t_full, 0, MARGIN)
     db[key] = {"variant": int(variant), "inner_eta": float(eta), "place": int(place),
                "ms": {"variant": {str(k): round(t, 4) for k, t in t_var.items()},
                       "inner_eta": {str(k): round(t, 4) for k, t in t_eta.items()},
-                      "place": {str(k): round(t, 4) for k, t in t_place.items()}}}
+                      "place": {str(k): round(t, 4) for k, t in t_place.items()},
+                      "place_full_batch": {str(k): round(t, 4) for k, t in t_full.items()}}}
     _save(db)
     return {"variant": int(variant), "inner_eta": float(eta), "place": int(place)}
 

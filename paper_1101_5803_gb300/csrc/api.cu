@@ -281,6 +281,12 @@ int pick_place(const mirage_ctx* ctx, const Prob<T>& P, int want = 0) {
             return PLACE_GLOBAL2;
         return PLACE_GLOBAL;
     }
+    if (want == 5 && sizeof(T) == 4) {
+        const KernelTable& t = table();
+        if ((t.cgls[0][PLACE_MID2][P.K < MAX_K ? P.K : 0] || t.cgls[0][PLACE_MID2][0]) &&
+            2 * ((long long)smem_bytes<T>(P, PLACE_MID) + 1024) <= ctx->max_smem_sm)
+            return PLACE_MID2;
+    }
     if (smem_bytes<T>(P, PLACE_SMEM) <= (size_t)ctx->max_smem) return PLACE_SMEM;
     if (sizeof(T) == 4 && smem_bytes<T>(P, PLACE_MID) <= (size_t)ctx->max_smem) return PLACE_MID;
     // all in the slab: two CTAs per SM where that kernel is compiled for the
@@ -490,7 +496,7 @@ int eval_impl(mirage_ctx* ctx, const mirage_problem_t* probs, int n_probs, const
     }
     const mirage_opts_t o = *opts;
     if (!(o.tol >= 0) || o.mode < 0 || o.mode > 1 || o.mem < 0 || o.mem > 1 || o.variant < 0 || o.variant > 7 ||
-        !(o.inner_eta == 0.0 || (o.inner_eta >= 1e-4 && o.inner_eta <= 0.5)) || o.place < 0 || o.place > 4) {
+        !(o.inner_eta == 0.0 || (o.inner_eta >= 1e-4 && o.inner_eta <= 0.5)) || o.place < 0 || o.place > 5) {
         set_error("eval_batch: bad options");
         return MIRAGE_ERR_ARG;
     }
@@ -685,7 +691,7 @@ int eval_impl(mirage_ctx* ctx, const mirage_problem_t* probs, int n_probs, const
         const void* fn = pick_cgls(prec, place, P.fft_m ? 0 : P.K);
         size_t item_smem = smem_bytes<T>(P, layout_of(place));
         long long item_slab = (long long)slab_bytes<T>(P, layout_of(place));
-        int per_sm = place == PLACE_GLOBAL2 ? 2 : 1, mode = 0;
+        int per_sm = two_per_sm(place) ? 2 : 1, mode = 0;
         bool fast = false;
         if (const void* ff = choose(P, mode, fast)) {
             fn = ff;

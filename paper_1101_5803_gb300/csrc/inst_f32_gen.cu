@@ -8,6 +8,7 @@ void fill_f32_gen(KernelTable& t) {
     t.cgls[0][1][0] = (const void*)k_cgls<float, 0, PLACE_GLOBAL>;
     t.cgls[0][PLACE_GLOBAL2][0] = (const void*)k_cgls<float, 0, PLACE_GLOBAL, 2>;
     t.cgls[0][2][0] = (const void*)k_cgls<float, 0, PLACE_MID>;
+    t.cgls[0][PLACE_MID2][0] = (const void*)k_cgls<float, 0, PLACE_MID, 2>;
     t.fwd[0][0] = (const void*)k_forward<float, 0>;
     t.fwd[0][9] = (const void*)k_forward<float, 9>;
     t.raytrace[0] = (const void*)k_raytrace<float>;

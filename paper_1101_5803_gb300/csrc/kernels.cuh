@@ -1301,10 +1301,13 @@ __host__ __device__ inline size_t align_up(size_t v, size_t a) {
 //   PLACE_MID    the two convolution inputs and the source vectors in
 //                shared memory, the rest in the slab (mid-size images)
 enum : int { PLACE_SMEM = 0, PLACE_GLOBAL = 1, PLACE_MID = 2 };
-// kernel-table index of the global-slab kernel compiled for two CTAs per SM
-// (its buffers are laid out as PLACE_GLOBAL)
-constexpr int PLACE_GLOBAL2 = 3;
-__host__ __device__ constexpr int layout_of(int place) { return place == PLACE_GLOBAL2 ? PLACE_GLOBAL : place; }
+// kernel-table indices of the global-slab and split kernels compiled for two
+// CTAs per SM (their buffers are laid out as PLACE_GLOBAL and PLACE_MID)
+constexpr int PLACE_GLOBAL2 = 3, PLACE_MID2 = 4;
+__host__ __device__ constexpr int layout_of(int place) {
+    return place == PLACE_GLOBAL2 ? PLACE_GLOBAL : place == PLACE_MID2 ? PLACE_MID : place;
+}
+__host__ __device__ constexpr bool two_per_sm(int place) { return place == PLACE_GLOBAL2 || place == PLACE_MID2; }
 
 template <typename T>
 __host__ __device__ inline size_t smem_bytes(const Prob<T>& P, int place) {

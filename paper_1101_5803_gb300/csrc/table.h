@@ -9,7 +9,7 @@ constexpr int MAX_K = 32;  // tap sides 1..31 (odd); index 0 = runtime-K kernel
 struct KernelTable {
     // cgls[prec][place][K], prec 0 = float, 1 = double; place = PLACE_SMEM,
     // PLACE_GLOBAL, PLACE_MID; nullptr = not compiled
-    const void* cgls[2][4][MAX_K];
+    const void* cgls[2][5][MAX_K];
     const void* fwd[2][MAX_K];
     const void* raytrace[2];
     const void* rt_trace[2];  // split ray trace: trace and count (many CTAs per candidate)

@@ -70,8 +70,8 @@ def test_tune_config_caches_and_agrees(tmp_path, monkeypatch):
 
 def test_general_kernel_placements_agree_bitwise():
     # the general kernel's work buffers in shared memory, split, or all in
-    # the L2-resident slab (one or two CTAs per SM): the same arithmetic in
-    # the same order
+    # the L2-resident slab (the last two with one or two CTAs per SM): the
+    # same arithmetic in the same order
     import __graft_entry__
     __graft_entry__.build()
     import synth
@@ -85,7 +85,7 @@ def test_general_kernel_placements_agree_bitwise():
     lens = torch.as_tensor(synth.lens_population(rng, 6), device="cuda")
     lams = torch.as_tensor(np.tile(synth.lambda_grid(5), (6, 1)), device="cuda")
     outs = [ctx.eval_batch([prob], lens, [0] * 6, lams, [5] * 6, tol=1e-6, variant=4, place=p, want_all_x=True)
-            for p in (1, 2, 3, 4)]
+            for p in (1, 2, 3, 4, 5)]
     for o in outs[1:]:
         for key in ("chi2", "reg", "iters", "all_x"):
             assert torch.equal(o[key], outs[0][key]), key

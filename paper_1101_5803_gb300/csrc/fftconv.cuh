@@ -13,8 +13,9 @@
 // Rows are transformed two at a time (one real row in the real part, the
 // next in the imaginary part, separated after the transform by the
 // Hermitian symmetry of real input).  The transforms themselves are
-// radix-2 Stockham (self-sorting) passes over a batch of rows held in
-// shared memory, with per-stage twiddle tables.
+// radix-4 Stockham (self-sorting) passes, with one radix-2 pass for odd
+// log2 M, over a batch of rows held in shared memory, with per-stage
+// twiddle tables.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -87,17 +88,54 @@ __device__ void fft_twiddles(typename CxOf<R>::type* tw, int M) {
     }
 }
 
-// nb transforms of length M, transform f at x + f * (M + 1); radix-2
-// Stockham passes ping-ponging between x and y.  Every thread of the CTA
-// takes part; the data must be complete (barrier) before the call.
+template <typename C>
+__device__ __forceinline__ C cmul(C a, C b) {
+    return cx<C>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// nb transforms of length M, transform f at x + f * (M + 1); Stockham
+// (self-sorting) passes ping-ponging between x and y: radix 4 while two
+// factors of two remain, then one radix-2 pass for odd log2 M.  A radix-r
+// pass at span ns takes, for j < M / r and k = j mod ns, the inputs
+// x[j + q M / r] (q < r) times exp(-+2 pi i q k / (r ns)), their length-r
+// DFT, and writes output p to (j - k) r + k + p ns.  Every thread of the
+// CTA takes part; the data must be complete (barrier) before the call.
 // Returns the buffer that holds the result.
 template <typename R>
 __device__ typename CxOf<R>::type* fft_batch(typename CxOf<R>::type* x, typename CxOf<R>::type* y,
                                              const typename CxOf<R>::type* tw, int M, int logM, int nb, bool inverse) {
     using C = typename CxOf<R>::type;
-    const int half = M >> 1, ld = M + 1;
-    const int nbf = nb << (logM - 1);  // butterflies per stage
-    for (int ns = 1; ns < M; ns <<= 1) {
+    const int ld = M + 1;
+    int ns = 1, lg = logM;
+    for (; lg >= 2; lg -= 2, ns <<= 2) {
+        const int q = M >> 2, lq = logM - 2;
+        for (int t = threadIdx.x; t < (nb << lq); t += blockDim.x) {
+            const int f = t >> lq, j = t & (q - 1);
+            const C* xf = x + f * ld;
+            C* yf = y + f * ld;
+            const int k = j & (ns - 1);
+            C w1 = tw[2 * ns - 1 + k];  // exp(-i pi k / (2 ns)) = exp(-2 pi i k / (4 ns))
+            if (inverse) w1.y = -w1.y;
+            const C w2 = cmul(w1, w1), w3 = cmul(w2, w1);
+            const C a = xf[j], b = cmul(w1, xf[j + q]), c = cmul(w2, xf[j + 2 * q]), d = cmul(w3, xf[j + 3 * q]);
+            const C s0 = cx<C>(a.x + c.x, a.y + c.y), s1 = cx<C>(a.x - c.x, a.y - c.y);
+            const C s2 = cx<C>(b.x + d.x, b.y + d.y), s3 = cx<C>(b.x - d.x, b.y - d.y);
+            // -i s3 for the forward transform, +i s3 for the inverse
+            const C is3 = inverse ? cx<C>(-s3.y, s3.x) : cx<C>(s3.y, -s3.x);
+            const int o = ((j - k) << 2) + k;
+            yf[o] = cx<C>(s0.x + s2.x, s0.y + s2.y);
+            yf[o + ns] = cx<C>(s1.x + is3.x, s1.y + is3.y);
+            yf[o + 2 * ns] = cx<C>(s0.x - s2.x, s0.y - s2.y);
+            yf[o + 3 * ns] = cx<C>(s1.x - is3.x, s1.y - is3.y);
+        }
+        __syncthreads();
+        C* t = x;
+        x = y;
+        y = t;
+    }
+    if (lg == 1) {
+        const int half = M >> 1;
+        const int nbf = nb << (logM - 1);
         for (int t = threadIdx.x; t < nbf; t += blockDim.x) {
             const int f = t >> (logM - 1), j = t & (half - 1);
             const C* xf = x + f * ld;
@@ -105,11 +143,10 @@ __device__ typename CxOf<R>::type* fft_batch(typename CxOf<R>::type* x, typename
             const int k = j & (ns - 1);
             C w = tw[ns - 1 + k];
             if (inverse) w.y = -w.y;
-            const C a = xf[j], b0 = xf[j + half];
-            const C b = cx<C>(w.x * b0.x - w.y * b0.y, w.x * b0.y + w.y * b0.x);
-            const int d = ((j - k) << 1) + k;
-            yf[d] = cx<C>(a.x + b.x, a.y + b.y);
-            yf[d + ns] = cx<C>(a.x - b.x, a.y - b.y);
+            const C a = xf[j], b = cmul(w, xf[j + half]);
+            const int o = ((j - k) << 1) + k;
+            yf[o] = cx<C>(a.x + b.x, a.y + b.y);
+            yf[o + ns] = cx<C>(a.x - b.x, a.y - b.y);
         }
         __syncthreads();
         C* t = x;

@@ -158,32 +158,27 @@ __device__ __forceinline__ void conv_tile_fast(const float* __restrict__ Pb, int
     }
 }
 
-// Sum of two compensated (hi, lo) pairs with error-free FP32 steps.
-__device__ __forceinline__ float2 pair_add(float2 a, float2 b) {
-    float s, e;
-    two_sum(a.x, b.x, s, e);
-    e += a.y + b.y;
-    const float hi = s + e;
-    return make_float2(hi, e - (hi - s));
-}
-
-// Block sum with one barrier, delivered to every thread of an NTHREADS
-// block: the warps' compensated pairs are combined along a fixed binary
-// tree (depth log2 of the warp count instead of a serial chain), so every
-// thread holds the same value.  `buf` holds 2 x 64 floats; alternate `half`.
-__device__ __forceinline__ float2 block_pair_tree(float v, float* buf, int half) {
+// Block sum of non-negative FP32 terms with one barrier, delivered to every
+// thread of an NTHREADS block: a butterfly within each warp, then the warp
+// sums along a fixed binary tree, so every thread holds the same value.
+// Sums of non-negative terms have no cancellation, so plain FP32 additions
+// keep ~log2(n) 2^-24 relative accuracy, far inside what the CG coefficients
+// of an inner solve (which stops at a 1e-2 reduction) need.  `buf` holds
+// 2 x 64 floats; alternate `half`.
+__device__ __forceinline__ float block_sum_tree(float v, float* buf, int half) {
     constexpr int NW = NTHREADS / 32;
-    float2* b = reinterpret_cast<float2*>(buf) + 32 * half;
-    const float2 w = warp_pair(v);
-    if ((threadIdx.x & 31) == 0) b[threadIdx.x >> 5] = w;
+    float* b = buf + 64 * half;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) b[threadIdx.x >> 5] = v;
     __syncthreads();
-    float2 x[NW];
+    float x[NW];
 #pragma unroll
     for (int i = 0; i < NW; ++i) x[i] = b[i];
 #pragma unroll
     for (int st = 1; st < NW; st *= 2)
 #pragma unroll
-        for (int i = 0; i + st < NW; i += 2 * st) x[i] = pair_add(x[i], x[i + st]);
+        for (int i = 0; i + st < NW; i += 2 * st) x[i] += x[i + st];
     return x[0];
 }
 
@@ -304,7 +299,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_cgls_fast(const __grid_constant
     double* red = reinterpret_cast<double*>(smem + 16);
     FastItem* fi = reinterpret_cast<FastItem*>(smem + 16 + 2 * 33 * sizeof(double));
     unsigned long long* phs = reinterpret_cast<unsigned long long*>(smem + 16 + 2 * 33 * sizeof(double) + 128);
-    float* pbuf = reinterpret_cast<float*>(red);  // 2 x 32 float2 for block_pair_tree
+    float* pbuf = reinterpret_cast<float*>(red);  // 2 x 64 floats for block_sum_tree
     int last_c = -1;
     int which = 0;
     // per-phase clocks (thread 0, kept in shared memory): 0 L p + H p,
@@ -756,9 +751,8 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_cgls_fast(const __grid_constant
             int half = 0, it_in = 0, best_it = 0, brk = 0, stop = 0;
             float gam, g0, best = 1.f;
             {
-                const float2 gp = block_pair_tree(gs, pbuf, half);  // its barrier also completes p
+                gam = block_sum_tree(gs, pbuf, half);  // its barrier also completes p
                 half ^= 1;
-                gam = gp.x + gp.y;
                 g0 = gam;
                 brk = !isfinite(gam);
                 stop = brk || !(gam > 0.f) || total_it >= maxit;
@@ -850,9 +844,8 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_cgls_fast(const __grid_constant
                     }
                         PHASE(1);
                         // delta = p^T A p; the reduction's barrier also completes P2
-                        const float2 dl = block_pair_tree(dl_part, pbuf, half);
+                        const float delta = block_sum_tree(dl_part, pbuf, half);
                         half ^= 1;
-                        const float delta = dl.x + dl.y;
                         PHASE(2);
                         if (!(delta > 0.f) || !isfinite(delta)) {
                             brk = 1;
@@ -1000,10 +993,9 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_cgls_fast(const __grid_constant
                     }
                 }
                 PHASE(7);
-                const float2 gp = block_pair_tree(gsum, pbuf, half);
+                const float gnew = block_sum_tree(gsum, pbuf, half);
                 half ^= 1;
                 PHASE(8);
-                const float gnew = gp.x + gp.y;
                 const float bt = gnew / gam;
                 gam = gnew;
                 ++it_in;

@@ -178,85 +178,30 @@ __device__ __forceinline__ double block_sum(double v, double* red, int which) {
     return r[32];
 }
 
-// Error-free FP32 summation step (Knuth's two-sum): s + e == a + b exactly.
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-    s = a + b;
-    const float bb = s - a;
-    e = (a - (s - bb)) + (b - bb);
-}
-
-// Warp sum of FP32 values carried as an unevaluated pair hi + lo (about
-// twice FP32 precision) on the FP32 pipe; FP64 arithmetic is reserved for
-// the final cross-warp sum.
-__device__ __forceinline__ double warp_sum_pair(float v) {
-    float hi = v, lo = 0.f;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
-        const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
-        float s, e;
-        two_sum(hi, h2, s, e);
-        e += lo + l2;
-        hi = s + e;
-        lo = e - (hi - s);
-    }
-    return (double)hi + (double)lo;
-}
-
-// Block sum delivered to thread 0 only (FP64 across warps); other threads
-// get 0.  The caller lets thread 0 derive its scalars, then synchronises.
+// Block sum of non-negative terms delivered to thread 0 only (FP64 across
+// warps); other threads get 0.  The caller lets thread 0 derive its
+// scalars, then synchronises.  FP32 terms are summed within a warp by a
+// plain FP32 butterfly: sums of non-negative terms have no cancellation, so
+// this keeps ~5 2^-24 relative accuracy, ample for the inner solves' CG
+// coefficients (the refinement's sums are FP64).
 template <typename T>
 __device__ __forceinline__ double block_sum_to0(T v, double* red) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     double wv;
-    if constexpr (sizeof(T) == 4)
-        wv = warp_sum_pair(v);
-    else
+    if constexpr (sizeof(T) == 4) {
+        float f = v;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) f += __shfl_xor_sync(0xffffffffu, f, o);
+        wv = (double)f;
+    } else {
         wv = warp_sum((double)v);
+    }
     if (lane == 0) red[warp] = wv;
     __syncthreads();
     double t = 0.0;
     if (threadIdx.x == 0)
         for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
     return t;
-}
-
-// Block sum with one barrier, delivered to every thread: each warp
-// publishes its compensated (hi, lo) pair, then every thread adds the
-// pairs in the same order with error-free FP32 steps, so all threads hold
-// the same value (accurate to ~1e-14 relative, like an FP64 sum of the
-// FP32 terms).  `buf` holds 2 x 64 floats; alternate `half` between calls.
-__device__ __forceinline__ float2 warp_pair(float v) {
-    float hi = v, lo = 0.f;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
-        const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
-        float s, e;
-        two_sum(hi, h2, s, e);
-        e += lo + l2;
-        hi = s + e;
-        lo = e - (hi - s);
-    }
-    return make_float2(hi, lo);
-}
-
-__device__ __forceinline__ float2 block_pair_all(float v, float* buf, int half) {
-    float2* b = reinterpret_cast<float2*>(buf) + 32 * half;
-    const float2 w = warp_pair(v);
-    if ((threadIdx.x & 31) == 0) b[threadIdx.x >> 5] = w;
-    __syncthreads();
-    float hi = 0.f, lo = 0.f;
-    const int nw = blockDim.x >> 5;
-    for (int i = 0; i < nw; ++i) {
-        const float2 x = b[i];
-        float s, e;
-        two_sum(hi, x.x, s, e);
-        e += lo + x.y;
-        hi = s + e;
-        lo = e - (hi - s);
-    }
-    return make_float2(hi, lo);
 }
 
 // Scalars of the inner CGLS, written by thread 0 and read by all threads

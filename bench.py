@@ -34,7 +34,7 @@ if ROOT not in sys.path:
 METRIC = "lens-model evals/s at 64^2 image, CG rel-res 1e-6 (256 cand x 16 lambda)"
 UNIT = "evals/s"
 N_CAND, N_LAM, TOL = 256, 16, 1e-6
-TIGHT_TOL = 3e-8  # the tighter internal tolerance of the accuracy section
+TIGHT_TOL = 2e-8  # the tighter internal tolerance of the accuracy section
 CONFIG = {"workload": "ga64: 64x64 image 0.05\"/px, 32x32 source +-0.8\", 9x9 PSF sigma 1.5px, Laplacian H, "
                       "256 candidates x 16 lambdas 1e-4..1e2, CGLS rel-res 1e-6, L-curve corner",
           "global_batch": N_CAND, "n_lambda": N_LAM, "l2": "flushed between timed steps (512 MiB write)"}
@@ -341,7 +341,7 @@ def run_gpu(args):
         sel = torch.as_tensor(idx, device="cuda")
         acc = {"sample": f"{n_acc} candidates x {N_LAM} lambdas of the timed population (FP64 dense-Cholesky oracle)",
                "oracle_s": t_oracle}
-        for name, tol in (("tol_1e-6", TOL), ("tol_3e-8", TIGHT_TOL)):
+        for name, tol in (("tol_1e-6", TOL), (f"tol_{TIGHT_TOL:g}", TIGHT_TOL)):
             sub = ctx.eval_batch(probs, wl.lens[sel].contiguous(), wl.prob_idx[idx], wl.lambdas[sel].contiguous(),
                                  wl.n_lam[idx], tol=tol, maxit=100000, want_all_x=True)
             X = sub["all_x"].double().cpu().numpy()
@@ -814,7 +814,7 @@ def run_workload(name: str, args) -> int:
             a, b = _errs(ct[j], Xt[j], mw.problems[c].geom.ns, refs[c], mw.n_lam[c])
             ce.append(a)
             se.append(b)
-        res["oracle_sample_tol_3e-8"] = dict(_summ(ce, se), items_flagged=int(
+        res[f"oracle_sample_tol_{TIGHT_TOL:g}"] = dict(_summ(ce, se), items_flagged=int(
             ((tout["item_status"].cpu().numpy() & 7) != 0)[np.arange(tout["item_status"].shape[1])[None, :]
                                                              < mw.n_lam[pick][:, None]].sum()))
     elif name == "ga128":

@@ -284,7 +284,7 @@ def test_eval_fp32_64px(mods, ctx32):
     _report("fp32_ga64", 1e-6, rec)
 
 
-TIGHT_TOL = 3e-8
+TIGHT_TOL = 2e-8
 
 
 def test_eval_fp32_64px_tight_tolerance(mods, ctx32):

@@ -134,7 +134,7 @@ typedef struct {
                           they do not apply.  Other values: MIRAGE_ERR_ARG. */
     double inner_eta;  /* FP32 contexts: the relative residual reduction each inner
                           solve of the refinement aims for (each solve stops at
-                          max(inner_eta, 0.8 tol / current residual)); 0 = the
+                          max(inner_eta, min(0.5, 0.8 tol / current residual))); 0 = the
                           default 0.01; otherwise 1e-4 <= inner_eta <= 0.5, else
                           MIRAGE_ERR_ARG.  Changes the iteration path, not the
                           solution (to tol).  FP64 contexts ignore it. */

@@ -722,7 +722,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_cgls_fast(const __grid_constant
             }
             prev_rel = rel64;  // accepted residuals decrease: this is the best iterate
             for (int i = tid; i < g.ns; i += bs) w.xb[i] = w.x64[i];
-            const double target = fmax(eta_min, FINAL_MARGIN * A.tol / rel64);
+            const double target = fmax(eta_min, fmin(MAX_TARGET, FINAL_MARGIN * A.tol / rel64));
 
             // ---- inner solve of the correction equation A d = r: Jacobi-
             // preconditioned CG on the normal equations (r = the FP64 residual

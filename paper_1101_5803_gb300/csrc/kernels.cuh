@@ -1252,8 +1252,11 @@ __host__ __device__ inline size_t align_up(size_t v, size_t a) {
 // (measured: every item of the benchmark batch still met the tolerance in
 // that pass, largest residual 0.998 tol) and is 5% faster than 0.3.  FP64
 // contexts, whose single inner solve normally reaches the tolerance, keep
-// the margin FINAL_MARGIN64.
-constexpr double FINAL_MARGIN = 0.8, FINAL_MARGIN64 = 0.3;
+// the margin FINAL_MARGIN64.  Every solve still aims for at least a
+// reduction by MAX_TARGET: a residual just above the tolerance (a warm
+// start) would otherwise ask for a reduction near 1, and two such steps in
+// a row read as stagnation.
+constexpr double FINAL_MARGIN = 0.8, FINAL_MARGIN64 = 0.3, MAX_TARGET = 0.5;
 
 enum : int { PLACE_SMEM = 0, PLACE_GLOBAL = 1, PLACE_MID = 2 };
 // kernel-table indices of the global-slab and split kernels compiled for two
@@ -1662,7 +1665,8 @@ __global__ void __launch_bounds__(NTHREADS, MINB) k_cgls(CglsArgs<T> A) {
             // Every vector of the recursion is of the size of the correction,
             // so rounding stays relative to it (an image-space CGLS residual
             // would carry the data misfit into every gradient).
-            const double target = fmax(eta_min, (sizeof(T) == 4 ? FINAL_MARGIN : FINAL_MARGIN64) * A.tol / rel64);
+            const double target =
+                fmax(eta_min, fmin(MAX_TARGET, (sizeof(T) == 4 ? FINAL_MARGIN : FINAL_MARGIN64) * A.tol / rel64));
             for (int i = tid; i < g.ns; i += bs) {
                 w.x[i] = 0;
                 const T z = w.minv[i] * w.s[i];
